@@ -1,0 +1,458 @@
+"""CPU oracle for the ML-KDMC correlated-pair path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product library never does.
+
+``mlkd_oracle.c`` restates Alg. 1 (KD path), Alg. 2 (correlated pair) and the
+random-number mapping/aggregation of Sec. 3 in FP64 with its own Philox4x32-10.
+This module adds, in plain numpy:
+
+* the quantities of interest F(x(T)) and the level difference
+  Y_l = F(x_l) - F(x_{l-1}) of eq. mlmc-compact (Sec. 4.1);
+* the per-level sums that set the sample counts, and the histogram counts of
+  the density estimator;
+* the adaptive sample-count rule of eqs. Nopt1/Noptj (Sec. 4.1).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mlkd_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
+
+QOI_X2 = 0            # F(x) = x^2 (free space)
+QOI_X2_PERIODIC = 1   # F(x) = (x mod 1)^2 on the periodic unit interval
+QOI_DENSITY = 2       # histogram density drives the sample counts
+INIT_ORIGIN = 0
+INIT_COSINE = 1
+RECIPE_24 = 0         # 24-bit uniforms (FP32 form of the stream)
+RECIPE_53 = 1         # 53-bit uniforms (FP64 form of the stream)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FP contraction, no fast-math)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".tmp%d" % os.getpid()
+    subprocess.check_call(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
+                           "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class LevelDesc(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double), ("mu", ctypes.c_double), ("sigma", ctypes.c_double),
+                ("dt", ctypes.c_double), ("n", ctypes.c_int64), ("M", ctypes.c_int32),
+                ("level", ctypes.c_int32), ("init", ctypes.c_int32), ("recipe", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("request", ctypes.c_uint32)]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            d, i64, u64, u32 = ctypes.c_double, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32
+            L.orc_philox4x32_10.argtypes = [P(u32), P(u32), P(u32)]
+            L.orc_philox4x32_10.restype = None
+            L.orc_uniform24.argtypes = [u32]
+            L.orc_uniform24.restype = d
+            L.orc_uniform53.argtypes = [u32, u32]
+            L.orc_uniform53.restype = d
+            for name in ("orc_fs", "orc_gs", "orc_hs", "orc_cosine_G", "orc_cosine_inverse"):
+                getattr(L, name).argtypes = [d]
+                getattr(L, name).restype = d
+            L.orc_advection.argtypes = [d, d, d, d]
+            L.orc_advection.restype = d
+            L.orc_diffusion.argtypes = [d, d, d, d, d]
+            L.orc_diffusion.restype = d
+            L.orc_zeta.argtypes = [d, d]
+            L.orc_zeta.restype = d
+            L.orc_theta_prime.argtypes = [d, d]
+            L.orc_theta_prime.restype = d
+            L.orc_beta.argtypes = [d, d, d]
+            L.orc_beta.restype = d
+            L.orc_pairs.argtypes = [P(LevelDesc), u64, i64, P(d), P(d), P(i64), P(i64)]
+            L.orc_pairs.restype = ctypes.c_int
+            L.orc_single_paths.argtypes = [P(LevelDesc), u64, i64, P(d), P(i64)]
+            L.orc_single_paths.restype = ctypes.c_int
+            L.orc_pair_injected.argtypes = [P(LevelDesc), d, P(d), P(d), P(d), i64, P(d), P(d),
+                                            P(i64), P(i64), i64, P(i64), P(d), P(d), P(d), P(d),
+                                            P(i64)]
+            L.orc_pair_injected.restype = ctypes.c_int
+            L.orc_coarse_draws.argtypes = [P(LevelDesc), u64, i64, i64, P(d), P(d), P(d), P(i64)]
+            L.orc_coarse_draws.restype = i64
+            L.orc_stream_draws.argtypes = [P(LevelDesc), u64, i64, P(d), P(d), P(d), P(d)]
+            L.orc_stream_draws.restype = None
+            _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 block (SC'11) for a 4-word counter and 2-word key."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().orc_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+# --------------------------------------------------------------------------
+# Problem description (the paper's problem statement, Sec. 4.1, in the
+# diffusive scaling: R = 1/eps^2, sigma = 1/eps).
+# --------------------------------------------------------------------------
+@dataclass
+class Problem:
+    eps: float
+    T: float
+    dt0: float
+    M: int = 2
+    L: int = 1
+    qoi: int = QOI_X2
+    init: int = INIT_ORIGIN
+    nbins: int = 0
+    lo: float = -3.0
+    hi: float = 3.0
+    tol: float = 0.0
+    n_warmup: int = 100
+    recipe: int = RECIPE_53
+    seed: int = 0
+    request: int = 0
+    mu: float = 0.0
+    n_fixed: list = field(default_factory=list)
+
+    @property
+    def R(self):
+        return 1.0 / (self.eps * self.eps)
+
+    @property
+    def sigma(self):
+        return 1.0 / self.eps
+
+    def steps0(self) -> int:
+        r = self.T / self.dt0
+        n0 = int(round(r))
+        if n0 < 1 or abs(r - n0) > 1e-12 * max(1.0, r):
+            raise ValueError("T/dt0 must be a positive integer")
+        return n0
+
+    def dt(self, level: int) -> float:
+        return self.dt0 / float(self.M) ** level
+
+    def nsteps(self, level: int) -> int:
+        return self.steps0() * self.M ** level
+
+    def level_desc(self, level: int) -> LevelDesc:
+        d = LevelDesc()
+        d.R, d.mu, d.sigma = self.R, self.mu, self.sigma
+        d.dt = self.dt(level)
+        d.n = self.nsteps(level)
+        d.M = self.M
+        d.level = level
+        d.init = self.init
+        d.recipe = self.recipe
+        d.seed = self.seed
+        d.request = self.request
+        return d
+
+    def bin_range(self):
+        if self.init == INIT_COSINE or self.qoi == QOI_X2_PERIODIC:
+            return 0.0, 1.0
+        return self.lo, self.hi
+
+    def periodic(self) -> bool:
+        return self.qoi == QOI_X2_PERIODIC or self.init == INIT_COSINE
+
+
+# --------------------------------------------------------------------------
+# Paths and pairs.
+# --------------------------------------------------------------------------
+def pairs(problem: Problem, level: int, first: int, count: int, threads: int = 1):
+    """Final positions (x_l, x_{l-1}) and event counts of pairs
+    [first, first+count) of one level.  Level 0 is Alg. 1 (x_c = 0)."""
+    d = problem.level_desc(level)
+    xf = np.zeros(count, np.float64)
+    xc = np.zeros(count, np.float64)
+    ef = np.zeros(count, np.int64)
+    ec = np.zeros(count, np.int64)
+    L = lib()
+    threads = max(1, min(int(threads), count if count > 0 else 1))
+    bounds = np.linspace(0, count, threads + 1).astype(np.int64)
+
+    def work(t):
+        a, b = int(bounds[t]), int(bounds[t + 1])
+        if b <= a:
+            return 0
+        dt = ctypes.c_double
+        i64 = ctypes.c_int64
+        return L.orc_pairs(ctypes.byref(d), first + a, b - a,
+                           ctypes.cast(xf.ctypes.data + 8 * a, ctypes.POINTER(dt)),
+                           ctypes.cast(xc.ctypes.data + 8 * a, ctypes.POINTER(dt)),
+                           ctypes.cast(ef.ctypes.data + 8 * a, ctypes.POINTER(i64)),
+                           ctypes.cast(ec.ctypes.data + 8 * a, ctypes.POINTER(i64)))
+
+    if threads == 1:
+        rcs = [work(0)]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            rcs = list(ex.map(work, range(threads)))
+    if any(rc != 0 for rc in rcs):
+        raise RuntimeError("oracle pair simulation failed: %r" % rcs)
+    return xf, xc, ef, ec
+
+
+def single_paths(problem: Problem, level: int, first: int, count: int, key_level: int = None):
+    """Independent single-level (Alg. 1) paths at dt_level, keyed by key_level."""
+    d = problem.level_desc(level)
+    if key_level is not None:
+        d.level = key_level
+    x = np.zeros(count, np.float64)
+    ev = np.zeros(count, np.int64)
+    rc = lib().orc_single_paths(ctypes.byref(d), first, count, _ptr(x, ctypes.c_double),
+                                _ptr(ev, ctypes.c_int64))
+    if rc:
+        raise RuntimeError("oracle path simulation failed")
+    return x, ev
+
+
+def pair_injected(R, mu, sigma, dt, n, M, x0, nu, E, chi, level=1):
+    """One path (level 0) or pair (level >= 1) on caller-chosen random numbers:
+    nu[k], E[k] for k = 0..K and chi[k] for k = 0..K-1 (the paper's y_l)."""
+    nu = np.ascontiguousarray(nu, np.float64)
+    E = np.ascontiguousarray(E, np.float64)
+    chi = np.ascontiguousarray(chi, np.float64)
+    assert len(nu) == len(E) and len(chi) >= len(nu) - 1
+    d = LevelDesc()
+    d.R, d.mu, d.sigma, d.dt, d.n, d.M, d.level = R, mu, sigma, dt, n, M, level
+    cap = 4096
+    kappa = np.zeros(cap, np.int64)
+    nu_t, E_t, chi_t, cc = (np.zeros(cap) for _ in range(4))
+    xf, xc = ctypes.c_double(), ctypes.c_double()
+    ef, ec, nco = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    dd = ctypes.c_double
+    rc = lib().orc_pair_injected(ctypes.byref(d), x0, _ptr(nu, dd), _ptr(E, dd), _ptr(chi, dd),
+                                 len(nu), ctypes.byref(xf), ctypes.byref(xc), ctypes.byref(ef),
+                                 ctypes.byref(ec), cap, _ptr(kappa, ctypes.c_int64),
+                                 _ptr(nu_t, dd), _ptr(E_t, dd), _ptr(chi_t, dd), _ptr(cc, dd),
+                                 ctypes.byref(nco))
+    if rc:
+        raise RuntimeError("injected pair ran out of random numbers (rc=%d)" % rc)
+    k = nco.value
+    return dict(xf=xf.value, xc=xc.value, ev_f=ef.value, ev_c=ec.value,
+                kappa=kappa[:k].copy(), nu_t=nu_t[:k].copy(), E_t=E_t[:k].copy(),
+                chi_t=chi_t[:k].copy(), coarse_collision=cc[:k].copy())
+
+
+def coarse_draws(problem: Problem, level: int, first: int, count: int, cap: int):
+    """Aggregated coarse random numbers (nu~, E~, chi~) of Philox pairs."""
+    d = problem.level_desc(level)
+    nu_t, E_t, chi_t = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+    pair_of = np.zeros(cap, np.int64)
+    dd = ctypes.c_double
+    w = lib().orc_coarse_draws(ctypes.byref(d), first, count, cap, _ptr(nu_t, dd), _ptr(E_t, dd),
+                               _ptr(chi_t, dd), _ptr(pair_of, ctypes.c_int64))
+    if w < 0:
+        raise RuntimeError("oracle coarse draws failed")
+    return nu_t[:w], E_t[:w], chi_t[:w], pair_of[:w]
+
+
+def stream_draws(problem: Problem, level: int, pair: int, K: int):
+    """(nu_0, E_0, u_x0) and (nu_k, E_k, chi_{k-1}) for k = 1..K of one stream."""
+    d = problem.level_desc(level)
+    init = np.zeros(3)
+    nu, E, chi = np.zeros(K), np.zeros(K), np.zeros(K)
+    dd = ctypes.c_double
+    lib().orc_stream_draws(ctypes.byref(d), pair, K, _ptr(init, dd), _ptr(nu, dd), _ptr(E, dd),
+                           _ptr(chi, dd))
+    return init, nu, E, chi
+
+
+# --------------------------------------------------------------------------
+# Quantities of interest and level sums (Sec. 4.1).
+# --------------------------------------------------------------------------
+def qoi_values(problem: Problem, x: np.ndarray) -> np.ndarray:
+    if problem.periodic():
+        xm = x - np.floor(x)
+        return xm * xm
+    return x * x
+
+
+def bin_index(problem: Problem, x: np.ndarray) -> np.ndarray:
+    """Histogram bin of each position; -1 when it falls outside [lo, hi)
+    (free space).  Periodic problems wrap x into [0, 1) first."""
+    lo, hi = problem.bin_range()
+    nb = problem.nbins
+    if problem.periodic():
+        x = x - np.floor(x)
+    h = (hi - lo) / nb
+    b = np.floor((x - lo) / h).astype(np.int64)
+    b[(x < lo) | (x >= hi)] = -1
+    b[b >= nb] = nb - 1
+    return b
+
+
+@dataclass
+class LevelSums:
+    n: int = 0
+    sy: float = 0.0
+    sy2: float = 0.0
+    sqf: float = 0.0
+    sqf2: float = 0.0
+    sqc: float = 0.0
+    sqc2: float = 0.0
+    events_f: int = 0
+    events_c: int = 0
+    hist_f: np.ndarray = None
+    hist_c: np.ndarray = None
+    hist_both: np.ndarray = None
+
+    def add(self, o: "LevelSums"):
+        self.n += o.n
+        for k in ("sy", "sy2", "sqf", "sqf2", "sqc", "sqc2"):
+            setattr(self, k, getattr(self, k) + getattr(o, k))
+        self.events_f += o.events_f
+        self.events_c += o.events_c
+        if o.hist_f is not None:
+            if self.hist_f is None:
+                self.hist_f = np.zeros_like(o.hist_f)
+                self.hist_c = np.zeros_like(o.hist_c)
+                self.hist_both = np.zeros_like(o.hist_both)
+            self.hist_f += o.hist_f
+            self.hist_c += o.hist_c
+            self.hist_both += o.hist_both
+
+    def mean(self):
+        return self.sy / self.n if self.n else 0.0
+
+    def var(self):
+        if self.n < 2:
+            return 0.0
+        return max(0.0, (self.sy2 - self.sy * self.sy / self.n) / (self.n - 1))
+
+    def cost(self):
+        return (self.events_f + self.events_c) / self.n if self.n else 0.0
+
+
+def level_sums(problem: Problem, level: int, xf, xc, ef, ec) -> LevelSums:
+    qf = qoi_values(problem, xf)
+    if level == 0:
+        qc = np.zeros_like(qf)
+        y = qf
+    else:
+        qc = qoi_values(problem, xc)
+        if problem.periodic():
+            y = qf - qc
+        else:
+            y = (xf - xc) * (xf + xc)     # x_f^2 - x_c^2 without cancellation
+    s = LevelSums(n=len(xf), sy=float(np.sum(y)), sy2=float(np.sum(y * y)),
+                  sqf=float(np.sum(qf)), sqf2=float(np.sum(qf * qf)),
+                  sqc=float(np.sum(qc)), sqc2=float(np.sum(qc * qc)),
+                  events_f=int(np.sum(ef)), events_c=int(np.sum(ec)))
+    if problem.nbins > 0:
+        nb = problem.nbins
+        bf = bin_index(problem, xf)
+        hf = np.bincount(bf[bf >= 0], minlength=nb).astype(np.int64)
+        if level == 0:
+            hc = np.zeros(nb, np.int64)
+            hb = np.zeros(nb, np.int64)
+        else:
+            bc = bin_index(problem, xc)
+            hc = np.bincount(bc[bc >= 0], minlength=nb).astype(np.int64)
+            same = (bf == bc) & (bf >= 0)
+            hb = np.bincount(bf[same], minlength=nb).astype(np.int64)
+        s.hist_f, s.hist_c, s.hist_both = hf, hc, hb
+    return s
+
+
+def run_level(problem: Problem, level: int, first: int, count: int, threads: int = 1) -> LevelSums:
+    xf, xc, ef, ec = pairs(problem, level, first, count, threads)
+    return level_sums(problem, level, xf, xc, ef, ec)
+
+
+# --------------------------------------------------------------------------
+# Adaptive MLMC (eqs. mse, statistical_contraint, Nopt1, Noptj; Sec. 4.1).
+# --------------------------------------------------------------------------
+def level_variance(problem: Problem, s: LevelSums) -> float:
+    """V_l of the quantity that sets N_l.  For a density QoI: the largest bin
+    variance of the per-bin density difference (sup norm over bins)."""
+    if problem.qoi == QOI_DENSITY and problem.nbins > 0 and s.n >= 2:
+        lo, hi = problem.bin_range()
+        h = (hi - lo) / problem.nbins
+        sy = (s.hist_f - s.hist_c).astype(np.float64)
+        sy2 = (s.hist_f + s.hist_c - 2 * s.hist_both).astype(np.float64)
+        v = (sy2 - sy * sy / s.n) / (s.n - 1)
+        return float(max(0.0, v.max())) / (h * h)
+    return s.var()
+
+
+def optimal_counts(V, C, tol):
+    """N_j = ceil(2/tol^2 sqrt(V_j/C_j) sum_i sqrt(V_i C_i))  (eqs. Nopt1/Noptj)."""
+    total = sum(math.sqrt(v * c) for v, c in zip(V, C))
+    out = []
+    for v, c in zip(V, C):
+        if v <= 0.0 or c <= 0.0:
+            out.append(0)
+        else:
+            out.append(int(math.ceil(2.0 / (tol * tol) * math.sqrt(v / c) * total)))
+    return out
+
+
+@dataclass
+class MLMCResult:
+    estimate: float
+    variance: float
+    levels: list
+    density: np.ndarray = None
+
+
+def estimate(problem: Problem, threads: int = 1, max_rounds: int = 64) -> MLMCResult:
+    """Adaptive MLMC on levels 0..L: warm-up, then grow N_l to the optimal
+    counts until the statistical constraint holds."""
+    L = problem.L
+    sums = [LevelSums() for _ in range(L + 1)]
+    if problem.n_fixed:
+        for l in range(L + 1):
+            sums[l].add(run_level(problem, l, 0, int(problem.n_fixed[l]), threads))
+    else:
+        for l in range(L + 1):
+            sums[l].add(run_level(problem, l, 0, problem.n_warmup, threads))
+        for _ in range(max_rounds):
+            V = [level_variance(problem, s) for s in sums]
+            C = [s.cost() for s in sums]
+            target = optimal_counts(V, C, problem.tol)
+            grew = False
+            for l in range(L + 1):
+                if target[l] > sums[l].n:
+                    sums[l].add(run_level(problem, l, sums[l].n, target[l] - sums[l].n, threads))
+                    grew = True
+            if not grew:
+                break
+    est = sum(s.mean() for s in sums)
+    var = sum(level_variance(problem, s) / s.n for s in sums if s.n > 0)
+    dens = None
+    if problem.nbins > 0:
+        lo, hi = problem.bin_range()
+        h = (hi - lo) / problem.nbins
+        dens = sum((s.hist_f - s.hist_c) / s.n for s in sums) / h
+    return MLMCResult(est, var, sums, dens)

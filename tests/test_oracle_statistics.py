@@ -1,0 +1,178 @@
+"""Statistical pins of the oracle (CPU only).
+
+* Mean-square displacement: for the homogeneous background the KD scheme
+  reproduces the first two moments of the kinetic process at every step size
+  (a and d are the exact conditional mean and spread, Sec. 2), so
+  E[x(T)^2] = mu^2 T^2 + 2 sigma^2/R^2 (RT - 1 + e^{-RT}); with R = 1/eps^2 and
+  sigma = 1/eps this is 2(T - eps^2(1 - e^{-T/eps^2})).  This holds for the
+  fine and for the coarse path of every pair, so E[Y_l] = 0 for F = x^2.
+* Brownian limit eps -> 0: x(T) ~ N(0, 2T).
+* Coarse random numbers: nu~ ~ N(0,1), E~ ~ Exp(1), chi~ ~ N(0,1) (Sec. 3.2,
+  tested as in Sec. 5.1 with the Anderson-Darling statistic).
+* Coarse law: x_{l-1}(T) of a pair has the law of an independent single-level
+  run at dt_{l-1} (two-sample tests).
+* Telescoping (eq. telsum): sum of level means = finest-level mean.
+* Sample counts (eqs. Nopt1/Noptj) and the MLMC error bound (eq. mse).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import stats
+
+
+def msd(eps, T, mu=0.0):
+    return mu * mu * T * T + 2.0 * (T - eps * eps * (1.0 - math.exp(-T / (eps * eps))))
+
+
+def ad_statistic(x, cdf):
+    """Anderson-Darling A^2 of a sample against a fully specified CDF
+    (eq. anderson, Sec. 5.1)."""
+    x = np.sort(np.asarray(x))
+    n = x.size
+    F = np.clip(cdf(x), 1e-300, 1 - 1e-16)
+    i = np.arange(1, n + 1)
+    return -n - np.sum((2 * i - 1) / n * (np.log(F) + np.log1p(-F[::-1])))
+
+
+# Asymptotic critical values of A^2 for a fully specified law: 1 % -> 3.857,
+# 0.1 % -> 5.973.  The paper rejects at p < 0.01 per test (Sec. 5.1); the
+# parametrised test below runs 24 such tests, so each uses the 0.1 % value to
+# keep the family-wise false-rejection rate near 2 %.
+AD_CRIT_01PCT = 5.973
+
+
+@pytest.mark.parametrize("eps,T,dt0,levels", [
+    (0.5, 0.5, 0.1, (0, 1, 2, 3)),      # the 2-level free-space configuration, R dt = 0.4 .. 0.05
+    (0.1, 1.0, 0.5, (0, 2, 4)),         # diffusive, R dt = 50 .. 3
+    (2.0, 1.0, 0.25, (0, 1, 3)),        # kinetic, R dt = 0.06 ..
+])
+def test_second_moment_closed_form(orc, eps, T, dt0, levels):
+    p = orc.Problem(eps=eps, T=T, dt0=dt0, M=2, L=max(levels), seed=21)
+    exact = msd(eps, T)
+    n = 200_000
+    for level in levels:
+        xf, xc, _, _ = orc.pairs(p, level, 0, n, threads=8)
+        for x in ([xf] if level == 0 else [xf, xc]):
+            q = x * x
+            assert abs(q.mean() - exact) < 4.5 * q.std() / math.sqrt(n), (level, q.mean(), exact)
+
+
+def test_first_and_second_moment_with_drift(orc):
+    eps, T, mu = 0.4, 0.5, 1.3
+    p = orc.Problem(eps=eps, T=T, dt0=0.25, M=2, L=2, seed=5, mu=mu)
+    n = 200_000
+    for level in (0, 2):
+        xf, xc, _, _ = orc.pairs(p, level, 0, n, threads=8)
+        for x in ([xf] if level == 0 else [xf, xc]):
+            assert abs(x.mean() - mu * T) < 4.5 * x.std() / math.sqrt(n)
+            q = x * x
+            assert abs(q.mean() - msd(eps, T, mu)) < 4.5 * q.std() / math.sqrt(n)
+
+
+def test_brownian_limit(orc):
+    p = orc.Problem(eps=1e-4, T=1.0, dt0=0.5, M=2, L=2, seed=8)
+    for level in (0, 2):
+        xf, xc, _, _ = orc.pairs(p, level, 0, 20_000, threads=8)
+        assert stats.kstest(xf / math.sqrt(2.0), "norm").pvalue > 1e-3
+        if level:
+            assert stats.kstest(xc / math.sqrt(2.0), "norm").pvalue > 1e-3
+
+
+@pytest.mark.parametrize("eps,dt0,M,level", [(0.5, 0.1, 2, 1), (0.1, 0.5, 2, 4), (0.2, 0.5, 4, 2),
+                                             (0.05, 0.5, 8, 2)])
+def test_coarse_random_numbers_have_the_required_laws(orc, eps, dt0, M, level):
+    """Sec. 5.1 protocol: A^2 of nu~, E~ and chi~ against their laws on
+    N = 1000 draws (the paper's sample size) and on N = 20000."""
+    p = orc.Problem(eps=eps, T=1.0, dt0=dt0, M=M, L=level, seed=4)
+    nu_t, E_t, chi_t, _ = orc.coarse_draws(p, level, 0, 20000, 20000)
+    assert len(nu_t) == 20000
+    norm = stats.norm.cdf
+    expo = stats.expon.cdf
+    for N in (1000, 20000):
+        sel = slice(0, N)
+        assert ad_statistic(nu_t[sel], norm) < AD_CRIT_01PCT
+        assert ad_statistic(E_t[sel], expo) < AD_CRIT_01PCT
+        assert ad_statistic(chi_t[sel], norm) < AD_CRIT_01PCT
+
+
+@pytest.mark.parametrize("eps,dt0,level", [(0.5, 0.1, 1), (0.2, 0.5, 3), (0.05, 0.5, 2)])
+def test_coarse_path_law_matches_single_level(orc, eps, dt0, level):
+    p = orc.Problem(eps=eps, T=1.0, dt0=dt0, M=2, L=level, seed=31)
+    n = 20_000
+    _, xc, _, ec = orc.pairs(p, level, 0, n, threads=8)
+    q = orc.Problem(eps=eps, T=1.0, dt0=dt0, M=2, L=level, seed=977)
+    xs, es = orc.single_paths(q, level - 1, 0, n)
+    assert stats.ks_2samp(xc, xs).pvalue > 1e-3
+    assert stats.anderson_ksamp([xc, xs]).pvalue > 1e-3
+    # same number of coarse events on average as the coarse scheme itself
+    assert abs(ec.mean() - es.mean()) <= 5 * math.sqrt(ec.var() / n + es.var() / n)
+
+
+def test_telescoping_sum(orc):
+    p = orc.Problem(eps=0.3, T=0.5, dt0=0.1, M=2, L=3, seed=17)
+    n = 100_000
+    total, var = 0.0, 0.0
+    for level in range(4):
+        s = orc.run_level(p, level, 0, n, threads=8)
+        total += s.mean()
+        var += s.var() / n
+    q = orc.Problem(eps=0.3, T=0.5, dt0=0.1, M=2, L=3, seed=18)
+    xf, _ = orc.single_paths(q, 3, 0, n)
+    direct = np.mean(xf * xf)
+    var += np.var(xf * xf) / n
+    assert abs(total - direct) < 4.5 * math.sqrt(var)
+
+
+def test_optimal_counts_formula(orc):
+    # J = 1 reduces to N = 2 V / tol^2
+    assert orc.optimal_counts([0.5], [3.0], 0.01) == [10000]
+    # three levels, computed by hand from eqs. Nopt1/Noptj:
+    # sum sqrt(V C) = 1 + 1 + 0.8 = 2.8; N_j = 200 sqrt(V_j/C_j) 2.8
+    assert orc.optimal_counts([1.0, 0.25, 0.04], [1.0, 4.0, 16.0], 0.1) == [560, 140, 28]
+    N = [560, 140, 28]
+    assert sum(v / n for v, n in zip([1.0, 0.25, 0.04], N)) == pytest.approx(0.1 ** 2 / 2)
+
+
+def test_mlmc_estimate_within_tolerance(orc):
+    """Repeated adaptive estimates of E[x(T)^2]: empirical MSE below tol^2
+    (bias is zero for this QoI)."""
+    eps, T = 0.5, 0.5
+    exact = msd(eps, T)
+    tol = 0.02
+    errs = []
+    for seed in range(20):
+        p = orc.Problem(eps=eps, T=T, dt0=0.1, M=2, L=2, tol=tol, seed=1000 + seed)
+        r = orc.estimate(p, threads=8)
+        assert r.variance <= tol * tol / 2 * 1.0000001
+        errs.append(r.estimate - exact)
+    mse = float(np.mean(np.square(errs)))
+    # 20 draws of a variance <= tol^2/2: chi-square bound at the 0.1 % level
+    assert mse < tol * tol / 2 * stats.chi2.ppf(0.999, 20) / 20
+
+
+def test_periodic_qoi_identity(orc):
+    """With x0 ~ 1 + cos(2 pi x) and a symmetric displacement D,
+    E[(x(T) mod 1)^2] = 1/3 + E[cos(2 pi D)]/(2 pi^2)."""
+    p = orc.Problem(eps=0.3, T=0.2, dt0=0.1, M=2, L=1, seed=2, init=orc.INIT_COSINE,
+                    qoi=orc.QOI_X2_PERIODIC)
+    n = 100_000
+    xf, _, _, _ = orc.pairs(p, 0, 0, n, threads=8)
+    L = orc.lib()
+    x0 = np.array([L.orc_cosine_inverse(orc.stream_draws(p, 0, j, 1)[0][2]) for j in range(n)])
+    D = xf - x0
+    lhs = orc.qoi_values(p, xf)
+    rhs = 1.0 / 3.0 + np.cos(2 * np.pi * D) / (2 * np.pi ** 2)
+    diff = lhs - rhs
+    assert abs(diff.mean()) < 4.5 * diff.std() / math.sqrt(n)
+
+
+def test_density_counts_consistent(orc):
+    p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=1, nbins=20, lo=-3.0, hi=3.0, seed=0)
+    xf, xc, ef, ec = orc.pairs(p, 1, 0, 5000)
+    s = orc.level_sums(p, 1, xf, xc, ef, ec)
+    inside_f = np.sum((xf >= -3) & (xf < 3))
+    assert s.hist_f.sum() == inside_f
+    assert np.all(s.hist_both <= np.minimum(s.hist_f, s.hist_c))
+    # sum over pairs of Y_b^2 = f + c - 2 both >= |sum Y_b|
+    assert np.all(s.hist_f + s.hist_c - 2 * s.hist_both >= np.abs(s.hist_f - s.hist_c))
