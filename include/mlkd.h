@@ -1,0 +1,191 @@
+/*
+ * mlkd.h -- C ABI of the GB300 multilevel kinetic-diffusion Monte Carlo
+ * library (ML-KDMC: Mortier, Robbe, Baelmans, Samaey, "Multilevel
+ * asymptotic-preserving Monte Carlo for kinetic-diffusive particle simulations
+ * of the Boltzmann-BGK equation").
+ *
+ * The library simulates, on one GPU, N_l correlated fine/coarse particle
+ * pairs per level l (Alg. 2), each pair driven by its own counter-based Philox
+ * stream, and reduces the level differences Y_l = F(x_l(T)) - F(x_{l-1}(T)) on
+ * the device into the sums that set each level's sample count (Sec. 4.1).
+ *
+ * Problem statement (Sec. 4.1, in the diffusive scaling): the homogeneous BGK
+ * background has collision rate R = 1/eps^2, post-collision velocity
+ * mu + sigma*nu with sigma = 1/eps and nu ~ N(0,1) (Sec. 2, "homogeneous
+ * case"); end time T; level-l step dt_l = dt0 * M^-l; quantity of interest
+ * F(x(T)); RMSE tolerance tol (eq. mse).
+ *
+ * Conventions for every call:
+ *   - Every call returns an mlkd_status; on error the outputs are untouched
+ *     and nothing has been enqueued on the caller's stream.
+ *   - The caller owns every host struct and array, the device arena handed to
+ *     mlkd_context_create, and the CUDA stream (passed as void*, a
+ *     cudaStream_t; NULL = the legacy default stream).  The library performs
+ *     no device allocation after mlkd_context_create returns.
+ *   - Pointers documented as "device" must point to memory of the context's
+ *     device; "host" pointers to ordinary host memory.
+ *   - A context is used by one host thread at a time, except mlkd_submit and
+ *     mlkd_poll, which lock internally.
+ */
+#ifndef MLKD_H
+#define MLKD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MLKD_API __attribute__((visibility("default")))
+#else
+#define MLKD_API
+#endif
+
+#define MLKD_ABI_VERSION 1
+#define MLKD_MAX_LEVELS 16      /* levels 0..15 */
+#define MLKD_MAX_BINS 1024
+
+typedef enum {
+    MLKD_OK = 0,
+    MLKD_EINVAL = -1,      /* invalid problem or argument                      */
+    MLKD_ENOMEM = -2,      /* arena too small for this problem                 */
+    MLKD_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed      */
+    MLKD_ETIMEDOUT = -4,   /* a bounded wait (device or poll) ran out          */
+    MLKD_EBUSY = -5,       /* no free slot or arena room (serving)             */
+    MLKD_ENOTFOUND = -6    /* unknown request id                               */
+} mlkd_status;
+
+/* Quantity of interest F(x(T)).  X2: x^2 in free space.  X2_PERIODIC:
+ * (x mod 1)^2 on the periodic unit interval.  DENSITY: the histogram density
+ * (nbins > 0) sets the sample counts through its largest bin variance; the
+ * scalar F is still reduced (x^2, or (x mod 1)^2 for the cosine start). */
+typedef enum { MLKD_QOI_X2 = 0, MLKD_QOI_X2_PERIODIC = 1, MLKD_QOI_DENSITY = 2 } mlkd_qoi;
+
+/* Initial position: x = 0, or density proportional to 1 + cos(2 pi x) on the
+ * periodic unit interval (inverse CDF of a uniform). */
+typedef enum { MLKD_INIT_ORIGIN = 0, MLKD_INIT_COSINE = 1 } mlkd_init;
+
+/* Arithmetic of the pair state.  FP64: state and sums in FP64 (53-bit
+ * uniforms, two Philox blocks per fine event).  FP32_DY64: FP32 state, 24-bit
+ * uniforms (one Philox block per fine event), Y_l formed and summed in FP64.
+ * FP32_COMP: FP32 state, Y_l formed in FP32 and summed as compensated FP32
+ * (sum, error) pairs.  Level statistics and the estimator are FP64 in every
+ * mode. */
+typedef enum { MLKD_PREC_FP64 = 0, MLKD_PREC_FP32_DY64 = 1, MLKD_PREC_FP32_COMP = 2 } mlkd_prec;
+
+/* The paper's problem statement (Sec. 4.1) in the diffusive scaling.
+ * Validation (MLKD_EINVAL otherwise): eps > 0, T > 0, dt0 > 0, T/dt0 a
+ * positive integer (relative 1e-12), M in 2..64, L in 0..15, the finest level
+ * has at most 2^30 fine steps, nbins in 0..1024 (>0 for DENSITY), lo < hi,
+ * tol > 0 or n_fixed != NULL for mlkd_estimate, n_warmup >= 2. */
+typedef struct {
+    double eps;            /* diffusive scaling: R = 1/eps^2, sigma = 1/eps    */
+    double mu;             /* mean post-collision velocity mu_v (usually 0)    */
+    double T;              /* end time                                         */
+    double dt0;            /* level-0 time step                                */
+    int32_t M;             /* refinement factor dt_{l-1}/dt_l                  */
+    int32_t L;             /* finest level                                     */
+    int32_t qoi;           /* mlkd_qoi                                         */
+    int32_t init;          /* mlkd_init                                        */
+    int32_t nbins;         /* histogram bins (0 = no histogram)                */
+    int32_t precision;     /* mlkd_prec                                        */
+    double lo, hi;         /* histogram range in free space (periodic: [0,1))  */
+    double tol;            /* RMSE tolerance for mlkd_estimate                 */
+    int32_t n_warmup;      /* warm-up pairs per level (the paper uses 100)     */
+    uint32_t request;      /* request id: fourth Philox counter word           */
+    uint64_t seed;         /* Philox key                                       */
+    const int64_t *n_fixed;/* host, length L+1: fixed N_l instead of tol, or NULL */
+} mlkd_problem;
+
+/* Sums over the pairs of one level (eq. mlmc-compact):
+ * n pairs, sum Y, sum Y^2, sum F(x_l), sum F(x_l)^2, sum F(x_{l-1}),
+ * sum F(x_{l-1})^2 (zero on level 0), executed fine and coarse KD events. */
+typedef struct {
+    int64_t n;
+    double sy, sy2, sqf, sqf2, sqc, sqc2;
+    uint64_t events_f, events_c;
+} mlkd_level_stats;
+
+/* Result of an adaptive estimate (eqs. mlmc-compact, mse, Nopt1, Noptj). */
+typedef struct {
+    double estimate;       /* sum_l mean(Y_l)                                  */
+    double variance;       /* sum_l V_l / N_l (statistical error, eq. mse)     */
+    int32_t n_levels;      /* L+1                                              */
+    int32_t rounds;        /* sample-count rounds after the warm-up            */
+    mlkd_level_stats lv[MLKD_MAX_LEVELS];
+    double var_level[MLKD_MAX_LEVELS];   /* V_l used for N_l                   */
+    double cost_level[MLKD_MAX_LEVELS];  /* C_l = KD events per sample          */
+    double *density;       /* host, nbins values or NULL: density estimate     */
+    double seconds;        /* wall time of the call                            */
+} mlkd_result;
+
+typedef struct mlkd_context mlkd_context;
+
+/* Human-readable name of a status code. */
+MLKD_API const char *mlkd_status_string(int status);
+
+/* MLKD_ABI_VERSION of the loaded library. */
+MLKD_API int mlkd_abi_version(void);
+
+/* Bytes of device arena a context needs to run this problem with
+ * mlkd_run_level / mlkd_estimate / mlkd_debug_pairs.  Returns 0 if the
+ * problem is invalid. */
+MLKD_API size_t mlkd_workspace_bytes(const mlkd_problem *problem);
+
+/* Creates a context on CUDA device `device` over a caller-owned device arena
+ * (`arena`, `arena_bytes`, 256-byte aligned).  The arena must stay valid
+ * until mlkd_context_destroy.  The library never frees it. */
+MLKD_API mlkd_status mlkd_context_create(int device, void *arena, size_t arena_bytes, mlkd_context **out);
+
+/* Waits for the context's own work and releases host-side state. */
+MLKD_API void mlkd_context_destroy(mlkd_context *ctx);
+
+/* Simulates pairs [first_pair, first_pair + n_pairs) of level `level`
+ * (Alg. 1 on level 0, Alg. 2 with the Sec. 3 coupling on level >= 1) on
+ * `stream` and returns their sums.  Pair p of level l always uses the Philox
+ * stream keyed by (seed, request, l, p), so any split of a pair range gives
+ * the same pairs.  hist_out (host, 3*nbins counts or NULL) receives per bin
+ * the number of fine positions, coarse positions, and pairs with both in it.
+ * Synchronous: returns after the sums are on the host. */
+MLKD_API mlkd_status mlkd_run_level(mlkd_context *ctx, const mlkd_problem *problem, int level,
+                           uint64_t first_pair, uint64_t n_pairs, void *stream,
+                           mlkd_level_stats *out, uint64_t *hist_out);
+
+/* Adaptive MLMC estimate on levels 0..L (Sec. 4.1): n_warmup pairs per level,
+ * then rounds that raise N_l to the optimal counts of eqs. Nopt1/Noptj with
+ * the statistical budget tol^2/2 (eq. statistical_contraint), using the
+ * device-side FP64 level sums; C_l is the mean number of KD events per
+ * sample.  With problem->n_fixed, runs exactly those N_l.  Synchronous. */
+MLKD_API mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *stream,
+                          mlkd_result *out);
+
+/* Per-pair results of pairs [first_pair, first_pair + n_pairs) of `level`:
+ * device arrays of n_pairs entries for the final fine and coarse positions
+ * (xc = 0 on level 0) and the fine and coarse KD event counts.  Any of the
+ * four may be NULL.  Same launch configuration and arithmetic as
+ * mlkd_run_level.  Synchronous. */
+MLKD_API mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int level,
+                             uint64_t first_pair, uint64_t n_pairs, void *stream, double *xf,
+                             double *xc, int32_t *kf, int32_t *kc);
+
+/* Device time of the pair kernel.  When enabled, the context records a CUDA
+ * event pair on the launching stream around every pair-kernel launch and adds
+ * the elapsed time once a call has synchronised that stream. */
+typedef struct {
+    uint64_t launches;       /* pair-kernel launches timed                      */
+    double pair_kernel_ms;   /* their summed device time                        */
+    uint64_t other_launches; /* finalize / controller / histogram launches      */
+} mlkd_kernel_timing;
+
+/* Turns the pair-kernel timing on (enable != 0) or off. */
+MLKD_API mlkd_status mlkd_context_set_timing(mlkd_context *ctx, int enable);
+
+/* Copies the accumulated timing to *out; reset != 0 zeroes it afterwards. */
+MLKD_API mlkd_status mlkd_context_get_timing(mlkd_context *ctx, mlkd_kernel_timing *out, int reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MLKD_H */

@@ -1,0 +1,249 @@
+"""Python binding of libmlkd (include/mlkd.h): argument marshalling only.
+
+Every step of the correlated-pair path runs in the CUDA library; this module
+builds ctypes structs, hands over device buffers and streams owned by
+PyTorch, and converts the results.  If the library is missing it raises: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libmlkd.so")
+
+MLKD_OK = 0
+MLKD_EINVAL = -1
+MLKD_ENOMEM = -2
+MLKD_ECUDA = -3
+MLKD_ETIMEDOUT = -4
+MLKD_EBUSY = -5
+MLKD_ENOTFOUND = -6
+
+QOI_X2, QOI_X2_PERIODIC, QOI_DENSITY = 0, 1, 2
+INIT_ORIGIN, INIT_COSINE = 0, 1
+PREC_FP64, PREC_FP32_DY64, PREC_FP32_COMP = 0, 1, 2
+MAX_LEVELS = 16
+MAX_BINS = 1024
+
+EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
+            "mlkd_context_create", "mlkd_context_destroy", "mlkd_run_level",
+            "mlkd_estimate", "mlkd_debug_pairs", "mlkd_context_set_timing",
+            "mlkd_context_get_timing"]
+
+
+class MlkdError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s (%d)" % (what, status_string(status), status))
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("mu", ctypes.c_double), ("T", ctypes.c_double),
+                ("dt0", ctypes.c_double), ("M", ctypes.c_int32), ("L", ctypes.c_int32),
+                ("qoi", ctypes.c_int32), ("init", ctypes.c_int32), ("nbins", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("lo", ctypes.c_double), ("hi", ctypes.c_double),
+                ("tol", ctypes.c_double), ("n_warmup", ctypes.c_int32),
+                ("request", ctypes.c_uint32), ("seed", ctypes.c_uint64),
+                ("n_fixed", ctypes.POINTER(ctypes.c_int64))]
+
+
+class LevelStats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("sy", ctypes.c_double), ("sy2", ctypes.c_double),
+                ("sqf", ctypes.c_double), ("sqf2", ctypes.c_double), ("sqc", ctypes.c_double),
+                ("sqc2", ctypes.c_double), ("events_f", ctypes.c_uint64),
+                ("events_c", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class KernelTiming(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint64), ("pair_kernel_ms", ctypes.c_double),
+                ("other_launches", ctypes.c_uint64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("estimate", ctypes.c_double), ("variance", ctypes.c_double),
+                ("n_levels", ctypes.c_int32), ("rounds", ctypes.c_int32),
+                ("lv", LevelStats * MAX_LEVELS), ("var_level", ctypes.c_double * MAX_LEVELS),
+                ("cost_level", ctypes.c_double * MAX_LEVELS),
+                ("density", ctypes.POINTER(ctypes.c_double)), ("seconds", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmlkd.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        vp, u64, i32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int32
+        L.mlkd_status_string.argtypes = [ctypes.c_int]
+        L.mlkd_status_string.restype = ctypes.c_char_p
+        L.mlkd_abi_version.restype = ctypes.c_int
+        L.mlkd_workspace_bytes.argtypes = [P(Problem)]
+        L.mlkd_workspace_bytes.restype = ctypes.c_size_t
+        L.mlkd_context_create.argtypes = [ctypes.c_int, vp, ctypes.c_size_t, P(vp)]
+        L.mlkd_context_create.restype = ctypes.c_int
+        L.mlkd_context_destroy.argtypes = [vp]
+        L.mlkd_context_destroy.restype = None
+        L.mlkd_run_level.argtypes = [vp, P(Problem), ctypes.c_int, u64, u64, vp, P(LevelStats),
+                                     P(ctypes.c_uint64)]
+        L.mlkd_run_level.restype = ctypes.c_int
+        L.mlkd_estimate.argtypes = [vp, P(Problem), vp, P(Result)]
+        L.mlkd_estimate.restype = ctypes.c_int
+        L.mlkd_debug_pairs.argtypes = [vp, P(Problem), ctypes.c_int, u64, u64, vp, vp, vp, vp, vp]
+        L.mlkd_debug_pairs.restype = ctypes.c_int
+        L.mlkd_context_set_timing.argtypes = [vp, ctypes.c_int]
+        L.mlkd_context_set_timing.restype = ctypes.c_int
+        L.mlkd_context_get_timing.argtypes = [vp, P(KernelTiming), ctypes.c_int]
+        L.mlkd_context_get_timing.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return lib().mlkd_status_string(int(status)).decode()
+    except RuntimeError:
+        return "status %d" % status
+
+
+def _check(rc, what):
+    if rc != MLKD_OK:
+        raise MlkdError(rc, what)
+
+
+def make_problem(eps, T, dt0, M=2, L=1, qoi=QOI_X2, init=INIT_ORIGIN, nbins=0, lo=-3.0, hi=3.0,
+                 tol=0.0, n_warmup=100, precision=PREC_FP64, seed=0, request=0, mu=0.0,
+                 n_fixed=None) -> Problem:
+    p = Problem()
+    p.eps, p.mu, p.T, p.dt0 = eps, mu, T, dt0
+    p.M, p.L, p.qoi, p.init, p.nbins, p.precision = M, L, qoi, init, nbins, precision
+    p.lo, p.hi, p.tol, p.n_warmup = lo, hi, tol, n_warmup
+    p.request, p.seed = request & 0xFFFFFFFF, seed & 0xFFFFFFFFFFFFFFFF
+    if n_fixed is not None:
+        arr = (ctypes.c_int64 * len(n_fixed))(*[int(v) for v in n_fixed])
+        p._n_fixed_keep = arr
+        p.n_fixed = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
+    return p
+
+
+def workspace_bytes(problem: Problem) -> int:
+    return int(lib().mlkd_workspace_bytes(ctypes.byref(problem)))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Context:
+    """mlkd_context over a device arena owned by a torch uint8 tensor."""
+
+    def __init__(self, device: int = 0, arena_bytes: int = 0):
+        import torch
+        L = lib()
+        self.device = device
+        need = int(L.mlkd_workspace_bytes(ctypes.byref(make_problem(1.0, 1.0, 1.0))))
+        nbytes = max(int(arena_bytes), need)
+        self.arena = torch.empty(nbytes, dtype=torch.uint8, device="cuda:%d" % device)
+        h = ctypes.c_void_p()
+        _check(L.mlkd_context_create(device, ctypes.c_void_p(self.arena.data_ptr()), nbytes,
+                                     ctypes.byref(h)), "mlkd_context_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().mlkd_context_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- mlkd_context_set_timing / mlkd_context_get_timing ------------------
+    def set_timing(self, enable: bool = True):
+        _check(lib().mlkd_context_set_timing(self.handle, 1 if enable else 0),
+               "mlkd_context_set_timing")
+
+    def get_timing(self, reset: bool = False) -> dict:
+        t = KernelTiming()
+        _check(lib().mlkd_context_get_timing(self.handle, ctypes.byref(t), 1 if reset else 0),
+               "mlkd_context_get_timing")
+        return {"launches": int(t.launches), "pair_kernel_ms": float(t.pair_kernel_ms),
+                "other_launches": int(t.other_launches)}
+
+    # -- mlkd_run_level ----------------------------------------------------
+    def run_level(self, problem: Problem, level: int, first_pair: int, n_pairs: int, stream=None):
+        st = LevelStats()
+        hist = None
+        hp = None
+        if problem.nbins > 0:
+            hist = np.zeros(3 * problem.nbins, np.uint64)
+            hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        _check(lib().mlkd_run_level(self.handle, ctypes.byref(problem), level, first_pair, n_pairs,
+                                    _stream_handle(stream), ctypes.byref(st), hp),
+               "mlkd_run_level")
+        out = st.as_dict()
+        if hist is not None:
+            nb = problem.nbins
+            out["hist_f"], out["hist_c"], out["hist_both"] = hist[:nb], hist[nb:2 * nb], hist[2 * nb:]
+        return out
+
+    # -- mlkd_debug_pairs --------------------------------------------------
+    def debug_pairs(self, problem: Problem, level: int, first_pair: int, n_pairs: int, stream=None):
+        import torch
+        dev = "cuda:%d" % self.device
+        xf = torch.empty(max(n_pairs, 1), dtype=torch.float64, device=dev)
+        xc = torch.empty(max(n_pairs, 1), dtype=torch.float64, device=dev)
+        kf = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=dev)
+        kc = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=dev)
+        vp = ctypes.c_void_p
+        _check(lib().mlkd_debug_pairs(self.handle, ctypes.byref(problem), level, first_pair,
+                                      n_pairs, _stream_handle(stream), vp(xf.data_ptr()),
+                                      vp(xc.data_ptr()), vp(kf.data_ptr()), vp(kc.data_ptr())),
+               "mlkd_debug_pairs")
+        n = n_pairs
+        return (xf[:n].cpu().numpy(), xc[:n].cpu().numpy(), kf[:n].cpu().numpy().astype(np.int64),
+                kc[:n].cpu().numpy().astype(np.int64))
+
+    # -- mlkd_estimate -----------------------------------------------------
+    def estimate(self, problem: Problem, stream=None):
+        r = Result()
+        dens = None
+        if problem.nbins > 0:
+            dens = np.zeros(problem.nbins, np.float64)
+            r.density = dens.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        _check(lib().mlkd_estimate(self.handle, ctypes.byref(problem), _stream_handle(stream),
+                                   ctypes.byref(r)), "mlkd_estimate")
+        n = r.n_levels
+        return EstimateResult(r.estimate, r.variance, r.rounds,
+                              [r.lv[l].as_dict() for l in range(n)],
+                              [r.var_level[l] for l in range(n)],
+                              [r.cost_level[l] for l in range(n)], dens, r.seconds)
+
+
+@dataclass
+class EstimateResult:
+    estimate: float
+    variance: float
+    rounds: int
+    levels: list
+    var_level: list
+    cost_level: list
+    density: np.ndarray
+    seconds: float

@@ -1,0 +1,491 @@
+// mlkd_capi.cu -- the C ABI of include/mlkd.h: problem validation, the
+// context over a caller-owned device arena, and the host side of the
+// per-level run and of the adaptive MLMC estimate (Sec. 4.1).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "mlkd_internal.h"
+#include "../../include/mlkd.h"
+
+using namespace mlkd;
+
+namespace {
+
+constexpr int kMaxBlocks = 4096;                  // grid cap of the pair kernel
+constexpr size_t kAlign = 256;
+constexpr uint32_t kWeylA = 0x9E3779B9u;         // Philox key increments (SC'11)
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Arena layout (offsets in bytes).
+struct Layout {
+    size_t partials, tmp_stats, acc_stats, tmp_hist, acc_hist, control, total;
+};
+
+Layout arena_layout()
+{
+    Layout L;
+    size_t off = 0;
+    L.partials = off;  off = align_up(off + (size_t)kMaxBlocks * kPartialWords * sizeof(double));
+    L.tmp_stats = off; off = align_up(off + sizeof(DevLevelStats));
+    L.acc_stats = off; off = align_up(off + MLKD_MAX_LEVELS * sizeof(DevLevelStats));
+    L.tmp_hist = off;  off = align_up(off + 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
+    L.acc_hist = off;  off = align_up(off + (size_t)MLKD_MAX_LEVELS * 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
+    L.control = off;   off = align_up(off + sizeof(DevControl));
+    L.total = off;
+    return L;
+}
+
+// Derived, validated description of a problem.
+struct Derived {
+    double R, sigma, mu;
+    long long n0;          // T / dt0
+    int mode;
+    bool periodic;
+    double lo, hi, h;
+};
+
+bool validate(const mlkd_problem *p, Derived *d)
+{
+    if (!p) return false;
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return false;
+    if (!(p->T > 0.0) || !(p->dt0 > 0.0) || !std::isfinite(p->T) || !std::isfinite(p->dt0)) return false;
+    if (!std::isfinite(p->mu)) return false;
+    if (p->M < 2 || p->M > 64) return false;
+    if (p->L < 0 || p->L >= MLKD_MAX_LEVELS) return false;
+    if (p->qoi < MLKD_QOI_X2 || p->qoi > MLKD_QOI_DENSITY) return false;
+    if (p->init != MLKD_INIT_ORIGIN && p->init != MLKD_INIT_COSINE) return false;
+    if (p->precision < MLKD_PREC_FP64 || p->precision > MLKD_PREC_FP32_COMP) return false;
+    if (p->nbins < 0 || p->nbins > MLKD_MAX_BINS) return false;
+    if (p->qoi == MLKD_QOI_DENSITY && p->nbins == 0) return false;
+    const double r = p->T / p->dt0;
+    const double n0 = std::nearbyint(r);
+    if (n0 < 1.0 || std::fabs(r - n0) > 1e-12 * std::max(1.0, r)) return false;
+    // finest level: n0 * M^L fine steps; FP32 state needs exact step indices
+    double nmax = n0;
+    for (int l = 0; l < p->L; ++l) nmax *= p->M;
+    const double cap = p->precision == MLKD_PREC_FP64 ? 1073741824.0 : 16777216.0;
+    if (nmax > cap) return false;
+    const double R = 1.0 / (p->eps * p->eps);
+    if (!std::isfinite(R) || R <= 0.0) return false;
+    d->R = R;
+    d->sigma = 1.0 / p->eps;
+    d->mu = p->mu;
+    d->n0 = (long long)n0;
+    d->mode = p->precision;
+    d->periodic = p->qoi == MLKD_QOI_X2_PERIODIC || p->init == MLKD_INIT_COSINE;
+    if (d->periodic) {
+        d->lo = 0.0;
+        d->hi = 1.0;
+    } else {
+        if (p->nbins > 0 && !(p->lo < p->hi && std::isfinite(p->lo) && std::isfinite(p->hi))) return false;
+        d->lo = p->lo;
+        d->hi = p->hi;
+    }
+    d->h = p->nbins > 0 ? (d->hi - d->lo) / p->nbins : 1.0;
+    return true;
+}
+
+long long ipow(long long b, int e)
+{
+    long long r = 1;
+    for (int i = 0; i < e; ++i) r *= b;
+    return r;
+}
+
+}  // namespace
+
+constexpr int kTimingRing = 64;
+
+struct mlkd_context {
+    int device;
+    bool timing;
+    int pending;
+    cudaEvent_t ev_start[kTimingRing], ev_stop[kTimingRing];
+    bool events_made;
+    unsigned long long launches, other_launches;
+    double kernel_ms;
+    int sm_count;
+    char *arena;
+    size_t arena_bytes;
+    Layout L;
+    double *partials;
+    DevLevelStats *tmp_stats, *acc_stats;
+    unsigned long long *tmp_hist, *acc_hist;
+    DevControl *control;
+};
+
+namespace {
+
+#define MLKD_CUDA(call)                                  \
+    do {                                                 \
+        if ((call) != cudaSuccess) return MLKD_ECUDA;    \
+    } while (0)
+
+// Fills the kernel parameters of pairs [first, first+count) of `level`.
+void fill_launch(const mlkd_problem *p, const Derived &d, int level, uint64_t first, uint64_t count,
+                 PairLaunch *P)
+{
+    std::memset(P, 0, sizeof(*P));
+    const long long Ml = ipow(p->M, level);
+    P->R = d.R;
+    P->mu = d.mu;
+    P->sigma = d.sigma;
+    P->dt = p->dt0 / (double)Ml;
+    P->lo = d.lo;
+    P->hi = d.hi;
+    P->h = d.h;
+    P->n = (int32_t)(d.n0 * Ml);
+    P->M = p->M;
+    P->periodic = d.periodic ? 1 : 0;
+    P->init = p->init;
+    P->nbins = p->nbins;
+    P->word2 = (uint32_t)level << 24;
+    P->request = p->request;
+    const uint32_t s0 = (uint32_t)p->seed, s1 = (uint32_t)(p->seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        P->keys.k0[r] = s0 + (uint32_t)r * kWeylA;
+        P->keys.k1[r] = s1 + (uint32_t)r * kWeylB;
+    }
+    P->first_pair = first;
+    P->n_pairs = count;
+}
+
+// Grid of the pair kernel: enough warps for the pairs, at most one full wave
+// of resident blocks; each warp gets an equal contiguous chunk.
+mlkd_status choose_grid(mlkd_context *ctx, int mode, bool coupled, int nbins, uint64_t count,
+                        int *grid, unsigned long long *ppw)
+{
+    KernelInfo info;
+    if (pair_kernel_info(mode, coupled, nbins, &info) != cudaSuccess) return MLKD_ECUDA;
+    const int per_sm = std::max(1, info.blocks_per_sm);
+    const long long wave = std::min<long long>((long long)ctx->sm_count * per_sm, kMaxBlocks);
+    const unsigned long long warps_needed = (count + 31) / 32;
+    const unsigned long long blocks_needed = (warps_needed + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const long long g = (long long)std::min<unsigned long long>(blocks_needed, (unsigned long long)wave);
+    *grid = (int)std::max<long long>(1, g);
+    const unsigned long long warps = (unsigned long long)(*grid) * kWarpsPerBlock;
+    *ppw = (count + warps - 1) / warps;
+    return MLKD_OK;
+}
+
+// Adds the elapsed time of every recorded pair-kernel launch; the stream of
+// those launches has been synchronised by the caller.
+mlkd_status harvest_timing(mlkd_context *ctx)
+{
+    for (int i = 0; i < ctx->pending; ++i) {
+        float ms = 0.0f;
+        MLKD_CUDA(cudaEventElapsedTime(&ms, ctx->ev_start[i], ctx->ev_stop[i]));
+        ctx->kernel_ms += ms;
+        ++ctx->launches;
+    }
+    ctx->pending = 0;
+    return MLKD_OK;
+}
+
+// Enqueues one level run: pair kernel + fixed-order finalize (+ accumulation).
+mlkd_status enqueue_level(mlkd_context *ctx, const mlkd_problem *p, const Derived &d, int level,
+                          uint64_t first, uint64_t count, cudaStream_t stream,
+                          bool accumulate, double *dxf, double *dxc, int32_t *dkf, int32_t *dkc)
+{
+    PairLaunch P;
+    fill_launch(p, d, level, first, count, &P);
+    int grid = 1;
+    unsigned long long ppw = 0;
+    mlkd_status st = choose_grid(ctx, d.mode, level > 0, p->nbins, count, &grid, &ppw);
+    if (st != MLKD_OK) return st;
+    P.pairs_per_warp = ppw;
+    P.partials = ctx->partials;
+    P.hist = p->nbins > 0 ? ctx->tmp_hist : nullptr;
+    P.dbg_xf = dxf;
+    P.dbg_xc = dxc;
+    P.dbg_kf = dkf;
+    P.dbg_kc = dkc;
+    if (p->nbins > 0)
+        MLKD_CUDA(cudaMemsetAsync(ctx->tmp_hist, 0, 3 * (size_t)p->nbins * sizeof(unsigned long long), stream));
+    const bool timed = ctx->timing && ctx->events_made;
+    if (timed && ctx->pending == kTimingRing) {
+        MLKD_CUDA(cudaStreamSynchronize(stream));
+        mlkd_status st2 = harvest_timing(ctx);
+        if (st2 != MLKD_OK) return st2;
+    }
+    if (timed) MLKD_CUDA(cudaEventRecord(ctx->ev_start[ctx->pending], stream));
+    MLKD_CUDA(launch_pair_kernel(d.mode, level > 0, P, grid, stream));
+    if (timed) MLKD_CUDA(cudaEventRecord(ctx->ev_stop[ctx->pending++], stream));
+    MLKD_CUDA(launch_finalize(ctx->partials, grid, (long long)count, ctx->tmp_stats,
+                              accumulate ? ctx->acc_stats + level : nullptr, stream));
+    ++ctx->other_launches;
+    if (accumulate && p->nbins > 0) {
+        MLKD_CUDA(launch_hist_accumulate(ctx->tmp_hist, ctx->acc_hist + (size_t)level * 3 * p->nbins,
+                                         3 * p->nbins, stream));
+        ++ctx->other_launches;
+    }
+    return MLKD_OK;
+}
+
+void to_host_stats(const DevLevelStats &s, mlkd_level_stats *o)
+{
+    o->n = s.n;
+    o->sy = s.sy;
+    o->sy2 = s.sy2;
+    o->sqf = s.sqf;
+    o->sqf2 = s.sqf2;
+    o->sqc = s.sqc;
+    o->sqc2 = s.sqc2;
+    o->events_f = s.events_f;
+    o->events_c = s.events_c;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mlkd_status_string(int status)
+{
+    switch (status) {
+    case MLKD_OK: return "ok";
+    case MLKD_EINVAL: return "invalid argument";
+    case MLKD_ENOMEM: return "arena too small";
+    case MLKD_ECUDA: return "CUDA error";
+    case MLKD_ETIMEDOUT: return "timed out";
+    case MLKD_EBUSY: return "busy";
+    case MLKD_ENOTFOUND: return "not found";
+    default: return "unknown status";
+    }
+}
+
+int mlkd_abi_version(void) { return MLKD_ABI_VERSION; }
+
+size_t mlkd_workspace_bytes(const mlkd_problem *problem)
+{
+    Derived d;
+    if (!validate(problem, &d)) return 0;
+    return arena_layout().total;
+}
+
+mlkd_status mlkd_context_create(int device, void *arena, size_t arena_bytes, mlkd_context **out)
+{
+    if (!out || !arena) return MLKD_EINVAL;
+    if (((uintptr_t)arena) % kAlign != 0) return MLKD_EINVAL;
+    const Layout L = arena_layout();
+    if (arena_bytes < L.total) return MLKD_ENOMEM;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess) return MLKD_ECUDA;
+    if (device < 0 || device >= ndev) return MLKD_EINVAL;
+    MLKD_CUDA(cudaSetDevice(device));
+    int sms = 0;
+    MLKD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    mlkd_context *c = new (std::nothrow) mlkd_context;
+    if (!c) return MLKD_ENOMEM;
+    c->device = device;
+    c->sm_count = sms;
+    c->timing = false;
+    c->pending = 0;
+    c->events_made = false;
+    c->launches = 0;
+    c->other_launches = 0;
+    c->kernel_ms = 0.0;
+    c->arena = (char *)arena;
+    c->arena_bytes = arena_bytes;
+    c->L = L;
+    c->partials = (double *)(c->arena + L.partials);
+    c->tmp_stats = (DevLevelStats *)(c->arena + L.tmp_stats);
+    c->acc_stats = (DevLevelStats *)(c->arena + L.acc_stats);
+    c->tmp_hist = (unsigned long long *)(c->arena + L.tmp_hist);
+    c->acc_hist = (unsigned long long *)(c->arena + L.acc_hist);
+    c->control = (DevControl *)(c->arena + L.control);
+    *out = c;
+    return MLKD_OK;
+}
+
+void mlkd_context_destroy(mlkd_context *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->events_made) {
+        cudaDeviceSynchronize();
+        for (int i = 0; i < kTimingRing; ++i) {
+            cudaEventDestroy(ctx->ev_start[i]);
+            cudaEventDestroy(ctx->ev_stop[i]);
+        }
+    }
+    delete ctx;
+}
+
+mlkd_status mlkd_context_set_timing(mlkd_context *ctx, int enable)
+{
+    if (!ctx) return MLKD_EINVAL;
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+    if (enable && !ctx->events_made) {
+        for (int i = 0; i < kTimingRing; ++i) {
+            MLKD_CUDA(cudaEventCreate(&ctx->ev_start[i]));
+            MLKD_CUDA(cudaEventCreate(&ctx->ev_stop[i]));
+        }
+        ctx->events_made = true;
+    }
+    ctx->timing = enable != 0;
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_context_get_timing(mlkd_context *ctx, mlkd_kernel_timing *out, int reset)
+{
+    if (!ctx || !out) return MLKD_EINVAL;
+    if (ctx->pending) {
+        MLKD_CUDA(cudaDeviceSynchronize());
+        mlkd_status st = harvest_timing(ctx);
+        if (st != MLKD_OK) return st;
+    }
+    out->launches = ctx->launches;
+    out->pair_kernel_ms = ctx->kernel_ms;
+    out->other_launches = ctx->other_launches;
+    if (reset) {
+        ctx->launches = 0;
+        ctx->other_launches = 0;
+        ctx->kernel_ms = 0.0;
+    }
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_run_level(mlkd_context *ctx, const mlkd_problem *problem, int level,
+                           uint64_t first_pair, uint64_t n_pairs, void *stream,
+                           mlkd_level_stats *out, uint64_t *hist_out)
+{
+    Derived d;
+    if (!ctx || !out || !validate(problem, &d)) return MLKD_EINVAL;
+    if (level < 0 || level > problem->L) return MLKD_EINVAL;
+    if (first_pair + n_pairs < first_pair) return MLKD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+    if (n_pairs == 0) {
+        std::memset(out, 0, sizeof(*out));
+        if (hist_out && problem->nbins > 0) std::memset(hist_out, 0, 3 * (size_t)problem->nbins * sizeof(uint64_t));
+        return MLKD_OK;
+    }
+    mlkd_status st = enqueue_level(ctx, problem, d, level, first_pair, n_pairs, s, false,
+                                   nullptr, nullptr, nullptr, nullptr);
+    if (st != MLKD_OK) return st;
+    DevLevelStats hs;
+    MLKD_CUDA(cudaMemcpyAsync(&hs, ctx->tmp_stats, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    if (hist_out && problem->nbins > 0)
+        MLKD_CUDA(cudaMemcpyAsync(hist_out, ctx->tmp_hist, 3 * (size_t)problem->nbins * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToHost, s));
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    to_host_stats(hs, out);
+    return harvest_timing(ctx);
+}
+
+mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int level,
+                             uint64_t first_pair, uint64_t n_pairs, void *stream, double *xf,
+                             double *xc, int32_t *kf, int32_t *kc)
+{
+    Derived d;
+    if (!ctx || !validate(problem, &d)) return MLKD_EINVAL;
+    if (level < 0 || level > problem->L) return MLKD_EINVAL;
+    if (!xf && (xc || kf || kc)) return MLKD_EINVAL;   // xf gates the per-pair writes
+    cudaStream_t s = (cudaStream_t)stream;
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+    if (n_pairs == 0) return MLKD_OK;
+    mlkd_status st = enqueue_level(ctx, problem, d, level, first_pair, n_pairs, s, false, xf, xc,
+                                   kf, kc);
+    if (st != MLKD_OK) return st;
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    return harvest_timing(ctx);
+}
+
+mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *stream,
+                          mlkd_result *out)
+{
+    Derived d;
+    if (!ctx || !out || !validate(problem, &d)) return MLKD_EINVAL;
+    if (!problem->n_fixed && !(problem->tol > 0.0)) return MLKD_EINVAL;
+    if (!problem->n_fixed && problem->n_warmup < 2) return MLKD_EINVAL;
+    const auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = (cudaStream_t)stream;
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+    const int nl = problem->L + 1;
+    const int nb = problem->nbins;
+    MLKD_CUDA(cudaMemsetAsync(ctx->acc_stats, 0, nl * sizeof(DevLevelStats), s));
+    if (nb > 0)
+        MLKD_CUDA(cudaMemsetAsync(ctx->acc_hist, 0, (size_t)nl * 3 * nb * sizeof(unsigned long long), s));
+    long long have[MLKD_MAX_LEVELS] = {0};
+    const int density = problem->qoi == MLKD_QOI_DENSITY ? 1 : 0;
+    DevControl ctl;
+    int rounds = 0;
+
+    auto run = [&](int l, long long target) -> mlkd_status {
+        if (target <= have[l]) return MLKD_OK;
+        mlkd_status st = enqueue_level(ctx, problem, d, l, (uint64_t)have[l],
+                                       (uint64_t)(target - have[l]), s, true, nullptr, nullptr,
+                                       nullptr, nullptr);
+        if (st == MLKD_OK) have[l] = target;
+        return st;
+    };
+    auto control = [&]() -> mlkd_status {
+        MLKD_CUDA(launch_controller(ctx->acc_stats, ctx->acc_hist, nl, nb, d.h, density,
+                                    problem->tol, ctx->control, s));
+        ++ctx->other_launches;
+        MLKD_CUDA(cudaMemcpyAsync(&ctl, ctx->control, sizeof(ctl), cudaMemcpyDeviceToHost, s));
+        MLKD_CUDA(cudaStreamSynchronize(s));
+        return harvest_timing(ctx);
+    };
+
+    mlkd_status st;
+    if (problem->n_fixed) {
+        for (int l = 0; l < nl; ++l) {
+            if (problem->n_fixed[l] < 0) return MLKD_EINVAL;
+            if ((st = run(l, problem->n_fixed[l])) != MLKD_OK) return st;
+        }
+        if ((st = control()) != MLKD_OK) return st;
+    } else {
+        for (int l = 0; l < nl; ++l)
+            if ((st = run(l, problem->n_warmup)) != MLKD_OK) return st;
+        for (;;) {
+            if ((st = control()) != MLKD_OK) return st;
+            bool grew = false;
+            for (int l = 0; l < nl; ++l) {
+                if (ctl.target[l] > have[l]) {
+                    if ((st = run(l, ctl.target[l])) != MLKD_OK) return st;
+                    grew = true;
+                }
+            }
+            if (!grew) break;
+            if (++rounds > 64) break;
+        }
+    }
+    DevLevelStats acc[MLKD_MAX_LEVELS];
+    MLKD_CUDA(cudaMemcpyAsync(acc, ctx->acc_stats, nl * sizeof(DevLevelStats), cudaMemcpyDeviceToHost, s));
+    unsigned long long hacc[3 * MLKD_MAX_BINS];
+    double *dens = out->density;
+    std::memset(out, 0, sizeof(*out));
+    out->density = dens;
+    if (dens && nb > 0) {
+        for (int i = 0; i < nb; ++i) dens[i] = 0.0;
+        MLKD_CUDA(cudaStreamSynchronize(s));
+        for (int l = 0; l < nl; ++l) {
+            MLKD_CUDA(cudaMemcpy(hacc, ctx->acc_hist + (size_t)l * 3 * nb, 3 * (size_t)nb * sizeof(unsigned long long),
+                                 cudaMemcpyDeviceToHost));
+            if (acc[l].n > 0)
+                for (int b = 0; b < nb; ++b)
+                    dens[b] += ((double)hacc[b] - (double)hacc[nb + b]) / (double)acc[l].n;
+        }
+        for (int b = 0; b < nb; ++b) dens[b] /= d.h;
+    }
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    out->estimate = ctl.estimate;
+    out->variance = ctl.variance;
+    out->n_levels = nl;
+    out->rounds = rounds;
+    for (int l = 0; l < nl; ++l) {
+        to_host_stats(acc[l], &out->lv[l]);
+        out->var_level[l] = ctl.var_level[l];
+        out->cost_level[l] = ctl.cost_level[l];
+    }
+    out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return harvest_timing(ctx);
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// mlkd_device.cuh -- device primitives of the correlated-pair path.
+//
+//   * Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) with the ten round
+//     keys precomputed on the host and read from the kernel's parameter bank.
+//   * uniform -> N(0,1) by Box-Muller and -> Exp(1) by -log u (the paper's
+//     draw sets of Alg. 1 and Alg. 2: nu_{k+1}, E_{k+1}, chi_k per fine event).
+//   * homogeneous KD coefficients a, d of eqs. advection/diffusion (Sec. 2)
+//     and the dimensionless aggregation weights of Sec. 3.2.
+//   * inverse CDF of the density 1 + cos(2 pi x) on [0, 1).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mlkd {
+
+constexpr uint32_t kPhiloxMulA = 0xD2511F53u;
+constexpr uint32_t kPhiloxMulB = 0xCD9E8D57u;
+
+struct PhiloxKeys {
+    uint32_t k0[10];   // key word 0 for rounds 0..9 (key + r * Weyl constant)
+    uint32_t k1[10];
+};
+
+// One Philox4x32-10 block.  Each round multiplies counter words 0 and 2 by the
+// two published multipliers (32x32 -> 64 bits), permutes and xors the high
+// halves with the other words and the round key.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &rk)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi_a = __umulhi(kPhiloxMulA, c.x);
+        const uint32_t lo_a = kPhiloxMulA * c.x;
+        const uint32_t hi_b = __umulhi(kPhiloxMulB, c.z);
+        const uint32_t lo_b = kPhiloxMulB * c.z;
+        c = make_uint4(hi_b ^ c.y ^ rk.k0[r], lo_b, hi_a ^ c.w ^ rk.k1[r], lo_a);
+    }
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Arithmetic of one precision.
+// ---------------------------------------------------------------------------
+template <typename Real> struct Arith;
+
+template <> struct Arith<float> {
+    static __device__ __forceinline__ float log_(float x) { return logf(x); }
+    static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
+    static __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
+    static __device__ __forceinline__ float sinpi_(float x) { return sinpif(x); }
+    static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
+
+    // (f(s)/s^3, g(s)/s^3, h(s)/s^2) for 0 <= s < 1 from their Taylor series:
+    //   f(s) = 2(e^{-s}-1) + s(e^{-s}+1) = sum_{n>=3} (-1)^n (2-n)     s^n/n!
+    //   g(s) = 1 - 2 s e^{-s} - e^{-2s}   = sum_{n>=3} (-1)^n (2n-2^n) s^n/n!
+    //   h(s) = e^{-s} + s - 1             = sum_{n>=2} (-1)^n          s^n/n!
+    // truncated where the next term is below 2^-24 of the leading one at s = 1.
+    static __device__ __forceinline__ float f_series(float s)
+    {
+        float p = 1.76649482e-09f;
+        p = fmaf(p, s, -2.0876757e-08f);  p = fmaf(p, s, 2.25468975e-07f);
+        p = fmaf(p, s, -2.20458554e-06f); p = fmaf(p, s, 1.92901235e-05f);
+        p = fmaf(p, s, -0.000148809524f); p = fmaf(p, s, 0.000992063492f);
+        p = fmaf(p, s, -0.00555555556f);  p = fmaf(p, s, 0.025f);
+        p = fmaf(p, s, -0.0833333333f);   p = fmaf(p, s, 0.166666667f);
+        return p;
+    }
+    static __device__ __forceinline__ float g_series(float s)
+    {
+        float p = 2.50352846e-08f;
+        p = fmaf(p, s, -1.87615515e-07f); p = fmaf(p, s, 1.31138152e-06f);
+        p = fmaf(p, s, -8.50101545e-06f); p = fmaf(p, s, 5.07555716e-05f);
+        p = fmaf(p, s, -0.000276675485f); p = fmaf(p, s, 0.00136133157f);
+        p = fmaf(p, s, -0.00595238095f);  p = fmaf(p, s, 0.0226190476f);
+        p = fmaf(p, s, -0.0722222222f);   p = fmaf(p, s, 0.183333333f);
+        p = fmaf(p, s, -0.333333333f);    p = fmaf(p, s, 0.333333333f);
+        return p;
+    }
+    static __device__ __forceinline__ float h_series(float s)
+    {
+        float p = -2.50521084e-08f;
+        p = fmaf(p, s, 2.75573192e-07f);  p = fmaf(p, s, -2.75573192e-06f);
+        p = fmaf(p, s, 2.48015873e-05f);  p = fmaf(p, s, -0.000198412698f);
+        p = fmaf(p, s, 0.00138888889f);   p = fmaf(p, s, -0.00833333333f);
+        p = fmaf(p, s, 0.0416666667f);    p = fmaf(p, s, -0.166666667f);
+        p = fmaf(p, s, 0.5f);
+        return p;
+    }
+    // z - sin z = z^3 S(z^2) with S = sum_{n>=1} (-1)^{n+1} z^{2n-2}/(2n+1)!,
+    // used for |z| <= pi/4.
+    static __device__ __forceinline__ float zms_series(float z2)
+    {
+        float p = -1.60590438e-10f;
+        p = fmaf(p, z2, 2.50521084e-08f);  p = fmaf(p, z2, -2.75573192e-06f);
+        p = fmaf(p, z2, 0.000198412698f);  p = fmaf(p, z2, -0.00833333333f);
+        p = fmaf(p, z2, 0.166666667f);
+        return p;
+    }
+    static constexpr int kNewtonIters = 5;
+};
+
+template <> struct Arith<double> {
+    static __device__ __forceinline__ double log_(double x) { return log(x); }
+    static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
+    static __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
+    static __device__ __forceinline__ double sinpi_(double x) { return sinpi(x); }
+    static __device__ __forceinline__ double floor_(double x) { return floor(x); }
+
+    // Same series as the float version, truncated below 2^-53 of the leading
+    // term at s = 1.
+    static __device__ __forceinline__ double f_series(double s)
+    {
+        double p = -7.398571721961897e-18;
+        p = fma(p, s, 1.3975079919261362e-16);  p = fma(p, s, -2.499073114973796e-15);
+        p = fma(p, s, 4.2171858815182813e-14);  p = fma(p, s, -6.6912682653423392e-13);
+        p = fma(p, s, 9.941312851365761e-12);   p = fma(p, s, -1.376489471727567e-10);
+        p = fma(p, s, 1.7664948220503776e-09);  p = fma(p, s, -2.08767569878681e-08);
+        p = fma(p, s, 2.2546897546897547e-07);  p = fma(p, s, -2.2045855379188711e-06);
+        p = fma(p, s, 1.9290123456790123e-05);  p = fma(p, s, -0.00014880952380952382);
+        p = fma(p, s, 0.00099206349206349201);  p = fma(p, s, -0.0055555555555555558);
+        p = fma(p, s, 0.025000000000000001);    p = fma(p, s, -0.083333333333333329);
+        p = fma(p, s, 0.16666666666666666);
+        return p;
+    }
+    static __device__ __forceinline__ double g_series(double s)
+    {
+        double p = 2.1632343257724527e-18;
+        p = fma(p, s, -2.7040392002191521e-17); p = fma(p, s, 3.2448385302886073e-16);
+        p = fma(p, s, -3.7315456265699741e-15); p = fma(p, s, 4.1046610433448451e-14);
+        p = fma(p, s, -4.3098159994772441e-13); p = fma(p, s, 4.3096680280428047e-12);
+        p = fma(p, s, -4.0939191001221986e-11); p = fma(p, s, 3.6840773569492835e-10);
+        p = fma(p, s, -3.1307488318070328e-09); p = fma(p, s, 2.5035284625231715e-08);
+        p = fma(p, s, -1.8761551499646739e-07); p = fma(p, s, 1.3113815197148531e-06);
+        p = fma(p, s, -8.5010154454598902e-06); p = fma(p, s, 5.0755571588904921e-05);
+        p = fma(p, s, -0.00027667548500881836); p = fma(p, s, 0.0013613315696649031);
+        p = fma(p, s, -0.0059523809523809521);  p = fma(p, s, 0.022619047619047618);
+        p = fma(p, s, -0.072222222222222215);   p = fma(p, s, 0.18333333333333332);
+        p = fma(p, s, -0.33333333333333331);    p = fma(p, s, 0.33333333333333331);
+        return p;
+    }
+    static __device__ __forceinline__ double h_series(double s)
+    {
+        double p = -8.2206352466243295e-18;
+        p = fma(p, s, 1.5619206968586225e-16);  p = fma(p, s, -2.8114572543455206e-15);
+        p = fma(p, s, 4.7794773323873853e-14);  p = fma(p, s, -7.6471637318198164e-13);
+        p = fma(p, s, 1.1470745597729725e-11);  p = fma(p, s, -1.6059043836821613e-10);
+        p = fma(p, s, 2.08767569878681e-09);    p = fma(p, s, -2.505210838544172e-08);
+        p = fma(p, s, 2.7557319223985888e-07);  p = fma(p, s, -2.7557319223985893e-06);
+        p = fma(p, s, 2.4801587301587302e-05);  p = fma(p, s, -0.00019841269841269841);
+        p = fma(p, s, 0.0013888888888888889);   p = fma(p, s, -0.0083333333333333332);
+        p = fma(p, s, 0.041666666666666664);    p = fma(p, s, -0.16666666666666666);
+        p = fma(p, s, 0.5);
+        return p;
+    }
+    static __device__ __forceinline__ double zms_series(double z2)
+    {
+        double p = 8.2206352466243295e-18;
+        p = fma(p, z2, -2.8114572543455206e-15); p = fma(p, z2, 7.6471637318198164e-13);
+        p = fma(p, z2, -1.6059043836821613e-10); p = fma(p, z2, 2.505210838544172e-08);
+        p = fma(p, z2, -2.7557319223985893e-06); p = fma(p, z2, 0.00019841269841269841);
+        p = fma(p, z2, -0.0083333333333333332);  p = fma(p, z2, 0.16666666666666666);
+        return p;
+    }
+    static constexpr int kNewtonIters = 7;
+};
+
+// ---------------------------------------------------------------------------
+// Draws of one fine event: nu_{k+1}, E_{k+1}, chi_k.
+//   float : one Philox block; u = ((w >> 8) + 1) 2^-24 in (0, 1].
+//   double: two Philox blocks (tag 0 and 1 in counter word 2);
+//           u = (((w_a << 21) ^ (w_b >> 11)) + 1) 2^-53 in (0, 1].
+// The init block (k = 0) gives nu_0 (cosine half of Box-Muller), E_0 and the
+// uniform of the initial position.
+// ---------------------------------------------------------------------------
+template <typename Real> struct Draw { Real nu, E, chi, u4; };
+
+__device__ __forceinline__ float unit24(uint32_t w)
+{
+    return __uint2float_rn((w >> 8) + 1u) * 0x1p-24f;
+}
+
+__device__ __forceinline__ double unit53(uint32_t wa, uint32_t wb)
+{
+    const unsigned long long m = ((unsigned long long)wa << 21) ^ (unsigned long long)(wb >> 11);
+    return __ull2double_rn(m + 1ull) * 0x1p-53;
+}
+
+template <typename Real>
+__device__ __forceinline__ Draw<Real> draw(uint32_t k, uint32_t pair_lo, uint32_t word2,
+                                           uint32_t request, const PhiloxKeys &rk);
+
+template <>
+__device__ __forceinline__ Draw<float> draw<float>(uint32_t k, uint32_t pair_lo, uint32_t word2,
+                                                   uint32_t request, const PhiloxKeys &rk)
+{
+    const uint4 w = philox4x32_10(make_uint4(k, pair_lo, word2, request), rk);
+    const float u1 = unit24(w.x), u2 = unit24(w.y), u3 = unit24(w.z);
+    const float r = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    Draw<float> d;
+    d.nu = r * c;
+    d.chi = r * s;
+    d.E = -logf(u3);
+    d.u4 = unit24(w.w);
+    return d;
+}
+
+template <>
+__device__ __forceinline__ Draw<double> draw<double>(uint32_t k, uint32_t pair_lo, uint32_t word2,
+                                                     uint32_t request, const PhiloxKeys &rk)
+{
+    const uint4 a = philox4x32_10(make_uint4(k, pair_lo, word2, request), rk);
+    const uint4 b = philox4x32_10(make_uint4(k, pair_lo, word2 ^ (1u << 16), request), rk);
+    const double u1 = unit53(a.x, a.y), u2 = unit53(a.z, a.w), u3 = unit53(b.x, b.y);
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    Draw<double> d;
+    d.nu = r * c;
+    d.chi = r * s;
+    d.E = -log(u3);
+    d.u4 = unit53(b.z, b.w);
+    return d;
+}
+
+// ---------------------------------------------------------------------------
+// Homogeneous background in the working precision.
+// ---------------------------------------------------------------------------
+template <typename Real> struct Background {
+    Real R, invR, mu, sigma;
+    Real two_c2;   // 2 sigma^2 / R^2
+    Real dt;       // fine step
+    Real Rdt;      // R dt
+    Real inv_Rdt;  // 1/(R dt): flight in fine steps per unit of E
+
+    // KD increment of the diffusive phase of length theta with final velocity
+    // offset dv = v' - mu (eqs. advection, diffusion):
+    //   a = mu theta + dv (1 - e^{-s})/R,
+    //   d = sqrt(2 sigma^2/R^2 f(s) + dv^2/R^2 g(s)),  s = R theta.
+    // Also returns s and om = 1 - e^{-s} for the aggregation weights.
+    __device__ __forceinline__ void kd_coeffs(Real theta, Real dv, Real &a, Real &d, Real &s,
+                                              Real &om) const
+    {
+        typedef Arith<Real> A;
+        s = R * theta;
+        const Real em = A::expm1_(-s);
+        om = -em;
+        Real f, g;
+        if (s < Real(1)) {
+            const Real s3 = s * s * s;
+            f = s3 * A::f_series(s);
+            g = s3 * A::g_series(s);
+        } else {
+            const Real e = Real(1) + em;
+            f = Real(2) * em + s * (e + Real(1));
+            g = Real(1) - Real(2) * s * e - e * e;
+        }
+        a = mu * theta + dv * om * invR;
+        const Real dvR = dv * invR;
+        Real d2 = two_c2 * f + dvR * dvR * g;
+        d = d2 > Real(0) ? A::sqrt_(d2) : Real(0);
+    }
+
+    // Dimensionless beta weight (Sec. 3.2, eq. weights-beta) of a diffusive
+    // phase with s = R theta and om = 1 - e^{-s}:
+    //   theta' = theta - zeta, zeta = om/R, so s' = R theta' = h(s), and
+    //   beta = (sigma/R) sqrt(2 h(s')).  Returns beta R / sigma squared.
+    __device__ __forceinline__ Real beta_hat_sq(Real s, Real om) const
+    {
+        typedef Arith<Real> A;
+        const Real sp = (s < Real(1)) ? s * s * A::h_series(s) : s - om;
+        const Real hp = (sp < Real(1)) ? sp * sp * A::h_series(sp) : A::expm1_(-sp) + sp;
+        return Real(2) * hp;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Initial position with density 1 + cos(2 pi x) on [0, 1): solve
+// G(y) = y - sin(2 pi y)/(2 pi) = u - 1/2 for y in [-1/2, 1/2] by Newton from
+// the small-|y| inverse y0 = cbrt(6 g/(2 pi)^2), with G' = 2 sin^2(pi y);
+// x = y + 1/2 wrapped into [0, 1).
+// ---------------------------------------------------------------------------
+template <typename Real> __device__ __forceinline__ Real cosine_G(Real y)
+{
+    typedef Arith<Real> A;
+    const Real two_pi = Real(6.283185307179586476925286766559);
+    if (y < Real(-0.125) || y > Real(0.125)) return y - A::sinpi_(Real(2) * y) / two_pi;
+    const Real z = two_pi * y;
+    const Real z2 = z * z;
+    return z2 * z * A::zms_series(z2) / two_pi;
+}
+
+template <typename Real> __device__ __forceinline__ Real cosine_inverse(Real u)
+{
+    typedef Arith<Real> A;
+    const Real two_pi_sq_over6 = Real(6.5797362673929057);   // (2 pi)^2 / 6
+    const Real g = u - Real(0.5);
+    Real y = A::cbrt_(g / two_pi_sq_over6);
+    y = fmin(fmax(y, Real(-0.5)), Real(0.5));
+#pragma unroll 1
+    for (int it = 0; it < A::kNewtonIters; ++it) {
+        const Real sp = A::sinpi_(y);
+        const Real gp = Real(2) * sp * sp;
+        if (!(gp > Real(0))) break;
+        y = y - (cosine_G(y) - g) / gp;
+        y = fmin(fmax(y, Real(-0.5)), Real(0.5));
+    }
+    Real x = y + Real(0.5);
+    if (x >= Real(1)) x -= Real(1);
+    return x;
+}
+
+}  // namespace mlkd

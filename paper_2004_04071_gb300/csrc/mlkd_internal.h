@@ -1,0 +1,79 @@
+// mlkd_internal.h -- shared between the kernel and host translation units of
+// the library (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mlkd_device.cuh"
+
+namespace mlkd {
+
+constexpr int kThreads = 128;          // threads per block of the pair kernel
+constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kPartialWords = 8;       // sy, sy2, sqf, sqf2, sqc, sqc2, ev_f, ev_c
+
+enum Mode { kModeFP64 = 0, kModeFP32DY64 = 1, kModeFP32Comp = 2 };
+
+// Device copy of one level's sums; same layout as mlkd_level_stats.
+struct DevLevelStats {
+    long long n;
+    double sy, sy2, sqf, sqf2, sqc, sqc2;
+    unsigned long long events_f, events_c;
+};
+
+// Parameters of one pair-kernel launch (passed by value as __grid_constant__).
+struct PairLaunch {
+    double R, mu, sigma, dt;   // background and fine step of this level
+    double lo, hi, h;          // histogram range [lo, hi) and bin width
+    int32_t n;                 // fine steps to T
+    int32_t M;                 // refinement factor
+    int32_t periodic;          // F = (x mod 1)^2 and wrapped bins
+    int32_t init;              // 0: x0 = 0; 1: cosine density
+    int32_t nbins;             // 0: no histogram
+    uint32_t word2;            // level << 24 (pair_hi xor'ed in per pair)
+    uint32_t request;
+    uint32_t pad_;
+    PhiloxKeys keys;
+    unsigned long long first_pair, n_pairs, pairs_per_warp;
+    double *partials;                  // [gridDim.x][kPartialWords]
+    unsigned long long *hist;          // [3][nbins] fine, coarse, both; or null
+    double *dbg_xf, *dbg_xc;           // optional per-pair outputs
+    int32_t *dbg_kf, *dbg_kc;
+};
+
+struct KernelInfo {
+    int blocks_per_sm;
+};
+
+// Kernel-variant occupancy (blocks per SM with kThreads threads).
+cudaError_t pair_kernel_info(int mode, bool coupled, int nbins, KernelInfo *out);
+
+// Launches the pair kernel on `grid` blocks.
+cudaError_t launch_pair_kernel(int mode, bool coupled, const PairLaunch &p, int grid,
+                               cudaStream_t stream);
+
+// Sums `nblocks` partial rows in a fixed order into *out (n = n_pairs).  If
+// acc != null also adds them to *acc.
+cudaError_t launch_finalize(const double *partials, int nblocks, long long n_pairs,
+                            DevLevelStats *out, DevLevelStats *acc, cudaStream_t stream);
+
+// Output of the on-device sample-count controller (eqs. Nopt1/Noptj).
+struct DevControl {
+    double estimate, variance;
+    double var_level[16];
+    double cost_level[16];
+    long long target[16];
+};
+
+// From the accumulated level sums (and histograms, for a density QoI),
+// computes V_l, C_l, N_l*, the estimate and its variance in FP64.
+cudaError_t launch_controller(const DevLevelStats *acc, const unsigned long long *hist_acc,
+                              int n_levels, int nbins, double h, int density_qoi, double tol,
+                              DevControl *out, cudaStream_t stream);
+
+// Adds hist [3*nbins] into acc [3*nbins] (integer).
+cudaError_t launch_hist_accumulate(const unsigned long long *hist, unsigned long long *acc,
+                                   int count, cudaStream_t stream);
+
+}  // namespace mlkd
