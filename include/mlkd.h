@@ -185,6 +185,34 @@ MLKD_API mlkd_status mlkd_context_set_timing(mlkd_context *ctx, int enable);
 /* Copies the accumulated timing to *out; reset != 0 zeroes it afterwards. */
 MLKD_API mlkd_status mlkd_context_get_timing(mlkd_context *ctx, mlkd_kernel_timing *out, int reset);
 
+/* Allocation-free variant of mlkd_run_level.  The paper has no counterpart:
+ * this entry point serves callers that may not allocate device memory at
+ * all -- code running inside a host application whose own allocator must own
+ * every device byte (a caching pool or a fixed device-memory budget), plugins
+ * whose host forbids cudaMalloc, and code paths where an allocation could
+ * block or fail at the wrong moment.  It needs no context and no arena.
+ *
+ * Scratch: the block partial sums, the level sums and the histogram counters
+ * live in one file-scope device array inside the library of
+ * MLKD_NOALLOC_SCRATCH_BYTES (137 472 bytes), which every GPU that loads the
+ * library holds until the process exits.  The first call on a device (with
+ * that device current) looks up the array's device address; make this first
+ * call before any stream capture on that device.
+ *
+ * Limits: nbins <= MLKD_NOALLOC_MAX_BINS, else MLKD_ENOMEM; the grid is
+ * capped at MLKD_NOALLOC_MAX_BLOCKS blocks (any n_pairs is accepted).
+ * All calls share the one array and each call overwrites it: calls whose GPU
+ * work overlaps (different streams or host threads) race on it and return
+ * wrong sums, so serialise them.  Problem validation, pair streams, outputs
+ * and synchronisation are as for mlkd_run_level; the call uses the current
+ * CUDA device and calls no device allocator. */
+#define MLKD_NOALLOC_MAX_BLOCKS 2048
+#define MLKD_NOALLOC_MAX_BINS 256
+#define MLKD_NOALLOC_SCRATCH_BYTES (MLKD_NOALLOC_MAX_BLOCKS * 64 + 256 + 3 * MLKD_NOALLOC_MAX_BINS * 8)
+MLKD_API mlkd_status mlkd_run_level_noalloc(const mlkd_problem *problem, int level,
+                                            uint64_t first_pair, uint64_t n_pairs, void *stream,
+                                            mlkd_level_stats *out, uint64_t *hist_out);
+
 #ifdef __cplusplus
 }
 #endif

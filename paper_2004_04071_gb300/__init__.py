@@ -33,7 +33,8 @@ MAX_BINS = 1024
 EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_context_create", "mlkd_context_destroy", "mlkd_run_level",
             "mlkd_estimate", "mlkd_debug_pairs", "mlkd_context_set_timing",
-            "mlkd_context_get_timing"]
+            "mlkd_context_get_timing", "mlkd_run_level_noalloc"]
+NOALLOC_MAX_BINS = 256
 
 
 class MlkdError(RuntimeError):
@@ -107,6 +108,9 @@ def lib():
         L.mlkd_context_set_timing.restype = ctypes.c_int
         L.mlkd_context_get_timing.argtypes = [vp, P(KernelTiming), ctypes.c_int]
         L.mlkd_context_get_timing.restype = ctypes.c_int
+        L.mlkd_run_level_noalloc.argtypes = [P(Problem), ctypes.c_int, u64, u64, vp, P(LevelStats),
+                                             P(ctypes.c_uint64)]
+        L.mlkd_run_level_noalloc.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -235,6 +239,26 @@ class Context:
                               [r.lv[l].as_dict() for l in range(n)],
                               [r.var_level[l] for l in range(n)],
                               [r.cost_level[l] for l in range(n)], dens, r.seconds)
+
+
+def run_level_noalloc(problem: Problem, level: int, first_pair: int, n_pairs: int, stream=None):
+    """mlkd_run_level_noalloc: level sums without a context or arena, for
+    callers that cannot allocate device memory (scratch lives in a static
+    device array inside the library; overlapping calls race)."""
+    st = LevelStats()
+    hist = None
+    hp = None
+    if problem.nbins > 0:
+        hist = np.zeros(3 * problem.nbins, np.uint64)
+        hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    _check(lib().mlkd_run_level_noalloc(ctypes.byref(problem), level, first_pair, n_pairs,
+                                        _stream_handle(stream), ctypes.byref(st), hp),
+           "mlkd_run_level_noalloc")
+    out = st.as_dict()
+    if hist is not None:
+        nb = problem.nbins
+        out["hist_f"], out["hist_c"], out["hist_both"] = hist[:nb], hist[nb:2 * nb], hist[2 * nb:]
+    return out
 
 
 @dataclass

@@ -5,6 +5,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "mlkd_internal.h"
@@ -489,3 +490,95 @@ mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point: the same pair kernel and finalize, with their
+// scratch in a file-scope device array instead of a caller arena.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoAllocStatsOffset = (size_t)MLKD_NOALLOC_MAX_BLOCKS * kPartialWords * sizeof(double);
+constexpr size_t kNoAllocHistOffset = kNoAllocStatsOffset + 256;
+constexpr size_t kNoAllocBytes = kNoAllocHistOffset + 3 * (size_t)MLKD_NOALLOC_MAX_BINS * sizeof(unsigned long long);
+static_assert(kNoAllocBytes == (size_t)MLKD_NOALLOC_SCRATCH_BYTES, "scratch size mismatch");
+static_assert(sizeof(DevLevelStats) <= 256, "level stats exceed their scratch slot");
+
+}  // namespace
+
+// Shared by every call on a device; see the header for the race rule.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_device_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `device` (the current device),
+// looked up once per device.
+mlkd_status noalloc_scratch(int device, unsigned char **out)
+{
+    if (device < 0 || device >= kNoAllocMaxDevices) return MLKD_EINVAL;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_device_ptr[device]) {
+        void *ptr = nullptr;
+        if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return MLKD_ECUDA;
+        g_noalloc_device_ptr[device] = ptr;
+    }
+    *out = (unsigned char *)g_noalloc_device_ptr[device];
+    return MLKD_OK;
+}
+
+}  // namespace
+
+extern "C" mlkd_status mlkd_run_level_noalloc(const mlkd_problem *problem, int level,
+                                              uint64_t first_pair, uint64_t n_pairs, void *stream,
+                                              mlkd_level_stats *out, uint64_t *hist_out)
+{
+    Derived d;
+    if (!out || !validate(problem, &d)) return MLKD_EINVAL;
+    if (level < 0 || level > problem->L) return MLKD_EINVAL;
+    if (first_pair + n_pairs < first_pair) return MLKD_EINVAL;
+    if (problem->nbins > MLKD_NOALLOC_MAX_BINS) return MLKD_ENOMEM;
+    int device = 0;
+    MLKD_CUDA(cudaGetDevice(&device));
+    unsigned char *scratch = nullptr;
+    mlkd_status st = noalloc_scratch(device, &scratch);
+    if (st != MLKD_OK) return st;
+    if (n_pairs == 0) {
+        std::memset(out, 0, sizeof(*out));
+        if (hist_out && problem->nbins > 0) std::memset(hist_out, 0, 3 * (size_t)problem->nbins * sizeof(uint64_t));
+        return MLKD_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int sms = 0;
+    MLKD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    KernelInfo info;
+    MLKD_CUDA(pair_kernel_info(d.mode, level > 0, problem->nbins, &info));
+    const long long wave = std::min<long long>((long long)sms * std::max(1, info.blocks_per_sm),
+                                               MLKD_NOALLOC_MAX_BLOCKS);
+    const unsigned long long warps_needed = (n_pairs + 31) / 32;
+    const unsigned long long blocks_needed = (warps_needed + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    const int grid = (int)std::max<long long>(
+        1, (long long)std::min<unsigned long long>(blocks_needed, (unsigned long long)wave));
+    const unsigned long long warps = (unsigned long long)grid * kWarpsPerBlock;
+
+    PairLaunch P;
+    fill_launch(problem, d, level, first_pair, n_pairs, &P);
+    P.pairs_per_warp = (n_pairs + warps - 1) / warps;
+    P.partials = (double *)scratch;
+    P.hist = problem->nbins > 0 ? (unsigned long long *)(scratch + kNoAllocHistOffset) : nullptr;
+    DevLevelStats *dstats = (DevLevelStats *)(scratch + kNoAllocStatsOffset);
+    if (problem->nbins > 0)   // counters keep the previous call's values
+        MLKD_CUDA(cudaMemsetAsync(P.hist, 0, 3 * (size_t)problem->nbins * sizeof(unsigned long long), s));
+    MLKD_CUDA(launch_pair_kernel(d.mode, level > 0, P, grid, s));
+    MLKD_CUDA(launch_finalize(P.partials, grid, (long long)n_pairs, dstats, nullptr, s));
+    DevLevelStats hs;
+    MLKD_CUDA(cudaMemcpyAsync(&hs, dstats, sizeof(hs), cudaMemcpyDeviceToHost, s));
+    if (hist_out && problem->nbins > 0)
+        MLKD_CUDA(cudaMemcpyAsync(hist_out, P.hist, 3 * (size_t)problem->nbins * sizeof(uint64_t),
+                                  cudaMemcpyDeviceToHost, s));
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    to_host_stats(hs, out);
+    return MLKD_OK;
+}
