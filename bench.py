@@ -50,7 +50,7 @@ LANES = 32
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32comp", "fp64"])
@@ -251,32 +251,40 @@ def run_gpu(args):
 
 
 def oracle_sample(cpu_seconds: float, fixed=None):
-    """Times the oracle on a bounded sample of the workload: for each eps and
-    level, a number of pairs proportional to that level's N_l, scaled so the
-    run takes about `cpu_seconds` on all host cores."""
+    """Times the oracle on a bounded sample of the workload.  Each round runs,
+    for every eps and level, a slice of pairs proportional to that level's
+    N_l (at least 32), continuing the pair index where the last round
+    stopped; rounds repeat until about `cpu_seconds` have passed, on all host
+    cores."""
     import oracle as O
     threads = os.cpu_count() or 1
     if fixed is None:
         fixed = [[max(100, 2 ** (12 - l)) for l in range(W.periodic_levels(e) + 1)] for e in EPS_SET]
-    # calibrate: a small slice first
-    def run(scale):
-        ev, t0 = 0, time.perf_counter()
-        for eps, n_l in zip(EPS_SET, fixed):
-            d = W.periodic_problem(eps)
-            p = O.Problem(**{k: d[k] for k in ("eps", "T", "dt0", "M", "L", "qoi", "init", "nbins",
-                                               "lo", "hi", "seed")})
-            for level, n in enumerate(n_l):
-                cnt = max(32, int(n * scale))
-                s = O.run_level(p, level, 0, cnt, threads=threads)
+    total = float(sum(sum(n) for n in fixed))
+    per_round = 2e5                                   # pairs per round over all levels
+    probs = []
+    for eps, n_l in zip(EPS_SET, fixed):
+        d = W.periodic_problem(eps)
+        p = O.Problem(**{k: d[k] for k in ("eps", "T", "dt0", "M", "L", "qoi", "init", "nbins",
+                                           "lo", "hi", "seed")})
+        probs.append((p, [max(32, int(per_round * n / total)) for n in n_l]))
+    nxt = [[0] * len(c) for _, c in probs]
+    ev, rounds, t0 = 0, 0, time.perf_counter()
+    while True:
+        for j, (p, counts) in enumerate(probs):
+            for level, cnt in enumerate(counts):
+                s = O.run_level(p, level, nxt[j][level], cnt, threads=threads)
+                nxt[j][level] += cnt
                 ev += s.events_f + s.events_c
-        return ev, time.perf_counter() - t0
-    ev, dt = run(1e-4)
-    scale = 1e-4 * max(1.0, cpu_seconds / max(dt, 1e-3))
-    scale = min(scale, 1.0)
-    ev, dt = run(scale)
+        rounds += 1
+        dt = time.perf_counter() - t0
+        if dt >= cpu_seconds:
+            break
+    pairs = sum(sum(x) for x in nxt)
     return {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": "every eps and level of the workload, %.3g of each N_l (>= 32 pairs), "
-                      "%d events in %.1f s" % (scale, ev, dt)}
+            "sample": "%d rounds over every eps and level of the workload, pairs per level "
+                      "proportional to N_l (>= 32): %d pairs, %d events in %.1f s"
+                      % (rounds, pairs, ev, dt)}
 
 
 def cpu_baseline(cpu_seconds, fixed):
@@ -291,7 +299,7 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    per_step = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    per_step = max(1.0, min(15.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_sample(per_step / 4)
     vals, evs, secs = [], 0, 0.0

@@ -154,6 +154,30 @@ void fill_launch(const mlkd_problem *p, const Derived &d, int level, uint64_t fi
     }
     P->first_pair = first;
     P->n_pairs = count;
+    BgParams<double> &b = P->bd;
+    b.R = P->R;
+    b.invR = 1.0 / P->R;
+    b.mu = P->mu;
+    b.sigma = P->sigma;
+    b.two_c2 = 2.0 * P->sigma * P->sigma / (P->R * P->R);
+    b.dt = P->dt;
+    b.Rdt = P->R * P->dt;
+    b.inv_Rdt = 1.0 / (P->R * P->dt);
+    b.lo = P->lo;
+    b.hi = P->hi;
+    b.inv_h = 1.0 / P->h;
+    BgParams<float> &f = P->bf;
+    f.R = (float)b.R;
+    f.invR = (float)b.invR;
+    f.mu = (float)b.mu;
+    f.sigma = (float)b.sigma;
+    f.two_c2 = (float)b.two_c2;
+    f.dt = (float)b.dt;
+    f.Rdt = (float)b.Rdt;
+    f.inv_Rdt = (float)b.inv_Rdt;
+    f.lo = (float)b.lo;
+    f.hi = (float)b.hi;
+    f.inv_h = (float)b.inv_h;
 }
 
 // Grid of the pair kernel: enough warps for the pairs, at most one full wave

@@ -45,7 +45,9 @@ template <typename Real> struct Arith;
 
 template <> struct Arith<float> {
     static __device__ __forceinline__ float log_(float x) { return logf(x); }
-    static __device__ __forceinline__ float expm1_(float x) { return expm1f(x); }
+    static __device__ __forceinline__ float exp_(float x) { return expf(x); }
+    static __device__ __forceinline__ float min_(float a, float b) { return fminf(a, b); }
+    static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
     static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
@@ -104,7 +106,9 @@ template <> struct Arith<float> {
 
 template <> struct Arith<double> {
     static __device__ __forceinline__ double log_(double x) { return log(x); }
-    static __device__ __forceinline__ double expm1_(double x) { return expm1(x); }
+    static __device__ __forceinline__ double exp_(double x) { return exp(x); }
+    static __device__ __forceinline__ double min_(double a, double b) { return fmin(a, b); }
+    static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
     static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
@@ -244,39 +248,44 @@ template <typename Real> struct Background {
     // offset dv = v' - mu (eqs. advection, diffusion):
     //   a = mu theta + dv (1 - e^{-s})/R,
     //   d = sqrt(2 sigma^2/R^2 f(s) + dv^2/R^2 g(s)),  s = R theta.
-    // Also returns s and om = 1 - e^{-s} for the aggregation weights.
-    __device__ __forceinline__ void kd_coeffs(Real theta, Real dv, Real &a, Real &d, Real &s,
+    // Also returns hs = h(s) = e^{-s} + s - 1 and om = 1 - e^{-s} for the
+    // aggregation weights.
+    // For s < 1 everything comes from the series (1 - e^{-s} = s - h(s));
+    // otherwise from e^{-s}, where the closed forms do not cancel.
+    __device__ __forceinline__ void kd_coeffs(Real theta, Real dv, Real &a, Real &d, Real &hs,
                                               Real &om) const
     {
         typedef Arith<Real> A;
-        s = R * theta;
-        const Real em = A::expm1_(-s);
-        om = -em;
+        const Real s = R * theta;
         Real f, g;
         if (s < Real(1)) {
-            const Real s3 = s * s * s;
-            f = s3 * A::f_series(s);
-            g = s3 * A::g_series(s);
+            const Real s2 = s * s;
+            hs = s2 * A::h_series(s);
+            om = s - hs;
+            f = s2 * s * A::f_series(s);
+            g = s2 * s * A::g_series(s);
         } else {
-            const Real e = Real(1) + em;
-            f = Real(2) * em + s * (e + Real(1));
+            const Real e = A::exp_(-s);
+            om = Real(1) - e;
+            hs = s - om;
+            f = Real(2) * (e - Real(1)) + s * (e + Real(1));
             g = Real(1) - Real(2) * s * e - e * e;
         }
         a = mu * theta + dv * om * invR;
         const Real dvR = dv * invR;
-        Real d2 = two_c2 * f + dvR * dvR * g;
+        const Real d2 = two_c2 * f + dvR * dvR * g;
         d = d2 > Real(0) ? A::sqrt_(d2) : Real(0);
     }
 
     // Dimensionless beta weight (Sec. 3.2, eq. weights-beta) of a diffusive
-    // phase with s = R theta and om = 1 - e^{-s}:
-    //   theta' = theta - zeta, zeta = om/R, so s' = R theta' = h(s), and
-    //   beta = (sigma/R) sqrt(2 h(s')).  Returns beta R / sigma squared.
-    __device__ __forceinline__ Real beta_hat_sq(Real s, Real om) const
+    // phase with h(s) = hs, s = R theta:
+    //   theta' = theta - zeta with zeta = (1 - e^{-s})/R, so s' = R theta' = h(s),
+    //   and beta = (sigma/R) sqrt(2 h(s')).  Returns (beta R / sigma)^2.
+    __device__ __forceinline__ Real beta_hat_sq(Real hs) const
     {
         typedef Arith<Real> A;
-        const Real sp = (s < Real(1)) ? s * s * A::h_series(s) : s - om;
-        const Real hp = (sp < Real(1)) ? sp * sp * A::h_series(sp) : A::expm1_(-sp) + sp;
+        const Real sp = hs;
+        const Real hp = (sp < Real(1)) ? sp * sp * A::h_series(sp) : A::exp_(-sp) + sp - Real(1);
         return Real(2) * hp;
     }
 };
@@ -303,14 +312,14 @@ template <typename Real> __device__ __forceinline__ Real cosine_inverse(Real u)
     const Real two_pi_sq_over6 = Real(6.5797362673929057);   // (2 pi)^2 / 6
     const Real g = u - Real(0.5);
     Real y = A::cbrt_(g / two_pi_sq_over6);
-    y = fmin(fmax(y, Real(-0.5)), Real(0.5));
+    y = A::min_(A::max_(y, Real(-0.5)), Real(0.5));
 #pragma unroll 1
     for (int it = 0; it < A::kNewtonIters; ++it) {
         const Real sp = A::sinpi_(y);
         const Real gp = Real(2) * sp * sp;
         if (!(gp > Real(0))) break;
         y = y - (cosine_G(y) - g) / gp;
-        y = fmin(fmax(y, Real(-0.5)), Real(0.5));
+        y = A::min_(A::max_(y, Real(-0.5)), Real(0.5));
     }
     Real x = y + Real(0.5);
     if (x >= Real(1)) x -= Real(1);

@@ -22,6 +22,15 @@ struct DevLevelStats {
     unsigned long long events_f, events_c;
 };
 
+// Derived constants of one level in one precision, computed on the host so
+// that the kernel reads them from the parameter bank with no arithmetic.
+template <typename Real> struct BgParams {
+    Real R, invR, mu, sigma;
+    Real two_c2;      // 2 sigma^2 / R^2
+    Real dt, Rdt, inv_Rdt;
+    Real lo, hi, inv_h;
+};
+
 // Parameters of one pair-kernel launch (passed by value as __grid_constant__).
 struct PairLaunch {
     double R, mu, sigma, dt;   // background and fine step of this level
@@ -35,6 +44,8 @@ struct PairLaunch {
     uint32_t request;
     uint32_t pad_;
     PhiloxKeys keys;
+    BgParams<double> bd;
+    BgParams<float> bf;
     unsigned long long first_pair, n_pairs, pairs_per_warp;
     double *partials;                  // [gridDim.x][kPartialWords]
     unsigned long long *hist;          // [3][nbins] fine, coarse, both; or null

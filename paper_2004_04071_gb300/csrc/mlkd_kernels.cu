@@ -21,8 +21,12 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 // ---------------------------------------------------------------------------
-// Accumulators of the six moment sums.  FP64 modes add doubles; the
-// compensated FP32 mode keeps (sum, error) pairs with an error-free TwoSum.
+// Per-lane sums of one launch: Y, Y^2, F(x_f), F(x_f)^2, F(x_c), F(x_c)^2.
+//   FP64 mode      : all six in FP64.
+//   FP32_DY64 mode : Y and Y^2 formed and summed in FP64 from the FP32 state;
+//                    the four F moments as compensated FP32 pairs.
+//   FP32_COMP mode : all six as compensated FP32 (sum, error) pairs.
+// Compensation is an error-free TwoSum per addition.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
 {
@@ -31,15 +35,34 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
     e = (a - (s - bp)) + (b - bp);
 }
 
-template <int MODE> struct Moments;
+struct CompF {
+    float s, c;
+    __device__ void zero() { s = 0.0f; c = 0.0f; }
+    __device__ void add(float x) {
+        float t, e;
+        two_sum(s, x, t, e);
+        s = t;
+        c += e;
+    }
+    __device__ void shfl_merge(int off) {
+        const float so = __shfl_down_sync(kFull, s, off);
+        const float co = __shfl_down_sync(kFull, c, off);
+        float t, e;
+        two_sum(s, so, t, e);
+        s = t;
+        c = c + co + e;
+    }
+    __device__ double value() const { return (double)s + (double)c; }
+};
 
-template <> struct Moments<kModeFP64> {
+template <int MODE> struct PairSums;
+
+template <> struct PairSums<kModeFP64> {
     double v[6];
     __device__ void zero() {
 #pragma unroll
         for (int j = 0; j < 6; ++j) v[j] = 0.0;
     }
-    __device__ void add(int j, double x) { v[j] += x; }
     __device__ void warp_reduce() {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
@@ -49,68 +72,133 @@ template <> struct Moments<kModeFP64> {
     __device__ double value(int j) const { return v[j]; }
 };
 
-template <> struct Moments<kModeFP32DY64> : Moments<kModeFP64> {};
+template <> struct PairSums<kModeFP32DY64> {
+    double sy, sy2;
+    CompF q[4];
+    __device__ void zero() {
+        sy = 0.0;
+        sy2 = 0.0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) q[j].zero();
+    }
+    __device__ void warp_reduce() {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            sy += __shfl_down_sync(kFull, sy, off);
+            sy2 += __shfl_down_sync(kFull, sy2, off);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) q[j].shfl_merge(off);
+        }
+    }
+    __device__ double value(int j) const { return j == 0 ? sy : j == 1 ? sy2 : q[j - 2].value(); }
+};
 
-template <> struct Moments<kModeFP32Comp> {
-    float s[6], c[6];
+template <> struct PairSums<kModeFP32Comp> {
+    CompF q[6];
     __device__ void zero() {
 #pragma unroll
-        for (int j = 0; j < 6; ++j) { s[j] = 0.0f; c[j] = 0.0f; }
-    }
-    __device__ void add(int j, float x) {
-        float t, e;
-        two_sum(s[j], x, t, e);
-        s[j] = t;
-        c[j] += e;
+        for (int j = 0; j < 6; ++j) q[j].zero();
     }
     __device__ void warp_reduce() {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)
 #pragma unroll
-            for (int j = 0; j < 6; ++j) {
-                const float so = __shfl_down_sync(kFull, s[j], off);
-                const float co = __shfl_down_sync(kFull, c[j], off);
-                float t, e;
-                two_sum(s[j], so, t, e);
-                s[j] = t;
-                c[j] = c[j] + co + e;
-            }
+            for (int j = 0; j < 6; ++j) q[j].shfl_merge(off);
     }
-    __device__ double value(int j) const { return (double)s[j] + (double)c[j]; }
+    __device__ double value(int j) const { return q[j].value(); }
 };
 
-// Precision in which F and Y are formed: FP64 except in the compensated
-// FP32 mode.
-template <int MODE> struct QoiReal { typedef double type; };
-template <> struct QoiReal<kModeFP32Comp> { typedef float type; };
-
-template <typename Q> __device__ __forceinline__ Q qoi_F(Q x, bool periodic)
+// QoI of one finished pair (eq. mlmc-compact): F(x) = x^2 in free space or
+// (x mod 1)^2 on the periodic unit interval; Y = F(x_f) - F(x_c), with
+// x_f^2 - x_c^2 formed as (x_f - x_c)(x_f + x_c).
+__device__ __forceinline__ void add_pair(PairSums<kModeFP64> &ps, double xf, double xc, bool coupled,
+                                         bool per)
 {
-    if (periodic) {
-        const Q m = x - floor(x);
-        return m * m;
-    }
-    return x * x;
+    const double mf = per ? xf - floor(xf) : xf;
+    const double mc = per ? xc - floor(xc) : xc;
+    const double Ff = mf * mf, Fc = coupled ? mc * mc : 0.0;
+    const double y = !coupled ? Ff : per ? Ff - Fc : (xf - xc) * (xf + xc);
+    ps.v[0] += y;
+    ps.v[1] += y * y;
+    ps.v[2] += Ff;
+    ps.v[3] += Ff * Ff;
+    ps.v[4] += Fc;
+    ps.v[5] += Fc * Fc;
+}
+
+__device__ __forceinline__ void add_pair(PairSums<kModeFP32DY64> &ps, float xf, float xc, bool coupled,
+                                         bool per)
+{
+    const float mf = per ? xf - floorf(xf) : xf;     // exact in FP32
+    const float mc = per ? xc - floorf(xc) : xc;
+    const double a = (double)mf, b = (double)mc;
+    const double y = !coupled ? a * a : per ? a * a - b * b : (a - b) * (a + b);
+    ps.sy += y;
+    ps.sy2 += y * y;
+    const float Ff = mf * mf, Fc = coupled ? mc * mc : 0.0f;
+    ps.q[0].add(Ff);
+    ps.q[1].add(Ff * Ff);
+    ps.q[2].add(Fc);
+    ps.q[3].add(Fc * Fc);
+}
+
+__device__ __forceinline__ void add_pair(PairSums<kModeFP32Comp> &ps, float xf, float xc, bool coupled,
+                                         bool per)
+{
+    const float mf = per ? xf - floorf(xf) : xf;
+    const float mc = per ? xc - floorf(xc) : xc;
+    const float Ff = mf * mf, Fc = coupled ? mc * mc : 0.0f;
+    const float y = !coupled ? Ff : per ? Ff - Fc : (xf - xc) * (xf + xc);
+    ps.q[0].add(y);
+    ps.q[1].add(y * y);
+    ps.q[2].add(Ff);
+    ps.q[3].add(Ff * Ff);
+    ps.q[4].add(Fc);
+    ps.q[5].add(Fc * Fc);
 }
 
 // Histogram bin of x: floor((x - lo)/h) inside [lo, hi), else -1; periodic
-// positions are first wrapped into [0, 1).
+// positions are first wrapped into [0, 1).  FP64 state uses the division in
+// FP64; FP32 state decides its bins in FP32.
 __device__ __forceinline__ int bin_of(double x, const PairLaunch &P)
 {
     if (P.periodic) x = x - floor(x);
     if (!(x >= P.lo && x < P.hi)) return -1;
-    int b = (int)floor((x - P.lo) / P.h);
+    const int b = (int)floor((x - P.lo) / P.h);
     return b < P.nbins ? b : P.nbins - 1;
 }
 
+struct BinsF {
+    float lo, hi, inv_h;
+    int nbins;
+    bool periodic;
+    __device__ int operator()(float x) const {
+        if (periodic) x = x - floorf(x);
+        if (!(x >= lo && x < hi)) return -1;
+        const int b = (int)floorf((x - lo) * inv_h);
+        return b < nbins ? b : nbins - 1;
+    }
+};
+
+__device__ __forceinline__ int bin_any(double x, const PairLaunch &P, const BinsF &) { return bin_of(x, P); }
+__device__ __forceinline__ int bin_any(float x, const PairLaunch &, const BinsF &bf) { return bf(x); }
+
 }  // namespace
 
+template <typename Real> __device__ __forceinline__ const BgParams<Real> &level_params(const PairLaunch &P);
+template <> __device__ __forceinline__ const BgParams<float> &level_params<float>(const PairLaunch &P) { return P.bf; }
+template <> __device__ __forceinline__ const BgParams<double> &level_params<double>(const PairLaunch &P) { return P.bd; }
+
+// Blocks per SM the register allocation must allow: FP32 state fits 64
+// registers (8 blocks of 128 threads); the FP64 form is bound by the FP64 pipe.
+template <typename Real> struct MinBlocks { static constexpr int value = 8; };
+template <> struct MinBlocks<double> { static constexpr int value = 1; };
+
 template <typename Real, int MODE, bool COUPLED>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, MinBlocks<Real>::value)
 pair_kernel(const __grid_constant__ PairLaunch P)
 {
     typedef Arith<Real> A;
-    typedef typename QoiReal<MODE>::type Q;
     extern __shared__ unsigned int s_hist[];          // [3][nbins]
     __shared__ double s_red[kWarpsPerBlock][kPartialWords];
 
@@ -118,15 +206,16 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     for (int i = threadIdx.x; i < 3 * nbins; i += blockDim.x) s_hist[i] = 0u;
     if (nbins > 0) __syncthreads();
 
+    const BgParams<Real> &bp = level_params<Real>(P);
     Background<Real> bg;
-    bg.R = (Real)P.R;
-    bg.invR = (Real)(1.0 / P.R);
-    bg.mu = (Real)P.mu;
-    bg.sigma = (Real)P.sigma;
-    bg.two_c2 = (Real)(2.0 * P.sigma * P.sigma / (P.R * P.R));
-    bg.dt = (Real)P.dt;
-    bg.Rdt = (Real)(P.R * P.dt);
-    bg.inv_Rdt = (Real)(1.0 / (P.R * P.dt));
+    bg.R = bp.R;
+    bg.invR = bp.invR;
+    bg.mu = bp.mu;
+    bg.sigma = bp.sigma;
+    bg.two_c2 = bp.two_c2;
+    bg.dt = bp.dt;
+    bg.Rdt = bp.Rdt;
+    bg.inv_Rdt = bp.inv_Rdt;
 
     const int n = P.n;
     const int M = P.M;
@@ -149,37 +238,28 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     uint32_t k = 0, evc = 0;
     bool fresh = true;
 
-    Moments<MODE> mom;
+    PairSums<MODE> mom;
     mom.zero();
+    BinsF binsf;
+    binsf.lo = P.bf.lo;
+    binsf.hi = P.bf.hi;
+    binsf.inv_h = P.bf.inv_h;
+    binsf.nbins = P.nbins;
+    binsf.periodic = P.periodic != 0;
     unsigned long long ev_f_sum = 0, ev_c_sum = 0;
 
     // Alg. 1 final drift, QoI, sums and histogram of the finished pair.
     auto finish_pair = [&]() {
         if (i_f < n) xf = xf + vf * ((Real)(n - i_f) * bg.dt);
         if (COUPLED && ic < n) xc = xc + vc * ((Real)(n - ic) * bg.dt);
-        const Q xfq = (Q)xf, xcq = (Q)xc;
-        const bool per = P.periodic != 0;
-        const Q Ff = qoi_F<Q>(xfq, per);
-        Q Fc = 0, y;
-        if (COUPLED) {
-            Fc = qoi_F<Q>(xcq, per);
-            y = per ? Ff - Fc : (xfq - xcq) * (xfq + xcq);
-        } else {
-            y = Ff;
-        }
-        mom.add(0, y);
-        mom.add(1, y * y);
-        mom.add(2, Ff);
-        mom.add(3, Ff * Ff);
-        mom.add(4, Fc);
-        mom.add(5, Fc * Fc);
+        add_pair(mom, xf, xc, COUPLED, P.periodic != 0);
         ev_f_sum += k;
         ev_c_sum += evc;
         if (nbins > 0) {
-            const int bf = bin_of((double)xf, P);
+            const int bf = bin_any(xf, P, binsf);
             if (bf >= 0) atomicAdd(&s_hist[bf], 1u);
             if (COUPLED) {
-                const int bc = bin_of((double)xc, P);
+                const int bc = bin_any(xc, P, binsf);
                 if (bc >= 0) atomicAdd(&s_hist[nbins + bc], 1u);
                 if (bc >= 0 && bc == bf) atomicAdd(&s_hist[2 * nbins + bf], 1u);
             }
@@ -243,8 +323,8 @@ pair_kernel(const __grid_constant__ PairLaunch P)
         const Real theta = bg.dt * ((Real)(sq + 1) - qf);         // eq. diffusive-time
         const Real dv = bg.sigma * d.nu;                          // v_{k+1} - mu
         const Real v1 = bg.mu + dv;
-        Real a, dd, s, om;
-        bg.kd_coeffs(theta, dv, a, dd, s, om);
+        Real a, dd, hs, om;
+        bg.kd_coeffs(theta, dv, a, dd, hs, om);
         xf = xf + vf * (qf * bg.dt) + (a + dd * d.chi);           // eq. position-update
         i_f += sq + 1;                                            // eq. time-update
         vf = v1;
@@ -254,12 +334,12 @@ pair_kernel(const __grid_constant__ PairLaunch P)
         if (COUPLED) {
             // Sec. 3.2 aggregation, streamed: this phase's chi with beta, and the
             // new phase's nu with alpha if it collides inside the coarse step.
-            const Real bh2 = bg.beta_hat_sq(s, om);
+            const Real bh2 = bg.beta_hat_sq(hs);
             if (fresh) { chi_first = d.chi; fresh = false; }
             num += A::sqrt_(bh2) * d.chi;
             den += bh2;
             if (qf < (Real)(Ec - i_f)) {
-                const Real ah = qf * bg.Rdt + om;                 // R (tau' ) = R tau + R zeta
+                const Real ah = qf * bg.Rdt + om;                 // R tau' = R tau + R zeta
                 num += ah * d.nu;
                 den += ah * ah;
             } else {
@@ -267,8 +347,8 @@ pair_kernel(const __grid_constant__ PairLaunch P)
                 // after it, the coarse flight tau~ = fine collision - E_c
                 // (homogeneous eq. epsilon-update), carried in fine units.
                 const Real thc = bg.dt * ((Real)(Ec - ic) - qc);
-                Real ac, dc, sc, omc;
-                bg.kd_coeffs(thc, dv, ac, dc, sc, omc);
+                Real ac, dc, hsc, omc;
+                bg.kd_coeffs(thc, dv, ac, dc, hsc, omc);
                 const Real chit = den > Real(0) ? num * A::rsqrt_(den) : chi_first;
                 xc = xc + vc * (qc * bg.dt) + (ac + dc * chit);
                 qc = qf - (Real)(Ec - i_f);
