@@ -5,9 +5,11 @@ Workload (a "step"): one full multilevel estimate of the periodic problem for
 each eps in {1, 0.1, 1e-3} -- density 1 + cos(2 pi x) on [0, 1), T = 1,
 dt0 = 0.5, M = 2, L = min(12, ceil(log2(dt0/(eps^2/4)))), QoI int x^2 f plus a
 128-bin density -- with the sample counts N_l that the variance-optimal rule
-gives for RMSE 1e-3 (fixed by one untimed adaptive pilot).  Every level of
-every eps runs the pair kernel, the fixed-order finalize and the FP64
-controller.
+gives for RMSE 1e-3 (fixed by one untimed adaptive pilot).  By default the
+three estimates run together in the batched form (one persistent pair kernel
+over a device work queue, scheduler and FP64 controller on the device, one
+CUDA graph per step) with the autotuned pairs-per-thread and
+substeps-per-launch; --form plain runs each level as its own launch.
 
 Metric: correlated particle-substeps (executed fine + coarse KD events) per
 second.  `value` is timed on the device with CUDA events; `e2e` is the host
@@ -53,7 +55,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32comp", "fp64"])
+    ap.add_argument("--precision", default="fp32comp", choices=["fp32", "fp32comp", "fp64"])
+    ap.add_argument("--form", default="batch", choices=["batch", "plain"],
+                    help="batched persistent form (default) or the per-level form")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     return ap.parse_args()
@@ -142,38 +146,60 @@ def run_gpu(args):
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     torch.cuda.set_device(local)
     prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
-    ctx = mk.Context(local)
+    base_cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=256, use_graph=1,
+                               max_requests=16, max_nbins=128)
+    ctx = mk.Context(local, arena_bytes=mk.batch_workspace_bytes(base_cfg))
     stream = torch.cuda.current_stream()
+    dev = "cuda:%d" % local
 
-    # ---- untimed pilot: N_l from the variance-optimal rule at tol 1e-3 ----
-    probs = problems_for_rank(rank)
-    fixed = []
-    for d in probs:
-        p = mk.make_problem(precision=prec, **{k: v for k, v in d.items()})
-        r = ctx.estimate(p)
-        fixed.append([lv["n"] for lv in r.levels])
-    step_problems = [mk.make_problem(precision=prec, n_fixed=n, **d) for d, n in zip(probs, fixed)]
+    # ---- untimed: N_l from the variance-optimal rule at tol 1e-3, and the
+    # time to tolerance of the adaptive estimate in this form -------------
+    dicts = problems_for_rank(rank)
+    adaptive = [mk.make_problem(precision=prec, **d) for d in dicts]
+    t0 = time.perf_counter()
+    if args.form == "batch":
+        pilot = ctx.estimate_batch(adaptive, base_cfg)
+    else:
+        pilot = [ctx.estimate(p) for p in adaptive]
+    ttt_first = time.perf_counter() - t0
+    fixed = [[lv["n"] for lv in r.levels] for r in pilot]
+    step_problems = [mk.make_problem(precision=prec, n_fixed=n, **d) for d, n in zip(dicts, fixed)]
 
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda:%d" % local)
+    cfg = base_cfg
+    tune = None
+    if args.form == "batch" and prec != mk.PREC_FP64:
+        cfg, secs = ctx.autotune_batch(step_problems, base_cfg)
+        tune = {"best": cfg.as_dict(), "seconds_ppt_major": secs}
 
     def step():
-        events = 0
-        for p in step_problems:
-            r = ctx.estimate(p, stream)
-            events += sum(lv["events_f"] + lv["events_c"] for lv in r.levels)
-        return events
+        if args.form == "batch":
+            rs = ctx.estimate_batch(step_problems, cfg, stream)
+        else:
+            rs = [ctx.estimate(p, stream) for p in step_problems]
+        return sum(lv["events_f"] + lv["events_c"] for r in rs for lv in r.levels), rs
+
+    # time to tolerance (adaptive, after warm-up of the code paths)
+    def ttt_once(problems):
+        t = time.perf_counter()
+        if args.form == "batch":
+            rs = ctx.estimate_batch(problems, cfg, stream)
+        else:
+            rs = [ctx.estimate(p, stream) for p in problems]
+        return time.perf_counter() - t, rs
 
     for _ in range(args.warmup):
         step()
-    ctx.set_timing(True)
-    ctx.get_timing(reset=True)
+    ttt = sorted(ttt_once(adaptive)[0] for _ in range(3))[1]
 
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    ctx.get_timing(reset=True)
     sampler = ClockSampler(local)
     sampler.start()
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     dev_ms, host_s, events_total = 0.0, 0.0, 0
+    last = None
     for _ in range(args.steps):
         flush.zero_()                       # L2 flush outside the timed window
         torch.cuda.synchronize()
@@ -181,7 +207,8 @@ def run_gpu(args):
         e1 = torch.cuda.Event(enable_timing=True)
         h0 = time.perf_counter()
         e0.record(stream)
-        events_total += step()
+        ev, last = step()
+        events_total += ev
         e1.record(stream)
         torch.cuda.synchronize()
         host_s += time.perf_counter() - h0
@@ -192,30 +219,41 @@ def run_gpu(args):
     clocks = sampler.stop()
     timing = ctx.get_timing(reset=True)
 
-    # max over ranks of the timed region; sum of the work
+    # roofline pass: the same step with the pair kernel timed per launch
+    # (batched form in its host-loop variant, per-level form as it is)
+    ctx.set_timing(True)
+    ctx.get_timing(reset=True)
+    fine = coarse = 0
+    rsteps = max(1, min(args.steps, 10))
+    for _ in range(rsteps):
+        if args.form == "batch":
+            hl = mk.batch_config(**dict(cfg.as_dict(), use_graph=0))
+            rs = ctx.estimate_batch(step_problems, hl, stream)
+        else:
+            rs = [ctx.estimate(p, stream) for p in step_problems]
+        fine += sum(lv["events_f"] for r in rs for lv in r.levels)
+        coarse += sum(lv["events_c"] for r in rs for lv in r.levels)
+    rt = ctx.get_timing(reset=True)
+    ctx.set_timing(False)
+
     t_dev = dev_ms / 1e3
     t_host = host_s
     ev = float(events_total)
     if world > 1:
-        t = torch.tensor([t_dev, t_host], dtype=torch.float64, device="cuda:%d" % local)
+        t = torch.tensor([t_dev, t_host], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([ev], dtype=torch.float64, device="cuda:%d" % local)
+        e = torch.tensor([ev], dtype=torch.float64, device=dev)
         dist.all_reduce(e, op=dist.ReduceOp.SUM)
         t_dev, t_host, ev = float(t[0]), float(t[1]), float(e[0])
 
-    # events split for the roofline of the pair kernel (rank-local)
-    fine = coarse = 0
-    for p in step_problems:
-        r = ctx.estimate(p)
-        fine += sum(lv["events_f"] for lv in r.levels)
-        coarse += sum(lv["events_c"] for lv in r.levels)
-    launches_per_step = timing["launches"] / max(1, args.steps)
-    kernel_s = timing["pair_kernel_ms"] / 1e3
-    algo_inst = (fine * INST_PER_FINE_EVENT + coarse * INST_PER_COARSE_EVENT) * args.steps
+    kernel_s = rt["pair_kernel_ms"] / 1e3
+    algo_inst = fine * INST_PER_FINE_EVENT + coarse * INST_PER_COARSE_EVENT
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     mhz = clocks.get("sm_mhz") or 1470.0
     peak = sm_count * SMSP_PER_SM * LANES * mhz * 1e6
     achieved = algo_inst / kernel_s if kernel_s > 0 else 0.0
+    kname = ("batch_pair_kernel" if args.form == "batch" else "pair_kernel") + \
+        {"fp32": "<float, FP32_DY64>", "fp32comp": "<float, FP32_COMP>", "fp64": "<double, FP64>"}[args.precision]
 
     out = {
         "metric": METRIC, "value": ev / t_dev, "unit": UNIT, "n_gpus": world,
@@ -226,8 +264,13 @@ def run_gpu(args):
         "data": "synthetic (Philox streams; analytic homogeneous background)",
         "config": {"workload": "periodic full MLMC, eps in {1,0.1,1e-3}, T=1, dt0=0.5, M=2, "
                                "L=min(12,ceil(log2(dt0/(eps^2/4)))), tol=1e-3, 128 bins",
-                   "precision": args.precision, "n_fixed": fixed,
+                   "form": args.form, "precision": args.precision, "n_fixed": fixed,
+                   "batch_config": cfg.as_dict() if args.form == "batch" else None,
+                   "autotune": tune,  # seconds over ppt {1,2,4,8} x substeps {16,64,256,unbounded}
                    "events_per_step": ev / args.steps / world,
+                   "time_to_tolerance_s": ttt, "time_to_tolerance_first_call_s": ttt_first,
+                   "estimates": [r.estimate for r in last],
+                   "variances": [r.variance for r in last],
                    "l2": "flushed (256 MB write) between timed steps; no input arrays"},
         "e2e": {"value": ev / t_host, "unit": UNIT,
                 "h2d_bytes_per_step": len(step_problems) * (88 + 8 * 13),
@@ -236,10 +279,13 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                      "unit": "Ginst/s (lane instructions)",
                      "frac": achieved / peak if peak else None, "traffic": None,
-                     "kernel": "pair_kernel<float, FP32_DY64, coupled>",
-                     "launches_per_step": launches_per_step,
-                     "avg_launch_ms": timing["pair_kernel_ms"] / max(1, timing["launches"]),
-                     "peak_basis": "152 SM x 4 SMSP x 32 lanes x median SM clock under load"},
+                     "kernel": kname,
+                     "launches_timed": rt["launches"],
+                     "avg_launch_ms": rt["pair_kernel_ms"] / max(1, rt["launches"]),
+                     "events_timed": fine + coarse,
+                     "peak_basis": "SMs x 4 SMSP x 32 lanes x median SM clock under load "
+                                   "(issue-slot bound; algorithmic 190 lane-inst per fine event, "
+                                   "50 per coarse event)"},
         "clocks": clocks,
     }
     if rank == 0:

@@ -185,6 +185,100 @@ MLKD_API mlkd_status mlkd_context_set_timing(mlkd_context *ctx, int enable);
 /* Copies the accumulated timing to *out; reset != 0 zeroes it afterwards. */
 MLKD_API mlkd_status mlkd_context_get_timing(mlkd_context *ctx, mlkd_kernel_timing *out, int reset);
 
+/* ---------------------------------------------------------------------------
+ * Batched form: many independent estimates (different eps, T, levels, QoI,
+ * tolerances) advanced together by one persistent pair kernel that pulls
+ * chunks of (request, level, pair range) from a device work queue.  Between
+ * slices a scheduler kernel finalizes every request whose round is complete
+ * (fixed-order FP64 sums of its chunk rows), runs the controller of Sec. 4.1
+ * for it and appends its next round, so requests never wait for one another's
+ * rounds.  With use_graph the whole loop is one CUDA graph whose device-side
+ * while-node repeats [scheduler, pair slice, bookkeeping] until every request
+ * has met its tolerance.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t pairs_per_thread;    /* pair states per lane, advanced together: 1, 2, 4 or 8   */
+    int32_t substeps_per_launch; /* event iterations per warp per pair-kernel launch; a chunk
+                                    in progress is stored and resumed (0: no limit)          */
+    int32_t use_graph;           /* 1: one CUDA graph with a device-side loop                 */
+    int32_t max_requests;        /* request slots of the batch region (<= 4096)             */
+    int32_t max_nbins;           /* histogram bins per request (<= 256)                      */
+} mlkd_batch_config;
+
+/* Arena bytes a context needs for the batched and serving forms with this
+ * configuration (the base workspace included); 0 if cfg is invalid. */
+MLKD_API size_t mlkd_batch_workspace_bytes(const mlkd_batch_config *cfg);
+
+/* Runs n independent estimates (each as in mlkd_estimate: warm-up, then
+ * rounds until eqs. Nopt1/Noptj are met, or n_fixed) in the batched form and
+ * writes results[i] for problems[i].  All problems must share precision and
+ * seed (request ids separate their streams), have nbins <= cfg->max_nbins,
+ * and n <= cfg->max_requests; the context arena must hold
+ * mlkd_batch_workspace_bytes(cfg).  Synchronous. */
+MLKD_API mlkd_status mlkd_estimate_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
+                                         const mlkd_batch_config *cfg, void *stream,
+                                         mlkd_result *results);
+
+/* Autotuner: times mlkd_estimate_batch on these problems for every
+ * pairs_per_thread in {1, 2, 4, 8} and substeps_per_launch in
+ * {16, 64, 256, 0 (unbounded)} (graph form), and writes the fastest
+ * configuration to *best (its other fields copied from *base).  seconds[16],
+ * if not NULL, receives the times in the order ppt-major. */
+MLKD_API mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
+                                         const mlkd_batch_config *base, void *stream,
+                                         mlkd_batch_config *best, double *seconds);
+
+/* ---------------------------------------------------------------------------
+ * Serving form: continuous batching of estimate requests.  mlkd_server_start
+ * starts a host scheduler thread on its own stream.  It admits submitted
+ * requests into free request slots of the batch region (the slot count is the
+ * HBM budget: cfg.batch.max_requests slots of the arena), then repeats one
+ * loop iteration of the batched form per slice.  Requests that arrive while
+ * others run join at the next slice; finished requests free their slot at
+ * once.  A request's result depends only on its own problem (never on what
+ * else is in flight), so it is the same alone and in the mix.
+ * While a server runs, mlkd_estimate_batch and mlkd_autotune_batch on the
+ * same context return MLKD_EBUSY.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    mlkd_batch_config batch;     /* kernel configuration; max_requests = slots           */
+    int32_t precision;           /* mlkd_prec of every request                            */
+    int32_t max_pending;         /* submitted, not yet admitted requests (EBUSY beyond)  */
+    uint64_t seed;               /* Philox key of every request                           */
+} mlkd_server_config;
+
+typedef struct {
+    uint64_t submitted, admitted, completed, cancelled, rejected;
+    uint64_t iterations;         /* scheduler / pair-slice iterations run                 */
+    double busy_seconds;         /* wall time spent in iterations                         */
+} mlkd_server_stats;
+
+/* Starts the server (arena must hold mlkd_batch_workspace_bytes(&cfg->batch)). */
+MLKD_API mlkd_status mlkd_server_start(mlkd_context *ctx, const mlkd_server_config *cfg);
+
+/* Queues an estimate request (same rules as mlkd_estimate; precision and seed
+ * must match the server's).  Returns MLKD_EBUSY if max_pending requests are
+ * already waiting for a slot.  *req_id identifies it for poll/cancel. */
+MLKD_API mlkd_status mlkd_submit(mlkd_context *ctx, const mlkd_problem *problem, uint64_t *req_id);
+
+/* Waits up to timeout_ms (0: do not wait, < 0: forever) for the request and
+ * copies its result (out->density: host, nbins values or NULL); out->seconds
+ * is the latency from submit to completion.  MLKD_ETIMEDOUT if it is not
+ * finished yet, MLKD_ENOTFOUND for an unknown, consumed or cancelled id.  A
+ * returned result is consumed. */
+MLKD_API mlkd_status mlkd_poll(mlkd_context *ctx, uint64_t req_id, int timeout_ms, mlkd_result *out);
+
+/* Cancels a request: a waiting one is dropped at once; an admitted one frees
+ * its slot as soon as its chunks in flight have drained. */
+MLKD_API mlkd_status mlkd_cancel(mlkd_context *ctx, uint64_t req_id);
+
+/* Counters of the running server. */
+MLKD_API mlkd_status mlkd_server_stats_get(mlkd_context *ctx, mlkd_server_stats *out);
+
+/* Stops the scheduler thread after its current iteration; requests not yet
+ * finished are dropped.  Safe to call on a context without a server. */
+MLKD_API mlkd_status mlkd_server_stop(mlkd_context *ctx);
+
 /* Allocation-free variant of mlkd_run_level.  The paper has no counterpart:
  * this entry point serves callers that may not allocate device memory at
  * all -- code running inside a host application whose own allocator must own

@@ -33,7 +33,9 @@ MAX_BINS = 1024
 EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_context_create", "mlkd_context_destroy", "mlkd_run_level",
             "mlkd_estimate", "mlkd_debug_pairs", "mlkd_context_set_timing",
-            "mlkd_context_get_timing", "mlkd_run_level_noalloc"]
+            "mlkd_context_get_timing", "mlkd_run_level_noalloc", "mlkd_batch_workspace_bytes",
+            "mlkd_estimate_batch", "mlkd_autotune_batch", "mlkd_server_start", "mlkd_submit",
+            "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -76,6 +78,45 @@ class Result(ctypes.Structure):
                 ("density", ctypes.POINTER(ctypes.c_double)), ("seconds", ctypes.c_double)]
 
 
+class BatchConfig(ctypes.Structure):
+    _fields_ = [("pairs_per_thread", ctypes.c_int32), ("substeps_per_launch", ctypes.c_int32),
+                ("use_graph", ctypes.c_int32), ("max_requests", ctypes.c_int32),
+                ("max_nbins", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def batch_config(pairs_per_thread=1, substeps_per_launch=256, use_graph=1, max_requests=64,
+                 max_nbins=128) -> BatchConfig:
+    c = BatchConfig()
+    c.pairs_per_thread, c.substeps_per_launch, c.use_graph = pairs_per_thread, substeps_per_launch, use_graph
+    c.max_requests, c.max_nbins = max_requests, max_nbins
+    return c
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("batch", BatchConfig), ("precision", ctypes.c_int32), ("max_pending", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
+                ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
+                ("rejected", ctypes.c_uint64), ("iterations", ctypes.c_uint64),
+                ("busy_seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+def server_config(batch: BatchConfig, precision=PREC_FP32_DY64, seed=0, max_pending=4096) -> ServerConfig:
+    c = ServerConfig()
+    c.batch = batch
+    c.precision, c.seed, c.max_pending = precision, seed & 0xFFFFFFFFFFFFFFFF, max_pending
+    return c
+
+
 _lib = None
 
 
@@ -111,6 +152,25 @@ def lib():
         L.mlkd_run_level_noalloc.argtypes = [P(Problem), ctypes.c_int, u64, u64, vp, P(LevelStats),
                                              P(ctypes.c_uint64)]
         L.mlkd_run_level_noalloc.restype = ctypes.c_int
+        L.mlkd_batch_workspace_bytes.argtypes = [P(BatchConfig)]
+        L.mlkd_batch_workspace_bytes.restype = ctypes.c_size_t
+        L.mlkd_estimate_batch.argtypes = [vp, P(Problem), ctypes.c_int, P(BatchConfig), vp, P(Result)]
+        L.mlkd_estimate_batch.restype = ctypes.c_int
+        L.mlkd_autotune_batch.argtypes = [vp, P(Problem), ctypes.c_int, P(BatchConfig), vp,
+                                          P(BatchConfig), P(ctypes.c_double)]
+        L.mlkd_autotune_batch.restype = ctypes.c_int
+        L.mlkd_server_start.argtypes = [vp, P(ServerConfig)]
+        L.mlkd_server_start.restype = ctypes.c_int
+        L.mlkd_submit.argtypes = [vp, P(Problem), P(ctypes.c_uint64)]
+        L.mlkd_submit.restype = ctypes.c_int
+        L.mlkd_poll.argtypes = [vp, ctypes.c_uint64, ctypes.c_int, P(Result)]
+        L.mlkd_poll.restype = ctypes.c_int
+        L.mlkd_cancel.argtypes = [vp, ctypes.c_uint64]
+        L.mlkd_cancel.restype = ctypes.c_int
+        L.mlkd_server_stats_get.argtypes = [vp, P(ServerStats)]
+        L.mlkd_server_stats_get.restype = ctypes.c_int
+        L.mlkd_server_stop.argtypes = [vp]
+        L.mlkd_server_stop.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -144,6 +204,10 @@ def make_problem(eps, T, dt0, M=2, L=1, qoi=QOI_X2, init=INIT_ORIGIN, nbins=0, l
 
 def workspace_bytes(problem: Problem) -> int:
     return int(lib().mlkd_workspace_bytes(ctypes.byref(problem)))
+
+
+def batch_workspace_bytes(cfg: BatchConfig) -> int:
+    return int(lib().mlkd_batch_workspace_bytes(ctypes.byref(cfg)))
 
 
 def _stream_handle(stream):
@@ -224,6 +288,82 @@ class Context:
         n = n_pairs
         return (xf[:n].cpu().numpy(), xc[:n].cpu().numpy(), kf[:n].cpu().numpy().astype(np.int64),
                 kc[:n].cpu().numpy().astype(np.int64))
+
+    # -- mlkd_estimate_batch / mlkd_autotune_batch ----------------------------
+    def estimate_batch(self, problems, cfg: BatchConfig, stream=None):
+        n = len(problems)
+        arr = (Problem * n)(*problems)
+        res = (Result * n)()
+        dens = []
+        for i, p in enumerate(problems):
+            d = None
+            if p.nbins > 0:
+                d = np.zeros(p.nbins, np.float64)
+                res[i].density = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            dens.append(d)
+        _check(lib().mlkd_estimate_batch(self.handle, arr, n, ctypes.byref(cfg),
+                                         _stream_handle(stream), res), "mlkd_estimate_batch")
+        out = []
+        for i in range(n):
+            r = res[i]
+            nl = r.n_levels
+            out.append(EstimateResult(r.estimate, r.variance, r.rounds,
+                                      [r.lv[l].as_dict() for l in range(nl)],
+                                      [r.var_level[l] for l in range(nl)],
+                                      [r.cost_level[l] for l in range(nl)], dens[i], r.seconds))
+        return out
+
+    def autotune_batch(self, problems, base: BatchConfig, stream=None):
+        n = len(problems)
+        arr = (Problem * n)(*problems)
+        best = BatchConfig()
+        secs = (ctypes.c_double * 16)()
+        _check(lib().mlkd_autotune_batch(self.handle, arr, n, ctypes.byref(base),
+                                         _stream_handle(stream), ctypes.byref(best), secs),
+               "mlkd_autotune_batch")
+        return best, list(secs)
+
+    # -- serving: mlkd_server_start / submit / poll / cancel / stop ----------
+    def server_start(self, cfg: ServerConfig):
+        _check(lib().mlkd_server_start(self.handle, ctypes.byref(cfg)), "mlkd_server_start")
+
+    def submit(self, problem: Problem) -> int:
+        rid = ctypes.c_uint64()
+        _check(lib().mlkd_submit(self.handle, ctypes.byref(problem), ctypes.byref(rid)), "mlkd_submit")
+        return int(rid.value)
+
+    def try_submit(self, problem: Problem):
+        """mlkd_submit returning (status, id) instead of raising."""
+        rid = ctypes.c_uint64()
+        rc = lib().mlkd_submit(self.handle, ctypes.byref(problem), ctypes.byref(rid))
+        return rc, int(rid.value)
+
+    def poll(self, req_id: int, timeout_ms: int = -1, nbins: int = 0):
+        """Returns (status, EstimateResult or None)."""
+        r = Result()
+        dens = None
+        if nbins > 0:
+            dens = np.zeros(nbins, np.float64)
+            r.density = dens.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        rc = lib().mlkd_poll(self.handle, req_id, timeout_ms, ctypes.byref(r))
+        if rc != MLKD_OK:
+            return rc, None
+        nl = r.n_levels
+        return rc, EstimateResult(r.estimate, r.variance, r.rounds,
+                                  [r.lv[l].as_dict() for l in range(nl)],
+                                  [r.var_level[l] for l in range(nl)],
+                                  [r.cost_level[l] for l in range(nl)], dens, r.seconds)
+
+    def cancel(self, req_id: int) -> int:
+        return lib().mlkd_cancel(self.handle, req_id)
+
+    def server_stats(self) -> dict:
+        st = ServerStats()
+        _check(lib().mlkd_server_stats_get(self.handle, ctypes.byref(st)), "mlkd_server_stats_get")
+        return st.as_dict()
+
+    def server_stop(self):
+        _check(lib().mlkd_server_stop(self.handle), "mlkd_server_stop")
 
     # -- mlkd_estimate -----------------------------------------------------
     def estimate(self, problem: Problem, stream=None):

@@ -1,0 +1,1379 @@
+// mlkd_batch.cu -- batched form: many independent MLMC estimates advanced by
+// one persistent pair kernel pulling chunks from a device work queue.
+//
+// Device state (in the context arena, after the base workspace):
+//   ReqDesc[max_requests]   problem of each request slot (host-written)
+//   ReqState[max_requests]  level sums, pairs scheduled, round bookkeeping
+//   Chunk[cap]              work queue: (request, level, first pair, count)
+//   rows[cap][8]            one row of sums per chunk (fixed-order input of
+//                           the finalize)
+//   hist[max_requests][16][3][max_nbins]  fine/coarse/both bin counts
+//   BatchCtl                queue head/tail and the live-request count
+//
+// One iteration of the loop: the scheduler kernel (one block per request)
+// finalizes every request whose round has completed, runs the FP64
+// controller of Sec. 4.1 for it and appends its next round's chunks (finest
+// level first); the pair kernel runs one slice; the bookkeeping kernel trims
+// the queue head and, in the graph form, sets the while-node condition.
+#include <condition_variable>
+#include <cstdio>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "mlkd_host.h"
+#include "mlkd_pair.cuh"
+
+namespace mlkd {
+
+constexpr int kBL = MLKD_MAX_LEVELS;            // levels per request
+constexpr int kMaxChunksPerJob = 2048;           // chunks per (request, level, round)
+constexpr int kChunkQuantum = 32;                // chunk sizes are multiples of one pair per lane
+constexpr int kTargetIters = 2048;               // target warp iterations per chunk
+constexpr long long kMaxChunkPairs = 1LL << 22;  // pairs per chunk at most
+constexpr int kSchedThreads = 256;
+
+struct ReqDesc {
+    BgParams<double> bd[kBL];
+    BgParams<float> bf[kBL];
+    long long n_fixed[kBL];
+    double tol, h;
+    int32_t n_level[kBL];
+    int32_t L, M, init, nbins, periodic, density, n_warmup, use_fixed;
+    uint32_t request;
+    int32_t pad_;
+};
+
+struct ReqState {
+    DevLevelStats acc[kBL];
+    long long have[kBL];
+    long long job_cb[kBL];      // first chunk id of this round's job per level
+    long long job_count[kBL];   // pairs of this round's job per level
+    int32_t job_nch[kBL];       // chunks of this round's job per level (0: none)
+    int32_t status;             // 0 free, 1 admitted, 2 running, 3 done
+    int32_t pending;            // chunks of the open round not yet finished
+    int32_t rounds;
+    int32_t pad_;
+    double estimate, variance;
+    double var_level[kBL], cost_level[kBL];
+    long long target[kBL];
+};
+
+struct Chunk {
+    int32_t req, level;
+    unsigned long long first;
+    int32_t count, pad_;
+};
+
+struct BatchCtl {
+    unsigned long long q_head, q_tail;
+    int32_t live;
+    int32_t iterations;         // loop iterations run (three kernel launches each)
+};
+
+// Persisted state of one warp between slices: the chunk it is working on.
+struct WarpHdr {
+    int32_t valid;
+    int32_t pad_;
+    unsigned long long c;        // chunk id
+    unsigned long long next;     // next unassigned pair of the chunk
+};
+
+struct BatchLaunch {
+    const ReqDesc *req;
+    ReqState *state;
+    Chunk *queue;
+    double *rows;
+    unsigned long long *hist;
+    BatchCtl *ctl;
+    WarpHdr *hdr;                // [grid warps]
+    int32_t *status_out;         // [slots]: status after the scheduler (host-readable copy)
+    uint32_t *lane_words;        // [words][grid lanes]: pair states and sums per lane
+    unsigned long long cap_mask;
+    int32_t max_nbins;
+    int32_t slice_iters;
+    int32_t n_slots;
+    int32_t pad_;
+    PhiloxKeys keys;
+};
+
+constexpr int kMaxPPT = 8;
+constexpr size_t kMaxLanes = 256ull * 16 * kThreads;   // lane slots: up to 256 SMs x 16 blocks
+
+// Lane words of T, stored word-major so that a warp's 32 lanes write 32
+// consecutive words.
+template <typename T> __device__ __forceinline__ void put_words(const T &v, uint32_t *base, size_t stride, int &w)
+{
+    static_assert(sizeof(T) % 4 == 0, "lane state must be whole words");
+    uint32_t tmp[sizeof(T) / 4];
+    memcpy(tmp, &v, sizeof(T));
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) base[(size_t)(w + i) * stride] = tmp[i];
+    w += (int)(sizeof(T) / 4);
+}
+
+template <typename T> __device__ __forceinline__ void get_words(T &v, const uint32_t *base, size_t stride, int &w)
+{
+    uint32_t tmp[sizeof(T) / 4];
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(T) / 4); ++i) tmp[i] = base[(size_t)(w + i) * stride];
+    memcpy(&v, tmp, sizeof(T));
+    w += (int)(sizeof(T) / 4);
+}
+
+template <typename Real, int MODE, int PPT> constexpr int lane_words()
+{
+    return (int)((PPT * sizeof(PairState<Real>) + sizeof(PairSums<MODE>) + 2 * sizeof(unsigned long long)) / 4) + 1;
+}
+
+// Blocks per SM of the batched pair kernel by pair states per lane.
+template <typename Real, int PPT> struct BatchMinBlocks { static constexpr int value = PPT == 1 ? 6 : PPT == 2 ? 4 : PPT == 4 ? 2 : 1; };
+template <int PPT> struct BatchMinBlocks<double, PPT> { static constexpr int value = 1; };
+
+template <typename Real> __device__ __forceinline__ const BgParams<Real> &req_params(const ReqDesc &D, int l);
+template <> __device__ __forceinline__ const BgParams<float> &req_params<float>(const ReqDesc &D, int l) { return D.bf[l]; }
+template <> __device__ __forceinline__ const BgParams<double> &req_params<double>(const ReqDesc &D, int l) { return D.bd[l]; }
+
+// ---------------------------------------------------------------------------
+// Persistent pair kernel.  Each warp works on one chunk at a time, taking
+// chunks from the queue until it is empty; a slice advances each warp at most
+// slice_iters event iterations (0: no limit), after which the warp stores its
+// chunk position, its PPT pair states and its sums and the next slice resumes
+// them.  Slicing changes no arithmetic and no order: results are the same for
+// every slice length.
+// ---------------------------------------------------------------------------
+template <typename Real, int MODE, int PPT>
+__global__ void __launch_bounds__(kThreads, (BatchMinBlocks<Real, PPT>::value))
+batch_pair_kernel(const __grid_constant__ BatchLaunch B)
+{
+    extern __shared__ unsigned int s_hist_all[];        // [warps][3 * max_nbins]
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const size_t gw = (size_t)blockIdx.x * kWarpsPerBlock + warp;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    uint32_t *lw = B.lane_words + gw * 32 + lane;
+    unsigned int *wh = s_hist_all + (size_t)warp * 3 * B.max_nbins;
+    WarpHdr *hdr = B.hdr + gw;
+
+    int valid = hdr->valid;
+    unsigned long long c = hdr->c;
+    unsigned long long next = hdr->next;                 // warp-uniform
+    int iters = 0;
+
+    Chunk ch;
+    const ReqDesc *D = nullptr;
+    LevelCtx<Real> L;
+    Bins bins;
+    bool coupled = false, per = false;
+    int nbins = 0;
+    unsigned long long end = 0;
+    PairState<Real> st[PPT];
+    bool active[PPT];
+    PairSums<MODE> mom;
+    unsigned long long ev_f_sum = 0, ev_c_sum = 0;
+
+    auto load_chunk = [&]() {
+        ch = B.queue[c & B.cap_mask];
+        D = &B.req[ch.req];
+        const int level = ch.level;
+        coupled = level > 0;
+        const BgParams<Real> &bp = req_params<Real>(*D, level);
+        L.bg.R = bp.R;
+        L.bg.invR = bp.invR;
+        L.bg.mu = bp.mu;
+        L.bg.sigma = bp.sigma;
+        L.bg.two_c2 = bp.two_c2;
+        L.bg.dt = bp.dt;
+        L.bg.Rdt = bp.Rdt;
+        L.bg.inv_Rdt = bp.inv_Rdt;
+        L.n = D->n_level[level];
+        L.M = D->M;
+        L.init = D->init;
+        L.word2 = (uint32_t)level << 24;
+        L.request = D->request;
+        per = D->periodic != 0;
+        nbins = D->nbins;
+        bins.lo = D->bd[level].lo;
+        bins.hi = D->bd[level].hi;
+        bins.h = D->h;
+        bins.lo_f = D->bf[level].lo;
+        bins.hi_f = D->bf[level].hi;
+        bins.inv_h_f = D->bf[level].inv_h;
+        bins.nbins = nbins;
+        bins.periodic = per;
+        end = ch.first + (unsigned long long)ch.count;
+        for (int i = lane; i < 3 * nbins; i += 32) wh[i] = 0u;
+        __syncwarp();
+    };
+    auto flush_hist = [&]() {
+        __syncwarp();
+        if (nbins > 0) {
+            unsigned long long *gh = B.hist + ((size_t)ch.req * kBL + ch.level) * 3 * B.max_nbins;
+            for (int i = lane; i < 3 * nbins; i += 32) {
+                const unsigned int v = wh[i];
+                if (v) atomicAdd(&gh[i], (unsigned long long)v);
+            }
+        }
+        __syncwarp();
+    };
+    auto finish = [&](int j) {
+        pair_drift<Real, 2>(st[j], L, coupled);
+        add_pair(mom, st[j].xf, st[j].xc, coupled, per);
+        ev_f_sum += st[j].k;
+        ev_c_sum += st[j].evc;
+        if (nbins > 0) {
+            const int bf = bins(st[j].xf);
+            if (bf >= 0) atomicAdd(&wh[bf], 1u);
+            if (coupled) {
+                const int bc = bins(st[j].xc);
+                if (bc >= 0) atomicAdd(&wh[nbins + bc], 1u);
+                if (bc >= 0 && bc == bf) atomicAdd(&wh[2 * nbins + bf], 1u);
+            }
+        }
+        active[j] = false;
+    };
+
+    if (valid) {                                      // resume the stored chunk
+        load_chunk();
+        int w = 0;
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) get_words(st[j], lw, stride, w);
+        get_words(mom, lw, stride, w);
+        get_words(ev_f_sum, lw, stride, w);
+        get_words(ev_c_sum, lw, stride, w);
+        uint32_t bits;
+        get_words(bits, lw, stride, w);
+#pragma unroll
+        for (int j = 0; j < PPT; ++j) active[j] = (bits >> j) & 1u;
+    }
+
+    for (;;) {
+        if (!valid) {
+            if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+            unsigned long long cn = 0;
+            if (lane == 0) cn = atomicAdd(&B.ctl->q_head, 1ull);
+            cn = __shfl_sync(kFullMask, cn, 0);
+            if (cn >= *(volatile unsigned long long *)&B.ctl->q_tail) break;
+            c = cn;
+            {
+                // a chunk of a cancelled request is dropped unprocessed
+                const Chunk peek = B.queue[c & B.cap_mask];
+                if (B.state[peek.req].status == 4) {
+                    if (lane == 0) atomicSub(&B.state[peek.req].pending, 1);
+                    continue;
+                }
+            }
+            load_chunk();
+            next = ch.first;
+            mom.zero();
+            ev_f_sum = 0;
+            ev_c_sum = 0;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                active[j] = false;
+                st[j].fresh = true;
+            }
+            valid = 1;
+        }
+        bool chunk_done = false;
+        for (;;) {
+            // the budget is checked before the refill, so a resumed slice runs
+            // exactly the sequence an unsliced run would
+            if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) {
+                const unsigned idle = __ballot_sync(kFullMask, !active[j]);
+                if (idle != 0u && next < end) {
+                    const unsigned rank = __popc(idle & ((1u << lane) - 1u));
+                    const unsigned long long cand = next + rank;
+                    if (!active[j] && cand < end) {
+                        active[j] = true;
+                        if (pair_start<Real, 2>(st[j], cand, L, B.keys, coupled)) finish(j);
+                    }
+                    next += __popc(idle);
+                    if (next > end) next = end;
+                }
+            }
+            bool any_local = false;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) any_local |= active[j];
+            if (!__any_sync(kFullMask, any_local)) {
+                if (next >= end) {
+                    chunk_done = true;
+                    break;
+                }
+                continue;
+            }
+#pragma unroll
+            for (int j = 0; j < PPT; ++j)
+                if (active[j] && pair_event<Real, 2>(st[j], L, B.keys, coupled)) finish(j);
+            ++iters;
+        }
+        if (!chunk_done) {
+            // budget spent inside the chunk: store it for the next slice
+            int w = 0;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) put_words(st[j], lw, stride, w);
+            put_words(mom, lw, stride, w);
+            put_words(ev_f_sum, lw, stride, w);
+            put_words(ev_c_sum, lw, stride, w);
+            uint32_t bits = 0;
+#pragma unroll
+            for (int j = 0; j < PPT; ++j) bits |= (active[j] ? 1u : 0u) << j;
+            put_words(bits, lw, stride, w);
+            flush_hist();
+            if (lane == 0) {
+                hdr->valid = 1;
+                hdr->c = c;
+                hdr->next = next;
+            }
+            return;
+        }
+        // one row of sums for this chunk (fixed reduction order)
+        mom.warp_reduce();
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            ev_f_sum += __shfl_down_sync(kFullMask, ev_f_sum, off);
+            ev_c_sum += __shfl_down_sync(kFullMask, ev_c_sum, off);
+        }
+        if (lane == 0) {
+            double *row = B.rows + (size_t)(c & B.cap_mask) * kPartialWords;
+#pragma unroll
+            for (int j = 0; j < 6; ++j) row[j] = mom.value(j);
+            row[6] = (double)ev_f_sum;
+            row[7] = (double)ev_c_sum;
+        }
+        flush_hist();
+        if (lane == 0) atomicSub(&B.state[ch.req].pending, 1);
+        valid = 0;
+    }
+    if (lane == 0) hdr->valid = 0;
+}
+
+// ---------------------------------------------------------------------------
+// Scheduler: one block per request slot.
+// ---------------------------------------------------------------------------
+__device__ long long chunk_size(long long count, double events_per_pair)
+{
+    double ch = 32.0 * kTargetIters / (events_per_pair > 1.0 ? events_per_pair : 1.0);
+    long long c = (long long)ch / kChunkQuantum * kChunkQuantum;
+    if (c < kChunkQuantum) c = kChunkQuantum;
+    if (c > kMaxChunkPairs) c = kMaxChunkPairs;
+    const long long min_for_cap = (count + kMaxChunksPerJob - 1) / kMaxChunksPerJob;
+    if (c < min_for_cap) c = (min_for_cap + kChunkQuantum - 1) / kChunkQuantum * kChunkQuantum;
+    return c;
+}
+
+__global__ void __launch_bounds__(kSchedThreads) batch_sched_kernel(const BatchLaunch B)
+{
+    const int r = blockIdx.x;
+    if (r >= B.n_slots) return;
+    ReqState &S = B.state[r];
+    const ReqDesc &D = B.req[r];
+    const int t = threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    __shared__ int s_status, s_pending;
+    __shared__ double s_var[kBL], s_cost[kBL];
+    __shared__ double s_max[kSchedThreads];
+    __shared__ long long s_target[kBL];
+    if (t == 0) {
+        s_status = S.status;
+        s_pending = S.pending;
+    }
+    __syncthreads();
+    const int status = s_status;
+    if (status == 0 || status == 3) {
+        if (t == 0) B.status_out[r] = status;
+        return;
+    }
+    if (status == 4) {                    // cancelled: free once its chunks have drained
+        if (t == 0) {
+            if (s_pending > 0) {
+                atomicAdd(&B.ctl->live, 1);
+                B.status_out[r] = 4;
+            } else {
+                S.status = 0;
+                B.status_out[r] = 0;
+            }
+        }
+        return;
+    }
+    if (status == 2 && s_pending > 0) {
+        if (t == 0) {
+            atomicAdd(&B.ctl->live, 1);
+            B.status_out[r] = 2;
+        }
+        return;
+    }
+    const int nl = D.L + 1;
+    if (status == 2) {
+        // finalize: fixed-order sums of each level's chunk rows (one warp per level)
+        for (int l = warp; l < nl; l += kSchedThreads / 32) {
+            const int nch = S.job_nch[l];
+            if (nch == 0) continue;
+            double v[kPartialWords];
+#pragma unroll
+            for (int j = 0; j < kPartialWords; ++j) v[j] = 0.0;
+            for (int i = lane; i < nch; i += 32) {
+                const double *row = B.rows + (size_t)((S.job_cb[l] + i) & B.cap_mask) * kPartialWords;
+#pragma unroll
+                for (int j = 0; j < kPartialWords; ++j) v[j] += row[j];
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int j = 0; j < kPartialWords; ++j) v[j] += __shfl_down_sync(kFullMask, v[j], off);
+            if (lane == 0) {
+                DevLevelStats &a = S.acc[l];
+                a.n += S.job_count[l];
+                a.sy += v[0];
+                a.sy2 += v[1];
+                a.sqf += v[2];
+                a.sqf2 += v[3];
+                a.sqc += v[4];
+                a.sqc2 += v[5];
+                a.events_f += (unsigned long long)llrint(v[6]);
+                a.events_c += (unsigned long long)llrint(v[7]);
+                S.job_nch[l] = 0;
+                S.job_count[l] = 0;
+            }
+        }
+        __syncthreads();
+        // controller (eqs. Nopt1/Noptj), FP64
+        for (int l = 0; l < nl; ++l) {
+            const double n = (double)S.acc[l].n;
+            double v = 0.0;
+            if (D.density && D.nbins > 0) {
+                const unsigned long long *H = B.hist + ((size_t)r * kBL + l) * 3 * B.max_nbins;
+                double m = 0.0;
+                for (int b = t; b < D.nbins; b += kSchedThreads) {
+                    const double sy = (double)H[b] - (double)H[D.nbins + b];
+                    const double sy2 = (double)H[b] + (double)H[D.nbins + b] - 2.0 * (double)H[2 * D.nbins + b];
+                    const double vb = n >= 2.0 ? (sy2 - sy * sy / n) / (n - 1.0) : 0.0;
+                    m = fmax(m, vb);
+                }
+                s_max[t] = m;
+                __syncthreads();
+                for (int stride = kSchedThreads / 2; stride > 0; stride >>= 1) {
+                    if (t < stride) s_max[t] = fmax(s_max[t], s_max[t + stride]);
+                    __syncthreads();
+                }
+                v = s_max[0] / (D.h * D.h);
+                __syncthreads();
+            } else if (n >= 2.0) {
+                v = (S.acc[l].sy2 - S.acc[l].sy * S.acc[l].sy / n) / (n - 1.0);
+            }
+            if (t == 0) {
+                s_var[l] = v > 0.0 ? v : 0.0;
+                s_cost[l] = n > 0.0 ? (double)(S.acc[l].events_f + S.acc[l].events_c) / n : 0.0;
+            }
+        }
+        __syncthreads();
+        if (t == 0) {
+            double est = 0.0, var = 0.0, total = 0.0;
+            for (int l = 0; l < nl; ++l) {
+                const double n = (double)S.acc[l].n;
+                if (n > 0.0) {
+                    est += S.acc[l].sy / n;
+                    var += s_var[l] / n;
+                }
+                total += sqrt(s_var[l] * s_cost[l]);
+                S.var_level[l] = s_var[l];
+                S.cost_level[l] = s_cost[l];
+            }
+            S.estimate = est;
+            S.variance = var;
+            bool grow = false;
+            for (int l = 0; l < nl; ++l) {
+                long long target = 0;
+                if (!D.use_fixed && s_var[l] > 0.0 && s_cost[l] > 0.0 && D.tol > 0.0) {
+                    const double tg = ceil(2.0 / (D.tol * D.tol) * sqrt(s_var[l] / s_cost[l]) * total);
+                    target = tg < 1e15 ? (long long)tg : 1000000000000000LL;
+                }
+                S.target[l] = target;
+                s_target[l] = target;
+                if (target > S.have[l]) grow = true;
+            }
+            if (!grow || D.use_fixed || S.rounds >= 64) {
+                S.status = 3;
+                s_status = 3;
+            } else {
+                S.rounds += 1;
+            }
+        }
+        __syncthreads();
+        if (s_status == 3) {
+            if (t == 0) B.status_out[r] = 3;
+            return;
+        }
+    } else if (t == 0) {
+        // admitted: warm-up round (or the fixed counts)
+        for (int l = 0; l < nl; ++l) {
+            const long long tg = D.use_fixed ? D.n_fixed[l] : (long long)D.n_warmup;
+            S.target[l] = tg;
+            s_target[l] = tg;
+        }
+    }
+    __syncthreads();
+    // plan: append this request's next round, finest level first
+    __shared__ long long s_cb[kBL];
+    __shared__ long long s_ch[kBL];
+    __shared__ int s_nch[kBL];
+    if (t == 0) {
+        int total_chunks = 0;
+        for (int l = nl - 1; l >= 0; --l) {
+            s_nch[l] = 0;
+            long long count = s_target[l] - S.have[l];
+            if (count <= 0) continue;
+            // a round schedules at most kMaxChunksPerJob chunks of at most
+            // kMaxChunkPairs pairs per level; the next round continues
+            const long long round_cap = (long long)kMaxChunksPerJob * kMaxChunkPairs;
+            if (count > round_cap) count = round_cap;
+            double epp = 1.0;
+            if (S.acc[l].n > 0) {
+                epp = (double)(S.acc[l].events_f + S.acc[l].events_c) / (double)S.acc[l].n;
+            } else {
+                const double nf = (double)D.n_level[l];
+                const double coll = (double)D.bd[l].Rdt * nf + 1.0;
+                epp = (coll < nf ? coll : nf) * (l > 0 ? 1.5 : 1.0);
+            }
+            const long long ch = chunk_size(count, epp);
+            const int nch = (int)((count + ch - 1) / ch);
+            s_ch[l] = ch;
+            s_nch[l] = nch;
+            s_cb[l] = (long long)atomicAdd(&B.ctl->q_tail, (unsigned long long)nch);
+            S.job_cb[l] = s_cb[l];
+            S.job_nch[l] = nch;
+            S.job_count[l] = count;
+            total_chunks += nch;
+        }
+        S.pending = total_chunks;
+        S.status = 2;
+        B.status_out[r] = 2;
+        atomicAdd(&B.ctl->live, 1);
+    }
+    __syncthreads();
+    for (int l = 0; l < nl; ++l) {
+        const int nch = s_nch[l];
+        for (int i = t; i < nch; i += kSchedThreads) {
+            const long long first = S.have[l] + (long long)i * s_ch[l];
+            long long cnt = S.have[l] + S.job_count[l] - first;
+            if (cnt > s_ch[l]) cnt = s_ch[l];
+            Chunk c;
+            c.req = r;
+            c.level = l;
+            c.first = (unsigned long long)first;
+            c.count = (int32_t)cnt;
+            c.pad_ = 0;
+            B.queue[(unsigned long long)(s_cb[l] + i) & B.cap_mask] = c;
+        }
+    }
+    __syncthreads();
+    if (t == 0)
+        for (int l = 0; l < nl; ++l)
+            if (s_nch[l] > 0) S.have[l] += S.job_count[l];
+}
+
+// Trims the queue head after a slice and publishes the loop condition.
+__global__ void batch_post_kernel(BatchCtl *ctl, int *live_out, cudaGraphConditionalHandle h, int use_graph)
+{
+    if (ctl->q_head > ctl->q_tail) ctl->q_head = ctl->q_tail;
+    ctl->iterations += 1;
+    const int live = ctl->live;
+    ctl->live = 0;
+    if (live_out) *live_out = live;
+    if (use_graph) cudaGraphSetConditional(h, live > 0 ? 1u : 0u);
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+struct BatchLayout {
+    size_t desc, state, queue, rows, hist, ctl, live, hdr, lanes, status, total;
+    unsigned long long cap;
+};
+
+static bool batch_cfg_ok(const mlkd_batch_config *c)
+{
+    if (!c) return false;
+    if (c->pairs_per_thread != 1 && c->pairs_per_thread != 2 && c->pairs_per_thread != 4 &&
+        c->pairs_per_thread != 8) return false;
+    if (c->substeps_per_launch < 0) return false;
+    if (c->max_requests < 1 || c->max_requests > 4096) return false;
+    if (c->max_nbins < 0 || c->max_nbins > 256) return false;
+    return true;
+}
+
+static BatchLayout batch_layout(const mlkd_batch_config *c)
+{
+    BatchLayout B;
+    unsigned long long need = (unsigned long long)c->max_requests * kBL * kMaxChunksPerJob;
+    unsigned long long cap = 1024;
+    while (cap < need) cap <<= 1;
+    B.cap = cap;
+    size_t off = arena_layout().total;
+    B.desc = off;  off = align_up(off + (size_t)c->max_requests * sizeof(ReqDesc));
+    B.state = off; off = align_up(off + (size_t)c->max_requests * sizeof(ReqState));
+    B.queue = off; off = align_up(off + (size_t)cap * sizeof(Chunk));
+    B.rows = off;  off = align_up(off + (size_t)cap * kPartialWords * sizeof(double));
+    B.hist = off;  off = align_up(off + (size_t)c->max_requests * kBL * 3 * (size_t)(c->max_nbins > 0 ? c->max_nbins : 1) * sizeof(unsigned long long));
+    B.ctl = off;   off = align_up(off + sizeof(BatchCtl));
+    B.live = off;  off = align_up(off + sizeof(int));
+    B.hdr = off;   off = align_up(off + (kMaxLanes / 32) * sizeof(WarpHdr));
+    const size_t words = (size_t)std::max(lane_words<float, kModeFP32Comp, kMaxPPT>(),
+                                          lane_words<double, kModeFP64, 1>());
+    B.lanes = off; off = align_up(off + words * kMaxLanes * sizeof(uint32_t));
+    B.status = off; off = align_up(off + (size_t)c->max_requests * sizeof(int32_t));
+    B.total = off;
+    return B;
+}
+
+struct BatchCache {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    mlkd_batch_config cfg{};
+    int mode = -1;
+    uint64_t seed = 0;
+    int n_slots = 0;
+    cudaStream_t stream = nullptr;
+};
+
+void batch_release(mlkd_context *ctx)
+{
+    if (!ctx || !ctx->batch) return;
+    if (ctx->batch->exec) cudaGraphExecDestroy(ctx->batch->exec);
+    if (ctx->batch->graph) cudaGraphDestroy(ctx->batch->graph);
+    delete ctx->batch;
+    ctx->batch = nullptr;
+}
+
+typedef void (*BatchKernelFn)(const BatchLaunch);
+
+static BatchKernelFn pick_batch(int mode, int ppt)
+{
+    switch (mode) {
+    case kModeFP64:
+        return batch_pair_kernel<double, kModeFP64, 1>;
+    case kModeFP32DY64:
+        return ppt == 1 ? batch_pair_kernel<float, kModeFP32DY64, 1>
+             : ppt == 2 ? batch_pair_kernel<float, kModeFP32DY64, 2>
+             : ppt == 4 ? batch_pair_kernel<float, kModeFP32DY64, 4>
+                        : batch_pair_kernel<float, kModeFP32DY64, 8>;
+    default:
+        return ppt == 1 ? batch_pair_kernel<float, kModeFP32Comp, 1>
+             : ppt == 2 ? batch_pair_kernel<float, kModeFP32Comp, 2>
+             : ppt == 4 ? batch_pair_kernel<float, kModeFP32Comp, 4>
+                        : batch_pair_kernel<float, kModeFP32Comp, 8>;
+    }
+}
+
+static void fill_desc(const mlkd_problem *p, const Derived &d, ReqDesc *D)
+{
+    std::memset(D, 0, sizeof(*D));
+    for (int l = 0; l <= p->L; ++l) {
+        PairLaunch P;
+        fill_launch(p, d, l, 0, 0, &P);
+        D->bd[l] = P.bd;
+        D->bf[l] = P.bf;
+        D->n_level[l] = P.n;
+        D->n_fixed[l] = p->n_fixed ? p->n_fixed[l] : 0;
+    }
+    D->tol = p->tol;
+    D->h = d.h;
+    D->L = p->L;
+    D->M = p->M;
+    D->init = p->init;
+    D->nbins = p->nbins;
+    D->periodic = d.periodic ? 1 : 0;
+    D->density = p->qoi == MLKD_QOI_DENSITY ? 1 : 0;
+    D->n_warmup = p->n_warmup;
+    D->use_fixed = p->n_fixed ? 1 : 0;
+    D->request = p->request;
+}
+
+static void fill_keys(uint64_t seed, PhiloxKeys *k)
+{
+    const uint32_t s0 = (uint32_t)seed, s1 = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k->k0[r] = s0 + (uint32_t)r * kWeylA;
+        k->k1[r] = s1 + (uint32_t)r * kWeylB;
+    }
+}
+
+static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_batch_config *cfg,
+                        int n_slots, uint64_t seed, BatchLaunch *B)
+{
+    std::memset(B, 0, sizeof(*B));
+    B->req = (const ReqDesc *)(ctx->arena + BL.desc);
+    B->state = (ReqState *)(ctx->arena + BL.state);
+    B->queue = (Chunk *)(ctx->arena + BL.queue);
+    B->rows = (double *)(ctx->arena + BL.rows);
+    B->hist = (unsigned long long *)(ctx->arena + BL.hist);
+    B->ctl = (BatchCtl *)(ctx->arena + BL.ctl);
+    B->hdr = (WarpHdr *)(ctx->arena + BL.hdr);
+    B->lane_words = (uint32_t *)(ctx->arena + BL.lanes);
+    B->status_out = (int32_t *)(ctx->arena + BL.status);
+    B->cap_mask = BL.cap - 1;
+    B->max_nbins = cfg->max_nbins > 0 ? cfg->max_nbins : 1;
+    B->slice_iters = cfg->substeps_per_launch;
+    B->n_slots = n_slots;
+    fill_keys(seed, &B->keys);
+}
+
+// Enqueues the loop body once: scheduler, pair slice, bookkeeping.
+static mlkd_status enqueue_body(mlkd_context *ctx, const BatchLaunch &B, int mode, int ppt, int grid,
+                                cudaGraphConditionalHandle h, int use_graph, int *live_dev,
+                                cudaStream_t s)
+{
+    batch_sched_kernel<<<B.n_slots, kSchedThreads, 0, s>>>(B);
+    MLKD_CUDA(cudaGetLastError());
+    const size_t smem = (size_t)kWarpsPerBlock * 3 * B.max_nbins * sizeof(unsigned int);
+    // host-loop form: the pair slice is timed like the per-level kernel
+    const bool timed = !use_graph && ctx->timing && ctx->events_made && ctx->pending < kTimingRing;
+    if (timed) MLKD_CUDA(cudaEventRecord(ctx->ev_start[ctx->pending], s));
+    pick_batch(mode, ppt)<<<grid, kThreads, smem, s>>>(B);
+    MLKD_CUDA(cudaGetLastError());
+    if (timed) MLKD_CUDA(cudaEventRecord(ctx->ev_stop[ctx->pending++], s));
+    batch_post_kernel<<<1, 1, 0, s>>>(B.ctl, live_dev, h, use_graph);
+    MLKD_CUDA(cudaGetLastError());
+    ctx->other_launches += 2;
+    if (!timed) ctx->launches += 1;
+    return MLKD_OK;
+}
+
+static mlkd_status batch_grid(mlkd_context *ctx, int mode, int ppt, int max_nbins, int *grid)
+{
+    int blocks = 0;
+    const size_t smem = (size_t)kWarpsPerBlock * 3 * (max_nbins > 0 ? max_nbins : 1) * sizeof(unsigned int);
+    MLKD_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, (const void *)pick_batch(mode, ppt),
+                                                           kThreads, smem));
+    *grid = ctx->sm_count * std::max(1, blocks);
+    if ((size_t)(*grid) * kThreads > kMaxLanes) *grid = (int)(kMaxLanes / kThreads);
+    return MLKD_OK;
+}
+
+static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
+                             const mlkd_batch_config *cfg, cudaStream_t s, mlkd_result *results)
+{
+    if (!ctx || !problems || n < 1 || !results || !batch_cfg_ok(cfg)) return MLKD_EINVAL;
+    if (ctx->server) return MLKD_EBUSY;
+    if (n > cfg->max_requests) return MLKD_EINVAL;
+    const BatchLayout BL = batch_layout(cfg);
+    if (ctx->arena_bytes < BL.total) return MLKD_ENOMEM;
+    std::vector<ReqDesc> desc(n);
+    int mode = -1;
+    uint64_t seed = 0;
+    for (int i = 0; i < n; ++i) {
+        Derived d;
+        if (!validate(&problems[i], &d)) return MLKD_EINVAL;
+        if (!problems[i].n_fixed && (!(problems[i].tol > 0.0) || problems[i].n_warmup < 2)) return MLKD_EINVAL;
+        if (problems[i].nbins > cfg->max_nbins) return MLKD_EINVAL;
+        if (i == 0) {
+            mode = d.mode;
+            seed = problems[i].seed;
+        } else if (d.mode != mode || problems[i].seed != seed) {
+            return MLKD_EINVAL;
+        }
+        fill_desc(&problems[i], d, &desc[i]);
+    }
+    const int ppt = mode == kModeFP64 ? 1 : cfg->pairs_per_thread;
+    const auto t0 = std::chrono::steady_clock::now();
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+
+    // reset the request slots, queue, histograms and control words
+    MLKD_CUDA(cudaMemcpyAsync(ctx->arena + BL.desc, desc.data(), n * sizeof(ReqDesc), cudaMemcpyHostToDevice, s));
+    MLKD_CUDA(cudaMemsetAsync(ctx->arena + BL.state, 0, (size_t)n * sizeof(ReqState), s));
+    std::vector<int32_t> admitted(n, 1);
+    for (int i = 0; i < n; ++i)
+        MLKD_CUDA(cudaMemcpyAsync(ctx->arena + BL.state + (size_t)i * sizeof(ReqState) + offsetof(ReqState, status),
+                                  &admitted[i], sizeof(int32_t), cudaMemcpyHostToDevice, s));
+    const size_t hist_bytes = (size_t)n * kBL * 3 * (size_t)(cfg->max_nbins > 0 ? cfg->max_nbins : 1) * sizeof(unsigned long long);
+    MLKD_CUDA(cudaMemsetAsync(ctx->arena + BL.hist, 0, hist_bytes, s));
+    MLKD_CUDA(cudaMemsetAsync(ctx->arena + BL.ctl, 0, sizeof(BatchCtl), s));
+    MLKD_CUDA(cudaMemsetAsync(ctx->arena + BL.hdr, 0, (kMaxLanes / 32) * sizeof(WarpHdr), s));
+
+    BatchLaunch B;
+    make_launch(ctx, BL, cfg, n, seed, &B);
+    int grid = 0;
+    mlkd_status st = batch_grid(ctx, mode, ppt, cfg->max_nbins, &grid);
+    if (st != MLKD_OK) return st;
+    int *live_dev = (int *)(ctx->arena + BL.live);
+
+    if (cfg->use_graph) {
+        BatchCache *bc = ctx->batch;
+        const bool reuse = bc && bc->exec && bc->mode == mode && bc->seed == seed && bc->n_slots == n &&
+                           std::memcmp(&bc->cfg, cfg, sizeof(*cfg)) == 0 && bc->stream == s;
+        if (!reuse) {
+            batch_release(ctx);
+            bc = new (std::nothrow) BatchCache;
+            if (!bc) return MLKD_ENOMEM;
+            ctx->batch = bc;
+            cudaGraph_t g = nullptr;
+            MLKD_CUDA(cudaGraphCreate(&g, 0));
+            bc->graph = g;
+            cudaGraphConditionalHandle h;
+            MLKD_CUDA(cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault));
+            cudaGraphNodeParams cp = {};
+            cp.type = cudaGraphNodeTypeConditional;
+            cp.conditional.handle = h;
+            cp.conditional.type = cudaGraphCondTypeWhile;
+            cp.conditional.size = 1;
+            cudaGraphNode_t node;
+            MLKD_CUDA(cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &cp));
+            cudaGraph_t body = cp.conditional.phGraph_out[0];
+            cudaStream_t cs;
+            MLKD_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+            cudaError_t e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                                          cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                cudaStreamDestroy(cs);
+                return MLKD_ECUDA;
+            }
+            st = enqueue_body(ctx, B, mode, ppt, grid, h, 1, nullptr, cs);
+            cudaGraph_t captured = nullptr;
+            e = cudaStreamEndCapture(cs, &captured);
+            cudaStreamDestroy(cs);
+            if (st != MLKD_OK) return st;
+            if (e != cudaSuccess) return MLKD_ECUDA;
+            ctx->other_launches -= 2;
+            ctx->launches -= 1;   // the capture launched nothing
+            MLKD_CUDA(cudaGraphInstantiate(&bc->exec, g, 0));
+            bc->cfg = *cfg;
+            bc->mode = mode;
+            bc->seed = seed;
+            bc->n_slots = n;
+            bc->stream = s;
+        }
+        MLKD_CUDA(cudaGraphLaunch(bc->exec, s));
+    } else {
+        for (int it = 0; it < 1000000; ++it) {
+            st = enqueue_body(ctx, B, mode, ppt, grid, 0, 0, live_dev, s);
+            if (st != MLKD_OK) return st;
+            int live = 0;
+            MLKD_CUDA(cudaMemcpyAsync(&live, live_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+            MLKD_CUDA(cudaStreamSynchronize(s));
+            st = harvest_timing(ctx);
+            if (st != MLKD_OK) return st;
+            if (live == 0) break;
+        }
+    }
+
+    // results
+    BatchCtl hctl;
+    MLKD_CUDA(cudaMemcpyAsync(&hctl, ctx->arena + BL.ctl, sizeof(hctl), cudaMemcpyDeviceToHost, s));
+    std::vector<ReqState> hs(n);
+    MLKD_CUDA(cudaMemcpyAsync(hs.data(), ctx->arena + BL.state, (size_t)n * sizeof(ReqState), cudaMemcpyDeviceToHost, s));
+    std::vector<unsigned long long> hh;
+    if (cfg->max_nbins > 0) {
+        hh.resize(hist_bytes / sizeof(unsigned long long));
+        MLKD_CUDA(cudaMemcpyAsync(hh.data(), ctx->arena + BL.hist, hist_bytes, cudaMemcpyDeviceToHost, s));
+    }
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    if (cfg->use_graph) {
+        ctx->launches += (unsigned long long)hctl.iterations;
+        ctx->other_launches += 2ull * (unsigned long long)hctl.iterations;
+    }
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    const int NB = cfg->max_nbins > 0 ? cfg->max_nbins : 1;
+    for (int i = 0; i < n; ++i) {
+        mlkd_result *o = &results[i];
+        double *dens = o->density;
+        std::memset(o, 0, sizeof(*o));
+        o->density = dens;
+        const ReqState &S = hs[i];
+        const int nl = problems[i].L + 1;
+        o->estimate = S.estimate;
+        o->variance = S.variance;
+        o->n_levels = nl;
+        o->rounds = S.rounds;
+        for (int l = 0; l < nl; ++l) {
+            const DevLevelStats &a = S.acc[l];
+            o->lv[l].n = a.n;
+            o->lv[l].sy = a.sy;
+            o->lv[l].sy2 = a.sy2;
+            o->lv[l].sqf = a.sqf;
+            o->lv[l].sqf2 = a.sqf2;
+            o->lv[l].sqc = a.sqc;
+            o->lv[l].sqc2 = a.sqc2;
+            o->lv[l].events_f = a.events_f;
+            o->lv[l].events_c = a.events_c;
+            o->var_level[l] = S.var_level[l];
+            o->cost_level[l] = S.cost_level[l];
+        }
+        const int nb = problems[i].nbins;
+        if (dens && nb > 0) {
+            Derived d;
+            validate(&problems[i], &d);
+            for (int b = 0; b < nb; ++b) dens[b] = 0.0;
+            for (int l = 0; l < nl; ++l) {
+                const unsigned long long *H = hh.data() + ((size_t)i * kBL + l) * 3 * NB;
+                if (S.acc[l].n > 0)
+                    for (int b = 0; b < nb; ++b)
+                        dens[b] += ((double)H[b] - (double)H[nb + b]) / (double)S.acc[l].n;
+            }
+            for (int b = 0; b < nb; ++b) dens[b] /= d.h;
+        }
+        o->seconds = secs;
+    }
+    return MLKD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Serving form.
+// ---------------------------------------------------------------------------
+struct ServerReq {
+    mlkd_problem p;
+    std::vector<int64_t> n_fixed;
+    double t_submit = 0.0, t_done = 0.0;
+    int slot = -1;
+    int state = 0;              // 0 waiting, 1 admitted, 2 done, 3 cancel requested
+    mlkd_result result;
+    std::vector<double> density;
+};
+
+struct Server {
+    mlkd_context *ctx = nullptr;
+    mlkd_server_config cfg;
+    BatchLayout BL;
+    BatchLaunch B;
+    int mode = 0, ppt = 1, grid = 1;
+    cudaStream_t stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::thread th;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    bool stop = false;
+    int error = MLKD_OK;
+    uint64_t next_id = 1;
+    std::deque<uint64_t> waiting;
+    std::unordered_map<uint64_t, ServerReq> reqs;
+    std::vector<uint64_t> slot_req;     // request id per slot, 0 = free
+    std::vector<int32_t> slot_status;
+    mlkd_server_stats stats{};
+    std::chrono::steady_clock::time_point t0;
+
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+static mlkd_status server_admit(Server *S, uint64_t id, int slot)
+{
+    ServerReq &q = S->reqs[id];
+    Derived d;
+    validate(&q.p, &d);
+    ReqDesc desc;
+    fill_desc(&q.p, d, &desc);
+    char *base = S->ctx->arena;
+    MLKD_CUDA(cudaMemcpyAsync(base + S->BL.desc + (size_t)slot * sizeof(ReqDesc), &desc, sizeof(desc),
+                              cudaMemcpyHostToDevice, S->stream));
+    MLKD_CUDA(cudaMemsetAsync(base + S->BL.state + (size_t)slot * sizeof(ReqState), 0, sizeof(ReqState), S->stream));
+    const int32_t admitted = 1;
+    MLKD_CUDA(cudaMemcpyAsync(base + S->BL.state + (size_t)slot * sizeof(ReqState) + offsetof(ReqState, status),
+                              &admitted, sizeof(admitted), cudaMemcpyHostToDevice, S->stream));
+    const size_t nb = (size_t)(S->cfg.batch.max_nbins > 0 ? S->cfg.batch.max_nbins : 1);
+    MLKD_CUDA(cudaMemsetAsync(base + S->BL.hist + (size_t)slot * kBL * 3 * nb * sizeof(unsigned long long), 0,
+                              kBL * 3 * nb * sizeof(unsigned long long), S->stream));
+    q.slot = slot;
+    q.state = 1;
+    S->slot_req[slot] = id;
+    return MLKD_OK;
+}
+
+static mlkd_status server_collect(Server *S, int slot)
+{
+    const uint64_t id = S->slot_req[slot];
+    ServerReq &q = S->reqs[id];
+    char *base = S->ctx->arena;
+    ReqState st;
+    const size_t nb = (size_t)(S->cfg.batch.max_nbins > 0 ? S->cfg.batch.max_nbins : 1);
+    std::vector<unsigned long long> h(kBL * 3 * nb);
+    MLKD_CUDA(cudaMemcpyAsync(&st, base + S->BL.state + (size_t)slot * sizeof(ReqState), sizeof(st),
+                              cudaMemcpyDeviceToHost, S->stream));
+    if (q.p.nbins > 0)
+        MLKD_CUDA(cudaMemcpyAsync(h.data(), base + S->BL.hist + (size_t)slot * kBL * 3 * nb * sizeof(unsigned long long),
+                                  h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost, S->stream));
+    const int32_t freed = 0;
+    MLKD_CUDA(cudaMemcpyAsync(base + S->BL.state + (size_t)slot * sizeof(ReqState) + offsetof(ReqState, status),
+                              &freed, sizeof(freed), cudaMemcpyHostToDevice, S->stream));
+    MLKD_CUDA(cudaStreamSynchronize(S->stream));
+    mlkd_result &o = q.result;
+    std::memset(&o, 0, sizeof(o));
+    const int nl = q.p.L + 1;
+    o.estimate = st.estimate;
+    o.variance = st.variance;
+    o.n_levels = nl;
+    o.rounds = st.rounds;
+    for (int l = 0; l < nl; ++l) {
+        const DevLevelStats &a = st.acc[l];
+        o.lv[l].n = a.n;
+        o.lv[l].sy = a.sy;
+        o.lv[l].sy2 = a.sy2;
+        o.lv[l].sqf = a.sqf;
+        o.lv[l].sqf2 = a.sqf2;
+        o.lv[l].sqc = a.sqc;
+        o.lv[l].sqc2 = a.sqc2;
+        o.lv[l].events_f = a.events_f;
+        o.lv[l].events_c = a.events_c;
+        o.var_level[l] = st.var_level[l];
+        o.cost_level[l] = st.cost_level[l];
+    }
+    if (q.p.nbins > 0) {
+        Derived d;
+        validate(&q.p, &d);
+        const int nbq = q.p.nbins;
+        q.density.assign(nbq, 0.0);
+        for (int l = 0; l < nl; ++l) {
+            const unsigned long long *H = h.data() + (size_t)l * 3 * nb;
+            if (st.acc[l].n > 0)
+                for (int b = 0; b < nbq; ++b)
+                    q.density[b] += ((double)H[b] - (double)H[nbq + b]) / (double)st.acc[l].n;
+        }
+        for (int b = 0; b < nbq; ++b) q.density[b] /= d.h;
+    }
+    q.t_done = S->now();
+    o.seconds = q.t_done - q.t_submit;
+    q.state = 2;
+    q.slot = -1;
+    S->slot_req[slot] = 0;
+    return MLKD_OK;
+}
+
+static void server_loop(Server *S)
+{
+    cudaSetDevice(S->ctx->device);
+    const int n = S->cfg.batch.max_requests;
+    for (;;) {
+        int active = 0;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (S->stop) break;
+            // cancellations of admitted requests: mark the device slot
+            for (int slot = 0; slot < n; ++slot) {
+                const uint64_t id = S->slot_req[slot];
+                if (!id) continue;
+                ServerReq &q = S->reqs[id];
+                if (q.state == 3 && S->slot_status[slot] != 4) {
+                    const int32_t cancel = 4;
+                    if (cudaMemcpyAsync(S->ctx->arena + S->BL.state + (size_t)slot * sizeof(ReqState) +
+                                            offsetof(ReqState, status),
+                                        &cancel, sizeof(cancel), cudaMemcpyHostToDevice, S->stream) != cudaSuccess)
+                        S->error = MLKD_ECUDA;
+                    S->slot_status[slot] = 4;
+                }
+            }
+            // admission: free slots take waiting requests in arrival order
+            for (int slot = 0; slot < n && !S->waiting.empty(); ++slot) {
+                if (S->slot_req[slot]) continue;
+                const uint64_t id = S->waiting.front();
+                S->waiting.pop_front();
+                if (server_admit(S, id, slot) != MLKD_OK) S->error = MLKD_ECUDA;
+                S->slot_status[slot] = 1;
+                S->stats.admitted += 1;
+            }
+            for (int slot = 0; slot < n; ++slot) active += S->slot_req[slot] ? 1 : 0;
+            if (active == 0) {
+                S->cv_work.wait_for(lk, std::chrono::milliseconds(2));
+                continue;
+            }
+        }
+        const double t_it = S->now();
+        if (cudaGraphLaunch(S->exec, S->stream) != cudaSuccess ||
+            cudaMemcpyAsync(S->slot_status.data(), S->B.status_out, n * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+            cudaStreamSynchronize(S->stream) != cudaSuccess) {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->error = MLKD_ECUDA;
+            S->stop = true;
+            S->cv_done.notify_all();
+            break;
+        }
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stats.iterations += 1;
+        S->stats.busy_seconds += S->now() - t_it;
+        bool any_done = false;
+        for (int slot = 0; slot < n; ++slot) {
+            const uint64_t id = S->slot_req[slot];
+            if (!id) continue;
+            ServerReq &q = S->reqs[id];
+            if (S->slot_status[slot] == 3 && q.state == 1) {
+                if (server_collect(S, slot) != MLKD_OK) S->error = MLKD_ECUDA;
+                S->stats.completed += 1;
+                any_done = true;
+            } else if (S->slot_status[slot] == 0 && q.state == 3) {
+                S->slot_req[slot] = 0;           // cancelled and drained
+                S->reqs.erase(id);
+                S->stats.cancelled += 1;
+            } else if (S->slot_status[slot] == 3 && q.state == 3) {
+                // finished before the cancel reached it: free and drop
+                const int32_t freed = 0;
+                cudaMemcpyAsync(S->ctx->arena + S->BL.state + (size_t)slot * sizeof(ReqState) +
+                                    offsetof(ReqState, status),
+                                &freed, sizeof(freed), cudaMemcpyHostToDevice, S->stream);
+                cudaStreamSynchronize(S->stream);
+                S->slot_req[slot] = 0;
+                S->reqs.erase(id);
+                S->stats.cancelled += 1;
+            }
+        }
+        if (any_done) S->cv_done.notify_all();
+    }
+    cudaStreamSynchronize(S->stream);
+}
+
+void server_release(mlkd_context *ctx)
+{
+    if (!ctx || !ctx->server) return;
+    Server *S = ctx->server;
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->stop = true;
+    }
+    S->cv_work.notify_all();
+    if (S->th.joinable()) S->th.join();
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->cv_done.notify_all();
+    }
+    if (S->exec) cudaGraphExecDestroy(S->exec);
+    if (S->graph) cudaGraphDestroy(S->graph);
+    if (S->stream) cudaStreamDestroy(S->stream);
+    ctx->server = nullptr;
+    delete S;
+}
+
+static mlkd_status server_start(mlkd_context *ctx, const mlkd_server_config *cfg)
+{
+    if (!ctx || !cfg || !batch_cfg_ok(&cfg->batch)) return MLKD_EINVAL;
+    if (cfg->precision < MLKD_PREC_FP64 || cfg->precision > MLKD_PREC_FP32_COMP) return MLKD_EINVAL;
+    if (cfg->max_pending < 1) return MLKD_EINVAL;
+    if (ctx->server) return MLKD_EBUSY;
+    const BatchLayout BL = batch_layout(&cfg->batch);
+    if (ctx->arena_bytes < BL.total) return MLKD_ENOMEM;
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+    Server *S = new (std::nothrow) Server;
+    if (!S) return MLKD_ENOMEM;
+    S->ctx = ctx;
+    S->cfg = *cfg;
+    S->BL = BL;
+    S->mode = cfg->precision;
+    S->ppt = S->mode == kModeFP64 ? 1 : cfg->batch.pairs_per_thread;
+    S->slot_req.assign(cfg->batch.max_requests, 0);
+    S->slot_status.assign(cfg->batch.max_requests, 0);
+    S->t0 = std::chrono::steady_clock::now();
+    auto fail = [&](mlkd_status st) {
+        if (S->exec) cudaGraphExecDestroy(S->exec);
+        if (S->graph) cudaGraphDestroy(S->graph);
+        if (S->stream) cudaStreamDestroy(S->stream);
+        delete S;
+        return st;
+    };
+    if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(MLKD_ECUDA);
+    const int n = cfg->batch.max_requests;
+    if (cudaMemsetAsync(ctx->arena + BL.state, 0, (size_t)n * sizeof(ReqState), S->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->arena + BL.ctl, 0, sizeof(BatchCtl), S->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->arena + BL.hdr, 0, (kMaxLanes / 32) * sizeof(WarpHdr), S->stream) != cudaSuccess ||
+        cudaMemsetAsync(ctx->arena + BL.status, 0, (size_t)n * sizeof(int32_t), S->stream) != cudaSuccess)
+        return fail(MLKD_ECUDA);
+    make_launch(ctx, BL, &cfg->batch, n, cfg->seed, &S->B);
+    if (batch_grid(ctx, S->mode, S->ppt, cfg->batch.max_nbins, &S->grid) != MLKD_OK) return fail(MLKD_ECUDA);
+    // one iteration as a graph: scheduler, pair slice, bookkeeping
+    if (cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(MLKD_ECUDA);
+    int *live_dev = (int *)(ctx->arena + BL.live);
+    batch_sched_kernel<<<n, kSchedThreads, 0, S->stream>>>(S->B);
+    const size_t smem = (size_t)kWarpsPerBlock * 3 * S->B.max_nbins * sizeof(unsigned int);
+    pick_batch(S->mode, S->ppt)<<<S->grid, kThreads, smem, S->stream>>>(S->B);
+    batch_post_kernel<<<1, 1, 0, S->stream>>>(S->B.ctl, live_dev, 0, 0);
+    const cudaError_t le = cudaGetLastError();
+    if (cudaStreamEndCapture(S->stream, &S->graph) != cudaSuccess || le != cudaSuccess) return fail(MLKD_ECUDA);
+    if (cudaGraphInstantiate(&S->exec, S->graph, 0) != cudaSuccess) return fail(MLKD_ECUDA);
+    if (cudaStreamSynchronize(S->stream) != cudaSuccess) return fail(MLKD_ECUDA);
+    ctx->server = S;
+    S->th = std::thread(server_loop, S);
+    return MLKD_OK;
+}
+
+}  // namespace mlkd
+
+using namespace mlkd;
+
+extern "C" {
+
+size_t mlkd_batch_workspace_bytes(const mlkd_batch_config *cfg)
+{
+    if (!batch_cfg_ok(cfg)) return 0;
+    return batch_layout(cfg).total;
+}
+
+mlkd_status mlkd_estimate_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
+                                const mlkd_batch_config *cfg, void *stream, mlkd_result *results)
+{
+    return run_batch(ctx, problems, n, cfg, (cudaStream_t)stream, results);
+}
+
+mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
+                                const mlkd_batch_config *base, void *stream,
+                                mlkd_batch_config *best, double *seconds)
+{
+    if (!ctx || !base || !best || !batch_cfg_ok(base)) return MLKD_EINVAL;
+    if (ctx->server) return MLKD_EBUSY;
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<mlkd_result> res(n);
+    const int ppts[4] = {1, 2, 4, 8};
+    const int slices[4] = {16, 64, 256, 0};
+    double best_t = 1e300;
+    *best = *base;
+    cudaEvent_t e0, e1;
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+    MLKD_CUDA(cudaEventCreate(&e0));
+    MLKD_CUDA(cudaEventCreate(&e1));
+    mlkd_status st = MLKD_OK;
+    for (int a = 0; a < 4 && st == MLKD_OK; ++a) {
+        for (int b = 0; b < 4 && st == MLKD_OK; ++b) {
+            mlkd_batch_config c = *base;
+            c.pairs_per_thread = ppts[a];
+            c.substeps_per_launch = slices[b];
+            c.use_graph = 1;
+            for (int i = 0; i < n; ++i) res[i].density = nullptr;
+            st = run_batch(ctx, problems, n, &c, s, res.data());       // warm (instantiates)
+            if (st != MLKD_OK) break;
+            if (cudaEventRecord(e0, s) != cudaSuccess) { st = MLKD_ECUDA; break; }
+            st = run_batch(ctx, problems, n, &c, s, res.data());
+            if (st != MLKD_OK) break;
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                st = MLKD_ECUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (seconds) seconds[a * 4 + b] = ms * 1e-3;
+            if (ms * 1e-3 < best_t) {
+                best_t = ms * 1e-3;
+                *best = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+mlkd_status mlkd_server_start(mlkd_context *ctx, const mlkd_server_config *cfg)
+{
+    return server_start(ctx, cfg);
+}
+
+mlkd_status mlkd_submit(mlkd_context *ctx, const mlkd_problem *problem, uint64_t *req_id)
+{
+    if (!ctx || !problem || !req_id) return MLKD_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return MLKD_EINVAL;
+    Derived d;
+    if (!validate(problem, &d)) return MLKD_EINVAL;
+    if (problem->precision != S->cfg.precision || problem->seed != S->cfg.seed) return MLKD_EINVAL;
+    if (problem->nbins > S->cfg.batch.max_nbins) return MLKD_EINVAL;
+    if (!problem->n_fixed && (!(problem->tol > 0.0) || problem->n_warmup < 2)) return MLKD_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->error != MLKD_OK) return (mlkd_status)S->error;
+    if ((int)S->waiting.size() >= S->cfg.max_pending) {
+        S->stats.rejected += 1;
+        return MLKD_EBUSY;
+    }
+    const uint64_t id = S->next_id++;
+    ServerReq &q = S->reqs[id];
+    q.p = *problem;
+    if (problem->n_fixed) {
+        q.n_fixed.assign(problem->n_fixed, problem->n_fixed + problem->L + 1);
+        q.p.n_fixed = q.n_fixed.data();
+    }
+    q.t_submit = S->now();
+    S->waiting.push_back(id);
+    S->stats.submitted += 1;
+    *req_id = id;
+    S->cv_work.notify_one();
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_poll(mlkd_context *ctx, uint64_t req_id, int timeout_ms, mlkd_result *out)
+{
+    if (!ctx || !out) return MLKD_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return MLKD_ENOTFOUND;
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end() || it->second.state == 3) return MLKD_ENOTFOUND;
+    auto ready = [&]() {
+        auto j = S->reqs.find(req_id);
+        return j == S->reqs.end() || j->second.state == 2 || S->error != MLKD_OK || S->stop;
+    };
+    if (timeout_ms < 0) {
+        S->cv_done.wait(lk, ready);
+    } else if (timeout_ms > 0) {
+        S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), ready);
+    }
+    it = S->reqs.find(req_id);
+    if (it == S->reqs.end()) return MLKD_ENOTFOUND;
+    if (it->second.state != 2) {
+        if (S->error != MLKD_OK) return (mlkd_status)S->error;
+        return MLKD_ETIMEDOUT;
+    }
+    double *dens = out->density;
+    *out = it->second.result;
+    out->density = dens;
+    if (dens)
+        for (size_t b = 0; b < it->second.density.size(); ++b) dens[b] = it->second.density[b];
+    S->reqs.erase(it);
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_cancel(mlkd_context *ctx, uint64_t req_id)
+{
+    if (!ctx) return MLKD_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return MLKD_ENOTFOUND;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(req_id);
+    if (it == S->reqs.end()) return MLKD_ENOTFOUND;
+    ServerReq &q = it->second;
+    if (q.state == 0) {
+        for (auto w = S->waiting.begin(); w != S->waiting.end(); ++w)
+            if (*w == req_id) {
+                S->waiting.erase(w);
+                break;
+            }
+        S->reqs.erase(it);
+        S->stats.cancelled += 1;
+    } else if (q.state == 1) {
+        q.state = 3;                 // the scheduler thread frees the slot once drained
+    } else if (q.state == 2) {
+        S->reqs.erase(it);           // finished: drop the result
+        S->stats.cancelled += 1;
+    }
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_server_stats_get(mlkd_context *ctx, mlkd_server_stats *out)
+{
+    if (!ctx || !out) return MLKD_EINVAL;
+    Server *S = ctx->server;
+    if (!S) return MLKD_ENOTFOUND;
+    std::lock_guard<std::mutex> lk(S->mu);
+    *out = S->stats;
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_server_stop(mlkd_context *ctx)
+{
+    if (!ctx) return MLKD_EINVAL;
+    server_release(ctx);
+    return MLKD_OK;
+}
+
+}  // extern "C"

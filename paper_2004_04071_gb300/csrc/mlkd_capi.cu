@@ -8,24 +8,13 @@
 #include <mutex>
 #include <new>
 
-#include "mlkd_internal.h"
-#include "../../include/mlkd.h"
+#include "mlkd_host.h"
 
 using namespace mlkd;
 
-namespace {
-
-constexpr int kMaxBlocks = 4096;                  // grid cap of the pair kernel
-constexpr size_t kAlign = 256;
-constexpr uint32_t kWeylA = 0x9E3779B9u;         // Philox key increments (SC'11)
-constexpr uint32_t kWeylB = 0xBB67AE85u;
+namespace mlkd {
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
-
-// Arena layout (offsets in bytes).
-struct Layout {
-    size_t partials, tmp_stats, acc_stats, tmp_hist, acc_hist, control, total;
-};
 
 Layout arena_layout()
 {
@@ -40,15 +29,6 @@ Layout arena_layout()
     L.total = off;
     return L;
 }
-
-// Derived, validated description of a problem.
-struct Derived {
-    double R, sigma, mu;
-    long long n0;          // T / dt0
-    int mode;
-    bool periodic;
-    double lo, hi, h;
-};
 
 bool validate(const mlkd_problem *p, Derived *d)
 {
@@ -98,34 +78,9 @@ long long ipow(long long b, int e)
     return r;
 }
 
-}  // namespace
+}  // namespace mlkd
 
-constexpr int kTimingRing = 64;
-
-struct mlkd_context {
-    int device;
-    bool timing;
-    int pending;
-    cudaEvent_t ev_start[kTimingRing], ev_stop[kTimingRing];
-    bool events_made;
-    unsigned long long launches, other_launches;
-    double kernel_ms;
-    int sm_count;
-    char *arena;
-    size_t arena_bytes;
-    Layout L;
-    double *partials;
-    DevLevelStats *tmp_stats, *acc_stats;
-    unsigned long long *tmp_hist, *acc_hist;
-    DevControl *control;
-};
-
-namespace {
-
-#define MLKD_CUDA(call)                                  \
-    do {                                                 \
-        if ((call) != cudaSuccess) return MLKD_ECUDA;    \
-    } while (0)
+namespace mlkd {
 
 // Fills the kernel parameters of pairs [first, first+count) of `level`.
 void fill_launch(const mlkd_problem *p, const Derived &d, int level, uint64_t first, uint64_t count,
@@ -180,6 +135,10 @@ void fill_launch(const mlkd_problem *p, const Derived &d, int level, uint64_t fi
     f.inv_h = (float)b.inv_h;
 }
 
+}  // namespace mlkd
+
+namespace {
+
 // Grid of the pair kernel: enough warps for the pairs, at most one full wave
 // of resident blocks; each warp gets an equal contiguous chunk.
 mlkd_status choose_grid(mlkd_context *ctx, int mode, bool coupled, int nbins, uint64_t count,
@@ -198,9 +157,11 @@ mlkd_status choose_grid(mlkd_context *ctx, int mode, bool coupled, int nbins, ui
     return MLKD_OK;
 }
 
+}  // namespace
+
 // Adds the elapsed time of every recorded pair-kernel launch; the stream of
 // those launches has been synchronised by the caller.
-mlkd_status harvest_timing(mlkd_context *ctx)
+mlkd_status mlkd::harvest_timing(mlkd_context *ctx)
 {
     for (int i = 0; i < ctx->pending; ++i) {
         float ms = 0.0f;
@@ -211,6 +172,8 @@ mlkd_status harvest_timing(mlkd_context *ctx)
     ctx->pending = 0;
     return MLKD_OK;
 }
+
+namespace {
 
 // Enqueues one level run: pair kernel + fixed-order finalize (+ accumulation).
 mlkd_status enqueue_level(mlkd_context *ctx, const mlkd_problem *p, const Derived &d, int level,
@@ -314,6 +277,8 @@ mlkd_status mlkd_context_create(int device, void *arena, size_t arena_bytes, mlk
     c->launches = 0;
     c->other_launches = 0;
     c->kernel_ms = 0.0;
+    c->batch = nullptr;
+    c->server = nullptr;
     c->arena = (char *)arena;
     c->arena_bytes = arena_bytes;
     c->L = L;
@@ -331,6 +296,8 @@ void mlkd_context_destroy(mlkd_context *ctx)
 {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    mlkd::server_release(ctx);
+    mlkd::batch_release(ctx);
     if (ctx->events_made) {
         cudaDeviceSynchronize();
         for (int i = 0; i < kTimingRing; ++i) {

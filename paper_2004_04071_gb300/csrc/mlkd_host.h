@@ -1,0 +1,80 @@
+// mlkd_host.h -- host-side internals shared by the C ABI translation units:
+// the context over the caller's arena, problem validation and the launch
+// parameters of one level.
+#pragma once
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "mlkd_internal.h"
+#include "../../include/mlkd.h"
+
+namespace mlkd {
+
+constexpr int kMaxBlocks = 4096;                  // grid cap of the pair kernel
+constexpr size_t kAlign = 256;
+constexpr uint32_t kWeylA = 0x9E3779B9u;         // Philox key increments (SC'11)
+constexpr uint32_t kWeylB = 0xBB67AE85u;
+constexpr int kTimingRing = 64;
+
+// Arena layout of the base workspace (offsets in bytes).
+struct Layout {
+    size_t partials, tmp_stats, acc_stats, tmp_hist, acc_hist, control, total;
+};
+
+// Derived, validated description of a problem.
+struct Derived {
+    double R, sigma, mu;
+    long long n0;          // T / dt0
+    int mode;
+    bool periodic;
+    double lo, hi, h;
+};
+
+size_t align_up(size_t v);
+Layout arena_layout();
+bool validate(const mlkd_problem *p, Derived *d);
+long long ipow(long long b, int e);
+void fill_launch(const mlkd_problem *p, const Derived &d, int level, uint64_t first, uint64_t count,
+                 PairLaunch *P);
+
+struct BatchCache;   // instantiated batch graph (mlkd_batch.cu)
+struct Server;       // serving form (mlkd_batch.cu)
+
+}  // namespace mlkd
+
+struct mlkd_context;
+
+namespace mlkd {
+void batch_release(mlkd_context *ctx);   // frees the batch graph cache (host side)
+void server_release(mlkd_context *ctx);  // stops a running server
+mlkd_status harvest_timing(mlkd_context *ctx);
+}
+
+struct mlkd_context {
+    int device;
+    bool timing;
+    int pending;
+    cudaEvent_t ev_start[mlkd::kTimingRing], ev_stop[mlkd::kTimingRing];
+    bool events_made;
+    unsigned long long launches, other_launches;
+    double kernel_ms;
+    int sm_count;
+    char *arena;
+    size_t arena_bytes;
+    mlkd::Layout L;
+    double *partials;
+    mlkd::DevLevelStats *tmp_stats, *acc_stats;
+    unsigned long long *tmp_hist, *acc_hist;
+    mlkd::DevControl *control;
+    mlkd::BatchCache *batch;    // lazily created by the batched form
+    mlkd::Server *server;       // running serving form, or null
+};
+
+#define MLKD_CUDA(call)                                  \
+    do {                                                 \
+        if ((call) != cudaSuccess) return MLKD_ECUDA;    \
+    } while (0)

@@ -13,177 +13,9 @@
 #include <cfloat>
 
 #include "mlkd_internal.h"
+#include "mlkd_pair.cuh"
 
 namespace mlkd {
-
-namespace {
-
-constexpr unsigned kFull = 0xffffffffu;
-
-// ---------------------------------------------------------------------------
-// Per-lane sums of one launch: Y, Y^2, F(x_f), F(x_f)^2, F(x_c), F(x_c)^2.
-//   FP64 mode      : all six in FP64.
-//   FP32_DY64 mode : Y and Y^2 formed and summed in FP64 from the FP32 state;
-//                    the four F moments as compensated FP32 pairs.
-//   FP32_COMP mode : all six as compensated FP32 (sum, error) pairs.
-// Compensation is an error-free TwoSum per addition.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
-{
-    s = a + b;
-    const float bp = s - a;
-    e = (a - (s - bp)) + (b - bp);
-}
-
-struct CompF {
-    float s, c;
-    __device__ void zero() { s = 0.0f; c = 0.0f; }
-    __device__ void add(float x) {
-        float t, e;
-        two_sum(s, x, t, e);
-        s = t;
-        c += e;
-    }
-    __device__ void shfl_merge(int off) {
-        const float so = __shfl_down_sync(kFull, s, off);
-        const float co = __shfl_down_sync(kFull, c, off);
-        float t, e;
-        two_sum(s, so, t, e);
-        s = t;
-        c = c + co + e;
-    }
-    __device__ double value() const { return (double)s + (double)c; }
-};
-
-template <int MODE> struct PairSums;
-
-template <> struct PairSums<kModeFP64> {
-    double v[6];
-    __device__ void zero() {
-#pragma unroll
-        for (int j = 0; j < 6; ++j) v[j] = 0.0;
-    }
-    __device__ void warp_reduce() {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int j = 0; j < 6; ++j) v[j] += __shfl_down_sync(kFull, v[j], off);
-    }
-    __device__ double value(int j) const { return v[j]; }
-};
-
-template <> struct PairSums<kModeFP32DY64> {
-    double sy, sy2;
-    CompF q[4];
-    __device__ void zero() {
-        sy = 0.0;
-        sy2 = 0.0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) q[j].zero();
-    }
-    __device__ void warp_reduce() {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            sy += __shfl_down_sync(kFull, sy, off);
-            sy2 += __shfl_down_sync(kFull, sy2, off);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) q[j].shfl_merge(off);
-        }
-    }
-    __device__ double value(int j) const { return j == 0 ? sy : j == 1 ? sy2 : q[j - 2].value(); }
-};
-
-template <> struct PairSums<kModeFP32Comp> {
-    CompF q[6];
-    __device__ void zero() {
-#pragma unroll
-        for (int j = 0; j < 6; ++j) q[j].zero();
-    }
-    __device__ void warp_reduce() {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int j = 0; j < 6; ++j) q[j].shfl_merge(off);
-    }
-    __device__ double value(int j) const { return q[j].value(); }
-};
-
-// QoI of one finished pair (eq. mlmc-compact): F(x) = x^2 in free space or
-// (x mod 1)^2 on the periodic unit interval; Y = F(x_f) - F(x_c), with
-// x_f^2 - x_c^2 formed as (x_f - x_c)(x_f + x_c).
-__device__ __forceinline__ void add_pair(PairSums<kModeFP64> &ps, double xf, double xc, bool coupled,
-                                         bool per)
-{
-    const double mf = per ? xf - floor(xf) : xf;
-    const double mc = per ? xc - floor(xc) : xc;
-    const double Ff = mf * mf, Fc = coupled ? mc * mc : 0.0;
-    const double y = !coupled ? Ff : per ? Ff - Fc : (xf - xc) * (xf + xc);
-    ps.v[0] += y;
-    ps.v[1] += y * y;
-    ps.v[2] += Ff;
-    ps.v[3] += Ff * Ff;
-    ps.v[4] += Fc;
-    ps.v[5] += Fc * Fc;
-}
-
-__device__ __forceinline__ void add_pair(PairSums<kModeFP32DY64> &ps, float xf, float xc, bool coupled,
-                                         bool per)
-{
-    const float mf = per ? xf - floorf(xf) : xf;     // exact in FP32
-    const float mc = per ? xc - floorf(xc) : xc;
-    const double a = (double)mf, b = (double)mc;
-    const double y = !coupled ? a * a : per ? a * a - b * b : (a - b) * (a + b);
-    ps.sy += y;
-    ps.sy2 += y * y;
-    const float Ff = mf * mf, Fc = coupled ? mc * mc : 0.0f;
-    ps.q[0].add(Ff);
-    ps.q[1].add(Ff * Ff);
-    ps.q[2].add(Fc);
-    ps.q[3].add(Fc * Fc);
-}
-
-__device__ __forceinline__ void add_pair(PairSums<kModeFP32Comp> &ps, float xf, float xc, bool coupled,
-                                         bool per)
-{
-    const float mf = per ? xf - floorf(xf) : xf;
-    const float mc = per ? xc - floorf(xc) : xc;
-    const float Ff = mf * mf, Fc = coupled ? mc * mc : 0.0f;
-    const float y = !coupled ? Ff : per ? Ff - Fc : (xf - xc) * (xf + xc);
-    ps.q[0].add(y);
-    ps.q[1].add(y * y);
-    ps.q[2].add(Ff);
-    ps.q[3].add(Ff * Ff);
-    ps.q[4].add(Fc);
-    ps.q[5].add(Fc * Fc);
-}
-
-// Histogram bin of x: floor((x - lo)/h) inside [lo, hi), else -1; periodic
-// positions are first wrapped into [0, 1).  FP64 state uses the division in
-// FP64; FP32 state decides its bins in FP32.
-__device__ __forceinline__ int bin_of(double x, const PairLaunch &P)
-{
-    if (P.periodic) x = x - floor(x);
-    if (!(x >= P.lo && x < P.hi)) return -1;
-    const int b = (int)floor((x - P.lo) / P.h);
-    return b < P.nbins ? b : P.nbins - 1;
-}
-
-struct BinsF {
-    float lo, hi, inv_h;
-    int nbins;
-    bool periodic;
-    __device__ int operator()(float x) const {
-        if (periodic) x = x - floorf(x);
-        if (!(x >= lo && x < hi)) return -1;
-        const int b = (int)floorf((x - lo) * inv_h);
-        return b < nbins ? b : nbins - 1;
-    }
-};
-
-__device__ __forceinline__ int bin_any(double x, const PairLaunch &P, const BinsF &) { return bin_of(x, P); }
-__device__ __forceinline__ int bin_any(float x, const PairLaunch &, const BinsF &bf) { return bf(x); }
-
-}  // namespace
 
 template <typename Real> __device__ __forceinline__ const BgParams<Real> &level_params(const PairLaunch &P);
 template <> __device__ __forceinline__ const BgParams<float> &level_params<float>(const PairLaunch &P) { return P.bf; }
@@ -198,7 +30,7 @@ template <typename Real, int MODE, bool COUPLED>
 __global__ void __launch_bounds__(kThreads, MinBlocks<Real>::value)
 pair_kernel(const __grid_constant__ PairLaunch P)
 {
-    typedef Arith<Real> A;
+    constexpr int CPL = COUPLED ? 1 : 0;
     extern __shared__ unsigned int s_hist[];          // [3][nbins]
     __shared__ double s_red[kWarpsPerBlock][kPartialWords];
 
@@ -207,18 +39,31 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     if (nbins > 0) __syncthreads();
 
     const BgParams<Real> &bp = level_params<Real>(P);
-    Background<Real> bg;
-    bg.R = bp.R;
-    bg.invR = bp.invR;
-    bg.mu = bp.mu;
-    bg.sigma = bp.sigma;
-    bg.two_c2 = bp.two_c2;
-    bg.dt = bp.dt;
-    bg.Rdt = bp.Rdt;
-    bg.inv_Rdt = bp.inv_Rdt;
+    LevelCtx<Real> L;
+    L.bg.R = bp.R;
+    L.bg.invR = bp.invR;
+    L.bg.mu = bp.mu;
+    L.bg.sigma = bp.sigma;
+    L.bg.two_c2 = bp.two_c2;
+    L.bg.dt = bp.dt;
+    L.bg.Rdt = bp.Rdt;
+    L.bg.inv_Rdt = bp.inv_Rdt;
+    L.n = P.n;
+    L.M = P.M;
+    L.init = P.init;
+    L.word2 = P.word2;
+    L.request = P.request;
 
-    const int n = P.n;
-    const int M = P.M;
+    Bins bins;
+    bins.lo = P.lo;
+    bins.hi = P.hi;
+    bins.h = P.h;
+    bins.lo_f = P.bf.lo;
+    bins.hi_f = P.bf.hi;
+    bins.inv_h_f = P.bf.inv_h;
+    bins.nbins = nbins;
+    bins.periodic = P.periodic != 0;
+
     const int lane = threadIdx.x & 31;
     const unsigned long long warp_id =
         (unsigned long long)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
@@ -229,147 +74,67 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     if (w_end > end_all) w_end = end_all;
     unsigned long long next = w_begin;                 // warp-uniform
 
-    // pair state (registers)
     bool active = false;
     unsigned long long pair = 0;
-    uint32_t pair_lo = 0, word2 = 0;
-    Real xf = 0, vf = 0, qf = 0, xc = 0, vc = 0, qc = 0, num = 0, den = 0, chi_first = 0;
-    int i_f = 0, ic = 0, Ec = 0;
-    uint32_t k = 0, evc = 0;
-    bool fresh = true;
-
+    PairState<Real> st;
+    st.fresh = true;
     PairSums<MODE> mom;
     mom.zero();
-    BinsF binsf;
-    binsf.lo = P.bf.lo;
-    binsf.hi = P.bf.hi;
-    binsf.inv_h = P.bf.inv_h;
-    binsf.nbins = P.nbins;
-    binsf.periodic = P.periodic != 0;
     unsigned long long ev_f_sum = 0, ev_c_sum = 0;
 
-    // Alg. 1 final drift, QoI, sums and histogram of the finished pair.
+    // QoI, sums and histogram of the finished pair.
     auto finish_pair = [&]() {
-        if (i_f < n) xf = xf + vf * ((Real)(n - i_f) * bg.dt);
-        if (COUPLED && ic < n) xc = xc + vc * ((Real)(n - ic) * bg.dt);
-        add_pair(mom, xf, xc, COUPLED, P.periodic != 0);
-        ev_f_sum += k;
-        ev_c_sum += evc;
+        pair_drift<Real, CPL>(st, L, COUPLED);
+        add_pair(mom, st.xf, st.xc, COUPLED, P.periodic != 0);
+        ev_f_sum += st.k;
+        ev_c_sum += st.evc;
         if (nbins > 0) {
-            const int bf = bin_any(xf, P, binsf);
+            const int bf = bins(st.xf);
             if (bf >= 0) atomicAdd(&s_hist[bf], 1u);
             if (COUPLED) {
-                const int bc = bin_any(xc, P, binsf);
+                const int bc = bins(st.xc);
                 if (bc >= 0) atomicAdd(&s_hist[nbins + bc], 1u);
                 if (bc >= 0 && bc == bf) atomicAdd(&s_hist[2 * nbins + bf], 1u);
             }
         }
         if (P.dbg_xf) {
             const unsigned long long j = pair - P.first_pair;
-            P.dbg_xf[j] = (double)xf;
-            if (P.dbg_xc) P.dbg_xc[j] = COUPLED ? (double)xc : 0.0;
-            if (P.dbg_kf) P.dbg_kf[j] = (int32_t)k;
-            if (P.dbg_kc) P.dbg_kc[j] = (int32_t)evc;
+            P.dbg_xf[j] = (double)st.xf;
+            if (P.dbg_xc) P.dbg_xc[j] = COUPLED ? (double)st.xc : 0.0;
+            if (P.dbg_kf) P.dbg_kf[j] = (int32_t)st.k;
+            if (P.dbg_kc) P.dbg_kc[j] = (int32_t)st.evc;
         }
         active = false;
     };
 
-    // Alg. 1 / Alg. 2 initialisation: nu_0, E_0 (shared by both paths), x_0.
-    auto start_pair = [&](unsigned long long p) {
-        pair = p;
-        pair_lo = (uint32_t)p;
-        word2 = P.word2 ^ (uint32_t)(p >> 32);
-        const Draw<Real> d0 = draw<Real>(0u, pair_lo, word2, P.request, P.keys);
-        const Real x0 = P.init ? cosine_inverse<Real>(d0.u4) : Real(0);
-        xf = x0;
-        vf = bg.mu + bg.sigma * d0.nu;
-        qf = d0.E * bg.inv_Rdt;
-        i_f = 0;
-        k = 0;
-        if (COUPLED) {
-            xc = x0;
-            vc = vf;
-            qc = qf;
-            ic = 0;
-            evc = 0;
-            num = Real(0);
-            den = Real(0);
-            fresh = true;
-            if (qf < (Real)n) Ec = M * ((int)qf / M + 1);
-        }
-        active = true;
-        if (!(qf < (Real)n)) finish_pair();            // no collision before T
-    };
-
     for (;;) {
         // refill idle lanes from the warp's chunk
-        const unsigned idle = __ballot_sync(kFull, !active);
+        const unsigned idle = __ballot_sync(kFullMask, !active);
         if (idle != 0u && next < w_end) {
             const unsigned rank = __popc(idle & ((1u << lane) - 1u));
             const unsigned long long cand = next + rank;
-            if (!active && cand < w_end) start_pair(cand);
+            if (!active && cand < w_end) {
+                pair = cand;
+                active = true;
+                if (pair_start<Real, CPL>(st, cand, L, P.keys, COUPLED)) finish_pair();
+            }
             next += __popc(idle);
             if (next > w_end) next = w_end;
         }
-        if (!__any_sync(kFull, active)) {
+        if (!__any_sync(kFullMask, active)) {
             if (next >= w_end) break;
             continue;
         }
         if (!active) continue;
-
-        // ---- one fine KD event (Alg. 1 KineticDiffusionStep) ----
-        const Draw<Real> d = draw<Real>(k + 1u, pair_lo, word2, P.request, P.keys);
-        const int sq = (int)qf;                                   // floor: qf >= 0
-        const Real theta = bg.dt * ((Real)(sq + 1) - qf);         // eq. diffusive-time
-        const Real dv = bg.sigma * d.nu;                          // v_{k+1} - mu
-        const Real v1 = bg.mu + dv;
-        Real a, dd, hs, om;
-        bg.kd_coeffs(theta, dv, a, dd, hs, om);
-        xf = xf + vf * (qf * bg.dt) + (a + dd * d.chi);           // eq. position-update
-        i_f += sq + 1;                                            // eq. time-update
-        vf = v1;
-        qf = d.E * bg.inv_Rdt;                                    // eq. intinv (homogeneous)
-        ++k;
-
-        if (COUPLED) {
-            // Sec. 3.2 aggregation, streamed: this phase's chi with beta, and the
-            // new phase's nu with alpha if it collides inside the coarse step.
-            const Real bh2 = bg.beta_hat_sq(hs);
-            if (fresh) { chi_first = d.chi; fresh = false; }
-            num += A::sqrt_(bh2) * d.chi;
-            den += bh2;
-            if (qf < (Real)(Ec - i_f)) {
-                const Real ah = qf * bg.Rdt + om;                 // R tau' = R tau + R zeta
-                num += ah * d.nu;
-                den += ah * ah;
-            } else {
-                // coarse KD step with nu~ = nu_{kappa}, chi~ (eq. chi-update) and,
-                // after it, the coarse flight tau~ = fine collision - E_c
-                // (homogeneous eq. epsilon-update), carried in fine units.
-                const Real thc = bg.dt * ((Real)(Ec - ic) - qc);
-                Real ac, dc, hsc, omc;
-                bg.kd_coeffs(thc, dv, ac, dc, hsc, omc);
-                const Real chit = den > Real(0) ? num * A::rsqrt_(den) : chi_first;
-                xc = xc + vc * (qc * bg.dt) + (ac + dc * chit);
-                qc = qf - (Real)(Ec - i_f);
-                ic = Ec;
-                vc = v1;
-                ++evc;
-                if (qc < (Real)(n - ic)) Ec = M * ((ic + (int)qc) / M + 1);
-                num = Real(0);
-                den = Real(0);
-                fresh = true;
-            }
-        }
-        if (!(qf < (Real)(n - i_f))) finish_pair();
+        if (pair_event<Real, CPL>(st, L, P.keys, COUPLED)) finish_pair();
     }
 
     // ---- block reduction of the sums (fixed order) ----
     mom.warp_reduce();
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        ev_f_sum += __shfl_down_sync(kFull, ev_f_sum, off);
-        ev_c_sum += __shfl_down_sync(kFull, ev_c_sum, off);
+        ev_f_sum += __shfl_down_sync(kFullMask, ev_f_sum, off);
+        ev_c_sum += __shfl_down_sync(kFullMask, ev_c_sum, off);
     }
     const int warp = threadIdx.x >> 5;
     if (lane == 0) {
@@ -502,8 +267,10 @@ controller_kernel(const DevLevelStats *acc, const unsigned long long *hist_acc, 
         for (int l = 0; l < n_levels; ++l) {
             const double v = s_var[l], c = out->cost_level[l];
             long long target = 0;
-            if (v > 0.0 && c > 0.0 && tol > 0.0)
-                target = (long long)ceil(2.0 / (tol * tol) * sqrt(v / c) * total);
+            if (v > 0.0 && c > 0.0 && tol > 0.0) {
+                const double tg = ceil(2.0 / (tol * tol) * sqrt(v / c) * total);
+                target = tg < 1e15 ? (long long)tg : 1000000000000000LL;
+            }
             out->target[l] = target;
         }
         out->estimate = est;

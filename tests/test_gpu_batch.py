@@ -1,0 +1,174 @@
+"""Batched form (one persistent pair kernel over a device work queue, rounds
+scheduled per request on the device) against the per-level form and the
+oracle (GPU only)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import gpu_problem, oracle_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mk():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2004_04071_gb300 as mk
+    mk.lib()
+    return mk
+
+
+@pytest.fixture(scope="module")
+def ctx(mk):
+    cfg = mk.batch_config(max_requests=64, max_nbins=128)
+    c = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
+    yield c
+    c.close()
+
+
+def mixed_problems(precision, seed=5):
+    return [
+        dict(eps=0.5, T=0.5, dt0=0.1, M=2, L=3, qoi=0, init=0, nbins=0, tol=0.01, n_warmup=100,
+             seed=seed, request=0),
+        dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=5, qoi=1, init=1, nbins=32, lo=0.0, hi=1.0, tol=0.003,
+             n_warmup=100, seed=seed, request=1),
+        dict(eps=2.0, T=1.0, dt0=0.25, M=2, L=2, qoi=0, init=0, nbins=0, tol=0.02, n_warmup=100,
+             seed=seed, request=2),
+        dict(eps=0.3, T=1.0, dt0=0.5, M=2, L=3, qoi=2, init=1, nbins=16, lo=0.0, hi=1.0, tol=0.05,
+             n_warmup=100, seed=seed, request=3),
+        dict(eps=1e-3, T=1.0, dt0=0.5, M=2, L=6, qoi=1, init=1, nbins=0, tol=0.003, n_warmup=100,
+             seed=seed, request=4),
+        dict(W.TWO_LEVEL, seed=seed, request=5),
+    ]
+
+
+def test_batch_matches_per_level_fp64(mk, ctx):
+    ds = mixed_problems(mk.PREC_FP64)
+    probs = [gpu_problem(mk, d, precision=mk.PREC_FP64) for d in ds]
+    cfg = mk.batch_config(max_requests=64, max_nbins=128)
+    rb = ctx.estimate_batch(probs, cfg)
+    for d, p, b in zip(ds, probs, rb):
+        r = ctx.estimate(p)
+        assert [lv["n"] for lv in b.levels] == [lv["n"] for lv in r.levels], d
+        for lb, lr in zip(b.levels, r.levels):
+            assert lb["events_f"] == lr["events_f"] and lb["events_c"] == lr["events_c"]
+            assert lb["sy"] == pytest.approx(lr["sy"], rel=1e-12, abs=1e-12)
+        assert b.estimate == pytest.approx(r.estimate, rel=1e-12, abs=1e-14)
+        assert b.variance == pytest.approx(r.variance, rel=1e-10)
+        if p.nbins:
+            np.testing.assert_allclose(b.density, r.density, rtol=1e-12, atol=1e-12)
+
+
+def test_batch_fixed_counts_match_oracle(orc, mk, ctx):
+    d = dict(W.TWO_LEVEL)
+    ro = orc.estimate(oracle_problem(orc, d), threads=8)
+    p = gpu_problem(mk, d, precision=mk.PREC_FP64)
+    (rb,) = ctx.estimate_batch([p], mk.batch_config(max_requests=64, max_nbins=128))
+    assert [lv["n"] for lv in rb.levels] == [10_000, 2_000]
+    assert rb.estimate == pytest.approx(ro.estimate, rel=1e-12)
+    np.testing.assert_allclose(rb.density, ro.density, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_batch_fp32_close_to_per_level(mk, ctx, precision):
+    ds = mixed_problems(precision)
+    probs = [gpu_problem(mk, d, precision=precision) for d in ds]
+    rb = ctx.estimate_batch(probs, mk.batch_config(pairs_per_thread=2, max_requests=64, max_nbins=128))
+    for p, b in zip(probs, rb):
+        r = ctx.estimate(p)
+        nb = [lv["n"] for lv in b.levels]
+        nr = [lv["n"] for lv in r.levels]
+        assert all(abs(x - y) <= max(1, 1e-6 * y) for x, y in zip(nb, nr)), (nb, nr)
+        if nb == nr:
+            assert b.estimate == pytest.approx(r.estimate, rel=1e-6, abs=1e-9)
+        if p.tol > 0:
+            assert b.variance <= p.tol ** 2 / 2 * (1 + 1e-6)
+
+
+def test_batch_deterministic_and_graph_equals_host_loop(mk, ctx):
+    probs = [gpu_problem(mk, d, precision=1) for d in mixed_problems(1, seed=9)]
+    g = mk.batch_config(pairs_per_thread=1, substeps_per_launch=64, use_graph=1, max_requests=64,
+                        max_nbins=128)
+    h = mk.batch_config(pairs_per_thread=1, substeps_per_launch=64, use_graph=0, max_requests=64,
+                        max_nbins=128)
+    a = ctx.estimate_batch(probs, g)
+    b = ctx.estimate_batch(probs, g)
+    c = ctx.estimate_batch(probs, h)
+    for x, y, z in zip(a, b, c):
+        assert x.estimate == y.estimate == z.estimate
+        assert [lv["sy2"] for lv in x.levels] == [lv["sy2"] for lv in z.levels]
+
+
+@pytest.mark.parametrize("ppt,slice_", [(1, 16), (2, 0), (4, 256), (8, 64)])
+def test_batch_configs_agree(mk, ctx, ppt, slice_):
+    """Kernel variants with other pairs-per-thread are separate compilations
+    whose FP32 contractions may differ by an ulp per event: estimates agree to
+    FP32 rounding, event counts exactly."""
+    probs = [gpu_problem(mk, d, precision=2) for d in mixed_problems(2, seed=11)]
+    ref = ctx.estimate_batch(probs, mk.batch_config(pairs_per_thread=1, substeps_per_launch=256,
+                                                    max_requests=64, max_nbins=128))
+    got = ctx.estimate_batch(probs, mk.batch_config(pairs_per_thread=ppt, substeps_per_launch=slice_,
+                                                    max_requests=64, max_nbins=128))
+    for x, y in zip(ref, got):
+        if [lv["n"] for lv in x.levels] == [lv["n"] for lv in y.levels]:
+            assert x.estimate == pytest.approx(y.estimate, rel=1e-6, abs=1e-9)
+            for lx, ly in zip(x.levels, y.levels):
+                assert lx["events_f"] == ly["events_f"]
+
+
+def test_batch_estimates_meet_tolerance(mk, ctx):
+    """E[x(T)^2] requests across eps: |estimate - closed form| within 4.5
+    sigma of the reported statistical error (bias is zero for this QoI)."""
+    ds = []
+    for i, eps in enumerate((1.0, 0.3, 0.1, 0.03, 0.01)):
+        ds.append(dict(eps=eps, T=0.5, dt0=0.1, M=2, L=3, qoi=0, init=0, nbins=0, tol=0.005,
+                       n_warmup=100, seed=3, request=i))
+    probs = [gpu_problem(mk, d, precision=1) for d in ds]
+    for d, r in zip(ds, ctx.estimate_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))):
+        exact = W.msd_closed_form(d["eps"], d["T"])
+        assert abs(r.estimate - exact) < 4.5 * math.sqrt(r.variance) + 1e-12
+        assert r.variance <= d["tol"] ** 2 / 2 * (1 + 1e-6)
+
+
+def test_batch_rejects_invalid(mk, ctx):
+    cfg = mk.batch_config(max_requests=64, max_nbins=128)
+    a = gpu_problem(mk, mixed_problems(1)[0], precision=1)
+    b = gpu_problem(mk, mixed_problems(1)[2], precision=2)
+    with pytest.raises(mk.MlkdError):
+        ctx.estimate_batch([a, b], cfg)                      # mixed precision
+    c = gpu_problem(mk, dict(mixed_problems(1)[2], seed=99), precision=1)
+    with pytest.raises(mk.MlkdError):
+        ctx.estimate_batch([a, c], cfg)                      # different seeds
+    small = mk.batch_config(max_requests=64, max_nbins=8)
+    d = gpu_problem(mk, mixed_problems(1)[1], precision=1)   # 32 bins
+    with pytest.raises(mk.MlkdError):
+        ctx.estimate_batch([d], small)
+
+
+def test_slice_length_changes_nothing(mk, ctx):
+    """A chunk stored at the end of a slice and resumed in the next gives the
+    same sums bit for bit, whatever the slice length."""
+    probs = [gpu_problem(mk, d, precision=1) for d in mixed_problems(1, seed=17)]
+    runs = [ctx.estimate_batch(probs, mk.batch_config(pairs_per_thread=2, substeps_per_launch=S,
+                                                      max_requests=64, max_nbins=128))
+            for S in (0, 7, 64, 1000)]
+    for rs in runs[1:]:
+        for x, y in zip(runs[0], rs):
+            assert x.estimate == y.estimate and x.variance == y.variance
+            assert [lv["sy2"] for lv in x.levels] == [lv["sy2"] for lv in y.levels]
+            if x.density is not None:
+                assert np.array_equal(x.density, y.density)
+
+
+def test_autotune_picks_from_grid(mk, ctx):
+    probs = [gpu_problem(mk, d, precision=2) for d in mixed_problems(2, seed=13)[:3]]
+    best, secs = ctx.autotune_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))
+    assert best.pairs_per_thread in (1, 2, 4, 8)
+    assert best.substeps_per_launch in (16, 64, 256, 0)
+    assert all(s > 0 for s in secs)
+    assert min(secs) == pytest.approx(secs[[1, 2, 4, 8].index(best.pairs_per_thread) * 4 +
+                                          [16, 64, 256, 0].index(best.substeps_per_launch)])
