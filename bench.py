@@ -60,6 +60,14 @@ def parse():
                     help="batched persistent form (default) or the per-level form")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--workload", default="periodic",
+                    choices=["periodic", "twolevel", "precision", "batched64", "serving"],
+                    help="periodic: the headline (full periodic MLMC); the others measure the "
+                         "two-level, precision, batched and serving configurations")
+    ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
+    ap.add_argument("--time-limit", type=float, default=60.0,
+                    help="serving: stop waiting for results after this many seconds")
     return ap.parse_args()
 
 
@@ -75,6 +83,22 @@ def problems_for_rank(rank: int):
     Philox request ids): weak scaling, no data-path exchange."""
     return [W.periodic_problem(eps, seed=0, tol=TOL) | {"request": rank * 16 + i}
             for i, eps in enumerate(EPS_SET)]
+
+
+def reduce_over_ranks(maxima, sums):
+    """Max over ranks of `maxima` and sum of `sums` (the timed region and the
+    work); unchanged on one rank.  Uses the process group's own device."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return list(maxima), list(sums)
+    dev = (torch.device("cuda", torch.cuda.current_device()) if dist.get_backend() == "nccl"
+           else torch.device("cpu"))
+    t = torch.tensor(list(maxima), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e = torch.tensor(list(sums), dtype=torch.float64, device=dev)
+    dist.all_reduce(e, op=dist.ReduceOp.SUM)
+    return t.cpu().tolist(), e.cpu().tolist()
 
 
 class ClockSampler:
@@ -236,15 +260,7 @@ def run_gpu(args):
     rt = ctx.get_timing(reset=True)
     ctx.set_timing(False)
 
-    t_dev = dev_ms / 1e3
-    t_host = host_s
-    ev = float(events_total)
-    if world > 1:
-        t = torch.tensor([t_dev, t_host], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e = torch.tensor([ev], dtype=torch.float64, device=dev)
-        dist.all_reduce(e, op=dist.ReduceOp.SUM)
-        t_dev, t_host, ev = float(t[0]), float(t[1]), float(e[0])
+    (t_dev, t_host), (ev,) = reduce_over_ranks([dev_ms / 1e3, host_s], [float(events_total)])
 
     kernel_s = rt["pair_kernel_ms"] / 1e3
     algo_inst = fine * INST_PER_FINE_EVENT + coarse * INST_PER_COARSE_EVENT
@@ -367,12 +383,217 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+
+
+# ---------------------------------------------------------------------------
+# Secondary workloads (one JSON line each).
+# ---------------------------------------------------------------------------
+def _gpu_setup(args, slots=64, nbins=128, substeps=256):
+    import torch
+    import paper_2004_04071_gb300 as mk
+    torch.cuda.set_device(0)
+    cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=substeps, use_graph=1,
+                          max_requests=slots, max_nbins=nbins)
+    ctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
+    return torch, mk, ctx, cfg
+
+
+def _events(rs):
+    return sum(lv["events_f"] + lv["events_c"] for r in rs for lv in r.levels)
+
+
+def run_twolevel(args):
+    """Two-level free-space problem with N_0 = 10^4, N_1 = 2000: estimate,
+    density and events/s in each precision, against the oracle."""
+    torch, mk, ctx, cfg = _gpu_setup(args)
+    import oracle as O
+    d = dict(W.TWO_LEVEL)
+    out = {"metric": "two-level MLMC (eps=0.5, T=0.5, N=[1e4, 2e3]): estimate and events/s",
+           "unit": "events/s", "higher_is_better": True, "data": "synthetic", "variants": {}}
+    po = O.Problem(**{k: d[k] for k in ("eps", "T", "dt0", "M", "L", "qoi", "init", "nbins", "lo",
+                                        "hi", "seed")}, n_fixed=list(d["n_fixed"]))
+    t0 = time.perf_counter()
+    ro = O.estimate(po, threads=os.cpu_count() or 1)
+    t_cpu = time.perf_counter() - t0
+    exact = W.msd_closed_form(d["eps"], d["T"])
+    for name, prec in (("fp64", mk.PREC_FP64), ("fp32", mk.PREC_FP32_DY64), ("fp32comp", mk.PREC_FP32_COMP)):
+        p = mk.make_problem(precision=prec, **d)
+        for _ in range(args.warmup):
+            ctx.estimate(p)
+        ts = []
+        for _ in range(max(1, args.steps)):
+            t = time.perf_counter()
+            r = ctx.estimate(p)
+            ts.append(time.perf_counter() - t)
+        out["variants"][name] = {"estimate": r.estimate, "std": math.sqrt(r.variance),
+                                 "abs_err_vs_oracle": abs(r.estimate - ro.estimate),
+                                 "density_max_abs_diff_vs_oracle":
+                                     float(max(abs(a - b) for a, b in zip(r.density, ro.density))),
+                                 "seconds_median": statistics.median(ts),
+                                 "events_per_s": _events([r]) / statistics.median(ts)}
+    out.update({"closed_form": exact, "oracle_estimate": ro.estimate, "oracle_seconds": t_cpu,
+                "value": out["variants"]["fp32comp"]["events_per_s"]})
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def run_precision(args):
+    """Precision form: the two-level free-space geometry at eps = 1e-2,
+    tol = 1e-4, adaptive, in FP64, FP32 state with Y in FP64, and FP32 state
+    with compensated FP32 sums.  Per level: mean Y, Var Y and their
+    difference from the FP64 run; time to tolerance of each variant; the CPU
+    oracle on the first level's sample for the per-level mean."""
+    torch, mk, ctx, cfg = _gpu_setup(args)
+    d = W.precision_problem(seed=0)
+    res = {}
+    variants = (("fp64", mk.PREC_FP64), ("fp64_u24", mk.PREC_FP64_U24), ("fp32", mk.PREC_FP32_DY64),
+                ("fp32comp", mk.PREC_FP32_COMP))
+    for name, prec in variants:
+        p = mk.make_problem(precision=prec, **d)
+        ctx.estimate(p)                                  # warm the code paths
+        t = time.perf_counter()
+        r = ctx.estimate(p)
+        secs = time.perf_counter() - t
+        lv = [{"n": x["n"], "mean_Y": x["sy"] / x["n"],
+               "var_Y": (x["sy2"] - x["sy"] ** 2 / x["n"]) / (x["n"] - 1)} for x in r.levels]
+        res[name] = {"estimate": r.estimate, "variance": r.variance, "time_to_tolerance_s": secs,
+                     "levels": lv, "events": _events([r])}
+    # the same N_l and the same 24-bit random numbers in FP64 and FP32 state:
+    # the per-level differences are the FP32 arithmetic error alone
+    fixed = [x["n"] for x in res["fp64_u24"]["levels"]]
+    same_n = {}
+    for name, prec in variants:
+        r = ctx.estimate(mk.make_problem(precision=prec, n_fixed=fixed, **d))
+        same_n[name] = [{"mean_Y": x["sy"] / x["n"],
+                         "var_Y": (x["sy2"] - x["sy"] ** 2 / x["n"]) / (x["n"] - 1)} for x in r.levels]
+    for name in ("fp32", "fp32comp"):
+        res[name]["vs_fp64_same_stream_same_N"] = [
+            {"abs_diff_mean_Y": abs(a["mean_Y"] - b["mean_Y"]),
+             "rel_diff_mean_Y": abs(a["mean_Y"] - b["mean_Y"]) / abs(b["mean_Y"]) if b["mean_Y"] else None,
+             "rel_diff_var_Y": abs(a["var_Y"] - b["var_Y"]) / b["var_Y"] if b["var_Y"] else None}
+            for a, b in zip(same_n[name], same_n["fp64_u24"])]
+    exact = W.msd_closed_form(d["eps"], d["T"])
+    out = {"metric": "precision form (eps=1e-2, tol=1e-4): per-level mean/var of Y_l by precision",
+           "unit": "s (time to tolerance)", "higher_is_better": False, "data": "synthetic",
+           "closed_form": exact, "variants": res,
+           "value": res["fp32comp"]["time_to_tolerance_s"],
+           "speedup_fp32comp_vs_fp64": res["fp64"]["time_to_tolerance_s"] / res["fp32comp"]["time_to_tolerance_s"]}
+    try:
+        import oracle as O
+        t = time.perf_counter()
+        po = O.Problem(**{k: d[k] for k in ("eps", "T", "dt0", "M", "L", "qoi", "init", "seed")})
+        n1 = min(fixed[1], 2_000_000)
+        s1 = O.run_level(po, 1, 0, n1, threads=os.cpu_count() or 1)
+        s1g = ctx.run_level(mk.make_problem(precision=mk.PREC_FP64, **d), 1, 0, n1)
+        out["oracle_level1"] = {"pairs": n1, "mean_Y": s1.mean(), "var_Y": s1.var(),
+                                "gpu_fp64_mean_Y": s1g["sy"] / s1g["n"],
+                                "abs_diff": abs(s1.mean() - s1g["sy"] / s1g["n"]),
+                                "cpu_seconds": time.perf_counter() - t, "cores": os.cpu_count()}
+    except Exception as exc:  # the CPU column must not sink the GPU numbers
+        out["oracle_level1"] = {"failed": str(exc)}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def run_batched64(args):
+    """64 independent estimators (eps log-uniform in [1e-4, 1], tol in
+    [1e-4, 1e-2], 3..14 levels; half E[x^2] free space, half periodic) in one
+    persistent kernel under a CUDA graph, autotuned."""
+    torch, mk, ctx, cfg = _gpu_setup(args, slots=64, nbins=1)
+    prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
+    dicts = [dict(r, seed=0) for r in W.batched_requests(64, seed=0)]
+    probs = [mk.make_problem(precision=prec, **dd) for dd in dicts]
+    # tune on a cheap sample of the mix: 16 of the requests at tol >= 2e-3
+    sample = [mk.make_problem(precision=prec, **dict(dd, tol=max(dd["tol"], 2e-3))) for dd in dicts[:16]]
+    best, secs = ctx.autotune_batch(sample, cfg)
+    ts, rs = [], None
+    for _ in range(args.warmup):
+        ctx.estimate_batch(probs, best)
+    for _ in range(max(1, args.steps)):
+        t = time.perf_counter()
+        rs = ctx.estimate_batch(probs, best)
+        ts.append(time.perf_counter() - t)
+    tm = statistics.median(ts)
+    ev = _events(rs)
+    npairs = [[lv["n"] for lv in r.levels] for r in rs]
+    ok = sum(1 for dd, r in zip(dicts, rs) if r.variance <= dd["tol"] ** 2 / 2 * (1 + 1e-9))
+    # each estimator alone (per-level form) for the comparison
+    t = time.perf_counter()
+    for p in probs:
+        ctx.estimate(p)
+    t_plain = time.perf_counter() - t
+    out = {"metric": "64 batched MLMC estimators: time to all tolerances", "value": tm, "unit": "s",
+           "higher_is_better": False, "data": "synthetic", "precision": args.precision,
+           "events_per_s": ev / tm, "events": ev, "best_config": best.as_dict(),
+           "autotune_seconds_ppt_major": secs, "met_tolerance": ok,
+           "levels_range": [min(len(x) for x in npairs), max(len(x) for x in npairs)],
+           "pairs_per_level_range": [min(min(x) for x in npairs), max(max(x) for x in npairs)],
+           "per_level_form_seconds": t_plain, "speedup_vs_per_level_form": t_plain / tm}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
+def run_serving(args):
+    """Poisson request stream (rate, count) of E[x^2] and 64-bin density
+    estimates with adaptive N_l, admitted into request slots as they free
+    up; latency from submit to result, p50/p99, estimates/s.  Requests still
+    running at the time limit are reported, not waited for."""
+    torch, mk, ctx, cfg = _gpu_setup(args, slots=64, nbins=64, substeps=2048)
+    prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
+    stream = W.serving_stream(args.requests, rate=args.rate, seed=0)
+    ctx.server_start(mk.server_config(cfg, precision=prec, seed=0, max_pending=1 << 20))
+    pending = {}
+    done = []
+    t0 = time.perf_counter()
+    i = 0
+    deadline = None
+    while True:
+        now = time.perf_counter() - t0
+        while i < len(stream) and stream[i]["arrival"] <= now:
+            d = dict(stream[i])
+            d.pop("arrival")
+            p = mk.make_problem(precision=prec, **d)
+            pending[ctx.submit(p)] = (d, p.nbins)
+            i += 1
+        for rid in list(pending):
+            rc, r = ctx.poll(rid, 0, nbins=pending[rid][1])
+            if rc == mk.MLKD_OK:
+                done.append((pending.pop(rid)[0], r))
+        if i >= len(stream) and not pending:
+            break
+        if i >= len(stream) and deadline is None:
+            deadline = time.perf_counter() + args.time_limit
+        if deadline is not None and time.perf_counter() > deadline:
+            break
+        time.sleep(0.0005)
+    wall = time.perf_counter() - t0
+    st = ctx.server_stats()
+    ctx.server_stop()
+    lat = sorted(r.seconds for _, r in done)
+    q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
+    ev = _events([r for _, r in done])
+    ok = sum(1 for d, r in done if r.variance <= d["tol"] ** 2 / 2 * (1 + 1e-9))
+    out = {"metric": "serving: p50/p99 latency and estimates/s (Poisson arrivals)",
+           "value": len(done) / wall, "unit": "estimates/s", "higher_is_better": True,
+           "data": "synthetic", "precision": args.precision, "requests": len(stream),
+           "rate": args.rate, "completed": len(done), "unfinished_at_limit": len(pending),
+           "latency_p50_s": q(0.5), "latency_p99_s": q(0.99), "wall_s": wall,
+           "events_per_s": ev / wall, "met_tolerance": ok, "server": st,
+           "note": "a 64-bin density at RMSE tol needs about 128/tol^2 level-0 samples under "
+                   "the per-bin reading; tight tolerances dominate the load"}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "periodic":
         run_gpu(args)
+    else:
+        {"twolevel": run_twolevel, "precision": run_precision, "batched64": run_batched64,
+         "serving": run_serving}[args.workload](args)
 
 
 if __name__ == "__main__":

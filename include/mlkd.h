@@ -71,15 +71,20 @@ typedef enum { MLKD_INIT_ORIGIN = 0, MLKD_INIT_COSINE = 1 } mlkd_init;
  * uniforms, two Philox blocks per fine event).  FP32_DY64: FP32 state, 24-bit
  * uniforms (one Philox block per fine event), Y_l formed and summed in FP64.
  * FP32_COMP: FP32 state, Y_l formed in FP32 and summed as compensated FP32
- * (sum, error) pairs.  Level statistics and the estimator are FP64 in every
+ * (sum, error) pairs.  FP64_U24: FP64 state and sums on the 24-bit stream of
+ * the FP32 modes (the same random numbers): the reference that isolates the
+ * FP32 arithmetic error.  Level statistics and the estimator are FP64 in every
  * mode. */
-typedef enum { MLKD_PREC_FP64 = 0, MLKD_PREC_FP32_DY64 = 1, MLKD_PREC_FP32_COMP = 2 } mlkd_prec;
+typedef enum { MLKD_PREC_FP64 = 0, MLKD_PREC_FP32_DY64 = 1, MLKD_PREC_FP32_COMP = 2,
+               MLKD_PREC_FP64_U24 = 3 } mlkd_prec;
 
 /* The paper's problem statement (Sec. 4.1) in the diffusive scaling.
  * Validation (MLKD_EINVAL otherwise): eps > 0, T > 0, dt0 > 0, T/dt0 a
  * positive integer (relative 1e-12), M in 2..64, L in 0..15, the finest level
  * has at most 2^30 fine steps, nbins in 0..1024 (>0 for DENSITY), lo < hi,
- * tol > 0 or n_fixed != NULL for mlkd_estimate, n_warmup >= 2. */
+ * tol > 0 or n_fixed != NULL for mlkd_estimate, n_warmup >= 2; a level set is
+ * strictly increasing within 0..L, ends at L, and no gap coarsens by more
+ * than 2^20. */
 typedef struct {
     double eps;            /* diffusive scaling: R = 1/eps^2, sigma = 1/eps    */
     double mu;             /* mean post-collision velocity mu_v (usually 0)    */
@@ -96,7 +101,13 @@ typedef struct {
     int32_t n_warmup;      /* warm-up pairs per level (the paper uses 100)     */
     uint32_t request;      /* request id: fourth Philox counter word           */
     uint64_t seed;         /* Philox key                                       */
-    const int64_t *n_fixed;/* host, length L+1: fixed N_l instead of tol, or NULL */
+    const int64_t *n_fixed;/* host, one count per estimator level: fixed N instead of tol, or NULL */
+    int32_t n_set;         /* 0: all levels 0..L; else the size J of level_set */
+    int32_t reserved_;
+    const int32_t *level_set; /* host, J strictly increasing levels ending at L, or NULL.
+                                 Estimator level j couples level level_set[j] with
+                                 level_set[j-1] (coarsening M^gap, Sec. 4.2); statistics,
+                                 n_fixed and results are indexed by j. */
 } mlkd_problem;
 
 /* Sums over the pairs of one level (eq. mlmc-compact):
@@ -169,6 +180,23 @@ MLKD_API mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *proble
 MLKD_API mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int level,
                              uint64_t first_pair, uint64_t n_pairs, void *stream, double *xf,
                              double *xc, int32_t *kf, int32_t *kc);
+
+/* Heuristic level selection (Alg. 3): given V[l] = Var(F(x_l)) for
+ * l = 0..L and Vd[l] = Var(Y_l) of the adjacent pair (l, l-1) for l = 1..L
+ * (Vd[0] ignored), takes the first l with Vd[l] < V[l] and the level below
+ * it, then adds every later level whose Vd falls below half the last added
+ * one; L is always included (the estimator's finest level).  Writes the set
+ * to set_out (room for L+1) and its size to *n_out.  Host only. */
+MLKD_API mlkd_status mlkd_level_select(const double *V, const double *Vd, int L, int32_t *set_out,
+                                       int32_t *n_out);
+
+/* Validation aid: the FP32 variate transforms of the pair kernel applied to
+ * n 32-bit Philox output words (device array `words`).  With the 24-bit
+ * uniform u = ((w >> 8) + 1) 2^-24 of each word it writes log u, sin 2 pi u and
+ * cos 2 pi u (device arrays of n floats; any may be NULL), exactly as the FP32
+ * kernels compute them for Box-Muller and -log u.  Synchronous. */
+MLKD_API mlkd_status mlkd_debug_transforms(const uint32_t *words, uint64_t n, float *log_u,
+                                           float *sin_2pi_u, float *cos_2pi_u, void *stream);
 
 /* Device time of the pair kernel.  When enabled, the context records a CUDA
  * event pair on the launching stream around every pair-kernel launch and adds

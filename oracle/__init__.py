@@ -59,7 +59,7 @@ class LevelDesc(ctypes.Structure):
     _fields_ = [("R", ctypes.c_double), ("mu", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("dt", ctypes.c_double), ("n", ctypes.c_int64), ("M", ctypes.c_int32),
                 ("level", ctypes.c_int32), ("init", ctypes.c_int32), ("recipe", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("request", ctypes.c_uint32)]
+                ("seed", ctypes.c_uint64), ("request", ctypes.c_uint32), ("coupled", ctypes.c_int32)]
 
 
 def lib():
@@ -141,6 +141,7 @@ class Problem:
     request: int = 0
     mu: float = 0.0
     n_fixed: list = field(default_factory=list)
+    level_set: list = field(default_factory=list)   # estimator levels (Sec. 4.2); empty: 0..L
 
     @property
     def R(self):
@@ -163,13 +164,22 @@ class Problem:
     def nsteps(self, level: int) -> int:
         return self.steps0() * self.M ** level
 
-    def level_desc(self, level: int) -> LevelDesc:
+    def estimator_levels(self):
+        """(fine level, coarsening to the previous estimator level) per
+        estimator level j: level_set[j] with M^(level_set[j] - level_set[j-1])."""
+        ls = list(self.level_set) if self.level_set else list(range(self.L + 1))
+        return [(l, self.M ** (l - ls[j - 1]) if j else self.M) for j, l in enumerate(ls)]
+
+    def level_desc(self, j: int) -> LevelDesc:
+        """Oracle description of estimator level j."""
+        level, m = self.estimator_levels()[j]
         d = LevelDesc()
         d.R, d.mu, d.sigma = self.R, self.mu, self.sigma
         d.dt = self.dt(level)
         d.n = self.nsteps(level)
-        d.M = self.M
+        d.M = m
         d.level = level
+        d.coupled = 1 if j > 0 else 0
         d.init = self.init
         d.recipe = self.recipe
         d.seed = self.seed
@@ -190,7 +200,8 @@ class Problem:
 # --------------------------------------------------------------------------
 def pairs(problem: Problem, level: int, first: int, count: int, threads: int = 1):
     """Final positions (x_l, x_{l-1}) and event counts of pairs
-    [first, first+count) of one level.  Level 0 is Alg. 1 (x_c = 0)."""
+    [first, first+count) of estimator level `level`.  Estimator level 0 is
+    Alg. 1 (x_c = 0)."""
     d = problem.level_desc(level)
     xf = np.zeros(count, np.float64)
     xc = np.zeros(count, np.float64)
@@ -222,9 +233,21 @@ def pairs(problem: Problem, level: int, first: int, count: int, threads: int = 1
     return xf, xc, ef, ec
 
 
+def _fine_desc(problem: Problem, level: int) -> LevelDesc:
+    """Single-path description of fine level `level` (any level, not an
+    estimator index)."""
+    d = LevelDesc()
+    d.R, d.mu, d.sigma = problem.R, problem.mu, problem.sigma
+    d.dt, d.n, d.M = problem.dt(level), problem.nsteps(level), problem.M
+    d.level = level
+    d.init, d.recipe, d.seed, d.request, d.coupled = (problem.init, problem.recipe, problem.seed,
+                                                      problem.request, 0)
+    return d
+
+
 def single_paths(problem: Problem, level: int, first: int, count: int, key_level: int = None):
     """Independent single-level (Alg. 1) paths at dt_level, keyed by key_level."""
-    d = problem.level_desc(level)
+    d = _fine_desc(problem, level)
     if key_level is not None:
         d.level = key_level
     x = np.zeros(count, np.float64)
@@ -245,6 +268,7 @@ def pair_injected(R, mu, sigma, dt, n, M, x0, nu, E, chi, level=1):
     assert len(nu) == len(E) and len(chi) >= len(nu) - 1
     d = LevelDesc()
     d.R, d.mu, d.sigma, d.dt, d.n, d.M, d.level = R, mu, sigma, dt, n, M, level
+    d.coupled = 1 if level != 0 else 0
     cap = 4096
     kappa = np.zeros(cap, np.int64)
     nu_t, E_t, chi_t, cc = (np.zeros(cap) for _ in range(4))
@@ -278,8 +302,9 @@ def coarse_draws(problem: Problem, level: int, first: int, count: int, cap: int)
 
 
 def stream_draws(problem: Problem, level: int, pair: int, K: int):
-    """(nu_0, E_0, u_x0) and (nu_k, E_k, chi_{k-1}) for k = 1..K of one stream."""
-    d = problem.level_desc(level)
+    """(nu_0, E_0, u_x0) and (nu_k, E_k, chi_{k-1}) for k = 1..K of one stream
+    (fine level `level`)."""
+    d = _fine_desc(problem, level)
     init = np.zeros(3)
     nu, E, chi = np.zeros(K), np.zeros(K), np.zeros(K)
     dd = ctypes.c_double
@@ -406,6 +431,29 @@ def level_variance(problem: Problem, s: LevelSums) -> float:
     return s.var()
 
 
+def level_select(V, Vd):
+    """Heuristic level selection (Alg. 3): the first level l whose
+    difference variance Vd[l] = Var(Q_l - Q_{l-1}) is below V[l] = Var(Q_l),
+    with the level below it; then each later level whose Vd is below half of
+    the last selected one.  The finest level L is always kept (the estimator
+    ends there).  Without any such l: the single level L."""
+    L = len(V) - 1
+    l = 1
+    while l <= L and Vd[l] > V[l]:
+        l += 1
+    if l > L:
+        return [L]
+    chosen = [l - 1, l]
+    vmin = Vd[l]
+    for k in range(l + 1, L + 1):
+        if Vd[k] < vmin / 2.0:
+            chosen.append(k)
+            vmin = Vd[k]
+    if chosen[-1] != L:
+        chosen.append(L)
+    return chosen
+
+
 def optimal_counts(V, C, tol):
     """N_j = ceil(2/tol^2 sqrt(V_j/C_j) sum_i sqrt(V_i C_i))  (eqs. Nopt1/Noptj)."""
     total = sum(math.sqrt(v * c) for v, c in zip(V, C))
@@ -429,20 +477,20 @@ class MLMCResult:
 def estimate(problem: Problem, threads: int = 1, max_rounds: int = 64) -> MLMCResult:
     """Adaptive MLMC on levels 0..L: warm-up, then grow N_l to the optimal
     counts until the statistical constraint holds."""
-    L = problem.L
-    sums = [LevelSums() for _ in range(L + 1)]
+    J = len(problem.estimator_levels())
+    sums = [LevelSums() for _ in range(J)]
     if problem.n_fixed:
-        for l in range(L + 1):
+        for l in range(J):
             sums[l].add(run_level(problem, l, 0, int(problem.n_fixed[l]), threads))
     else:
-        for l in range(L + 1):
+        for l in range(J):
             sums[l].add(run_level(problem, l, 0, problem.n_warmup, threads))
         for _ in range(max_rounds):
             V = [level_variance(problem, s) for s in sums]
             C = [s.cost() for s in sums]
             target = optimal_counts(V, C, problem.tol)
             grew = False
-            for l in range(L + 1):
+            for l in range(J):
                 if target[l] > sums[l].n:
                     sums[l].add(run_level(problem, l, sums[l].n, target[l] - sums[l].n, threads))
                     grew = True

@@ -472,12 +472,13 @@ typedef struct {
     double R, mu, sigma;
     double dt;       /* fine step of this level */
     int64_t n;       /* fine steps to T         */
-    int32_t M;
-    int32_t level;   /* 0: single path (Alg. 1); >=1: pair (Alg. 2) */
+    int32_t M;       /* coarsening of the pair's coarse path                    */
+    int32_t level;   /* fine level: Philox counter word 2                        */
     int32_t init;
     int32_t recipe;
     uint64_t seed;
     uint32_t request;
+    int32_t coupled; /* 0: single path (Alg. 1); 1: correlated pair (Alg. 2)    */
 } orc_level_desc;
 
 static void orc_make_stream(const orc_level_desc *d, uint64_t pair, orc_stream *s)
@@ -508,7 +509,7 @@ ORC_EXPORT int orc_pairs(const orc_level_desc *d, uint64_t first, int64_t count,
         orc_stream s;
         orc_make_stream(d, first + (uint64_t)j, &s);
         int rc;
-        if (d->level == 0) {
+        if (!d->coupled) {
             rc = orc_run_single(&P, &s, d->init, NULL, &xf[j], &ev_f[j]);
             xc[j] = 0.0;
             ev_c[j] = 0;
@@ -550,7 +551,7 @@ ORC_EXPORT int orc_pair_injected(const orc_level_desc *d, double x0, const doubl
     s.injected = 1; s.nu = nu; s.E = E; s.chi = chi; s.len = len;
     orc_trace tr = {cap, 0, kappa, nu_t, E_t, chi_t, coarse_collision};
     int rc;
-    if (d->level == 0) {
+    if (!d->coupled) {
         rc = orc_run_single(&P, &s, ORC_INIT_ORIGIN, &x0, xf, ev_f);
         *xc = 0.0; *ev_c = 0;
     } else {

@@ -26,7 +26,7 @@ MLKD_ENOTFOUND = -6
 
 QOI_X2, QOI_X2_PERIODIC, QOI_DENSITY = 0, 1, 2
 INIT_ORIGIN, INIT_COSINE = 0, 1
-PREC_FP64, PREC_FP32_DY64, PREC_FP32_COMP = 0, 1, 2
+PREC_FP64, PREC_FP32_DY64, PREC_FP32_COMP, PREC_FP64_U24 = 0, 1, 2, 3
 MAX_LEVELS = 16
 MAX_BINS = 1024
 
@@ -35,7 +35,8 @@ EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_estimate", "mlkd_debug_pairs", "mlkd_context_set_timing",
             "mlkd_context_get_timing", "mlkd_run_level_noalloc", "mlkd_batch_workspace_bytes",
             "mlkd_estimate_batch", "mlkd_autotune_batch", "mlkd_server_start", "mlkd_submit",
-            "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop"]
+            "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop",
+            "mlkd_debug_transforms", "mlkd_level_select"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -52,7 +53,8 @@ class Problem(ctypes.Structure):
                 ("precision", ctypes.c_int32), ("lo", ctypes.c_double), ("hi", ctypes.c_double),
                 ("tol", ctypes.c_double), ("n_warmup", ctypes.c_int32),
                 ("request", ctypes.c_uint32), ("seed", ctypes.c_uint64),
-                ("n_fixed", ctypes.POINTER(ctypes.c_int64))]
+                ("n_fixed", ctypes.POINTER(ctypes.c_int64)), ("n_set", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32), ("level_set", ctypes.POINTER(ctypes.c_int32))]
 
 
 class LevelStats(ctypes.Structure):
@@ -171,6 +173,11 @@ def lib():
         L.mlkd_server_stats_get.restype = ctypes.c_int
         L.mlkd_server_stop.argtypes = [vp]
         L.mlkd_server_stop.restype = ctypes.c_int
+        L.mlkd_debug_transforms.argtypes = [vp, u64, vp, vp, vp, vp]
+        L.mlkd_debug_transforms.restype = ctypes.c_int
+        L.mlkd_level_select.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int,
+                                        P(ctypes.c_int32), P(ctypes.c_int32)]
+        L.mlkd_level_select.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -189,7 +196,7 @@ def _check(rc, what):
 
 def make_problem(eps, T, dt0, M=2, L=1, qoi=QOI_X2, init=INIT_ORIGIN, nbins=0, lo=-3.0, hi=3.0,
                  tol=0.0, n_warmup=100, precision=PREC_FP64, seed=0, request=0, mu=0.0,
-                 n_fixed=None) -> Problem:
+                 n_fixed=None, level_set=None) -> Problem:
     p = Problem()
     p.eps, p.mu, p.T, p.dt0 = eps, mu, T, dt0
     p.M, p.L, p.qoi, p.init, p.nbins, p.precision = M, L, qoi, init, nbins, precision
@@ -199,7 +206,44 @@ def make_problem(eps, T, dt0, M=2, L=1, qoi=QOI_X2, init=INIT_ORIGIN, nbins=0, l
         arr = (ctypes.c_int64 * len(n_fixed))(*[int(v) for v in n_fixed])
         p._n_fixed_keep = arr
         p.n_fixed = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int64))
+    if level_set is not None:
+        ls = (ctypes.c_int32 * len(level_set))(*[int(v) for v in level_set])
+        p._level_set_keep = ls
+        p.level_set = ctypes.cast(ls, ctypes.POINTER(ctypes.c_int32))
+        p.n_set = len(level_set)
     return p
+
+
+def debug_transforms(words_dev, log_dev=None, sin_dev=None, cos_dev=None, stream=None):
+    """mlkd_debug_transforms on torch device tensors (uint32 words in an int32
+    tensor, float32 outputs)."""
+    vp = ctypes.c_void_p
+    ptr = lambda t: vp(t.data_ptr()) if t is not None else vp(0)
+    _check(lib().mlkd_debug_transforms(ptr(words_dev), words_dev.numel(), ptr(log_dev), ptr(sin_dev),
+                                       ptr(cos_dev), _stream_handle(stream)), "mlkd_debug_transforms")
+
+
+def level_select(V, Vd):
+    """mlkd_level_select (Alg. 3): level set from V_l = Var(F(x_l)) and
+    Vd_l = Var(Y_l) (Vd[0] unused)."""
+    L = len(V) - 1
+    v = (ctypes.c_double * (L + 1))(*[float(x) for x in V])
+    vd = (ctypes.c_double * (L + 1))(*[float(x) for x in Vd])
+    out = (ctypes.c_int32 * (L + 1))()
+    n = ctypes.c_int32()
+    _check(lib().mlkd_level_select(v, vd, L, out, ctypes.byref(n)), "mlkd_level_select")
+    return [int(out[i]) for i in range(n.value)]
+
+
+def level_variances(result):
+    """(V_l, Vd_l) of an all-levels estimate: variance of F on each level's
+    fine path and of the adjacent difference Y_l."""
+    V, Vd = [], []
+    for lv in result.levels:
+        n = lv["n"]
+        V.append((lv["sqf2"] - lv["sqf"] ** 2 / n) / (n - 1) if n > 1 else 0.0)
+        Vd.append((lv["sy2"] - lv["sy"] ** 2 / n) / (n - 1) if n > 1 else 0.0)
+    return V, Vd
 
 
 def workspace_bytes(problem: Problem) -> int:

@@ -41,6 +41,8 @@ struct ReqDesc {
     long long n_fixed[kBL];
     double tol, h;
     int32_t n_level[kBL];
+    int32_t M_level[kBL];       // coarsening to the previous estimator level
+    int32_t level_of[kBL];      // fine level of estimator level j (Philox counter word)
     int32_t L, M, init, nbins, periodic, density, n_warmup, use_fixed;
     uint32_t request;
     int32_t pad_;
@@ -189,9 +191,9 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         L.bg.Rdt = bp.Rdt;
         L.bg.inv_Rdt = bp.inv_Rdt;
         L.n = D->n_level[level];
-        L.M = D->M;
+        L.M = D->M_level[level];
         L.init = D->init;
-        L.word2 = (uint32_t)level << 24;
+        L.word2 = (uint32_t)D->level_of[level] << 24;
         L.request = D->request;
         per = D->periodic != 0;
         nbins = D->nbins;
@@ -290,7 +292,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                     const unsigned long long cand = next + rank;
                     if (!active[j] && cand < end) {
                         active[j] = true;
-                        if (pair_start<Real, 2>(st[j], cand, L, B.keys, coupled)) finish(j);
+                        if (pair_start<Real, 2, ModeRecipe<MODE>::value>(st[j], cand, L, B.keys, coupled)) finish(j);
                     }
                     next += __popc(idle);
                     if (next > end) next = end;
@@ -308,7 +310,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             }
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
-                if (active[j] && pair_event<Real, 2>(st[j], L, B.keys, coupled)) finish(j);
+                if (active[j] && pair_event<Real, 2, ModeRecipe<MODE>::value>(st[j], L, B.keys, coupled)) finish(j);
             ++iters;
         }
         if (!chunk_done) {
@@ -656,6 +658,8 @@ static BatchKernelFn pick_batch(int mode, int ppt)
     switch (mode) {
     case kModeFP64:
         return batch_pair_kernel<double, kModeFP64, 1>;
+    case kModeFP64U24:
+        return batch_pair_kernel<double, kModeFP64U24, 1>;
     case kModeFP32DY64:
         return ppt == 1 ? batch_pair_kernel<float, kModeFP32DY64, 1>
              : ppt == 2 ? batch_pair_kernel<float, kModeFP32DY64, 2>
@@ -672,17 +676,19 @@ static BatchKernelFn pick_batch(int mode, int ppt)
 static void fill_desc(const mlkd_problem *p, const Derived &d, ReqDesc *D)
 {
     std::memset(D, 0, sizeof(*D));
-    for (int l = 0; l <= p->L; ++l) {
+    for (int l = 0; l < d.J; ++l) {
         PairLaunch P;
         fill_launch(p, d, l, 0, 0, &P);
         D->bd[l] = P.bd;
         D->bf[l] = P.bf;
         D->n_level[l] = P.n;
+        D->M_level[l] = P.M;
+        D->level_of[l] = d.lev[l];
         D->n_fixed[l] = p->n_fixed ? p->n_fixed[l] : 0;
     }
     D->tol = p->tol;
     D->h = d.h;
-    D->L = p->L;
+    D->L = d.J - 1;                    // estimator levels 0..J-1
     D->M = p->M;
     D->init = p->init;
     D->nbins = p->nbins;
@@ -778,7 +784,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         }
         fill_desc(&problems[i], d, &desc[i]);
     }
-    const int ppt = mode == kModeFP64 ? 1 : cfg->pairs_per_thread;
+    const int ppt = (mode == kModeFP64 || mode == kModeFP64U24) ? 1 : cfg->pairs_per_thread;
     const auto t0 = std::chrono::steady_clock::now();
     MLKD_CUDA(cudaSetDevice(ctx->device));
 
@@ -883,7 +889,9 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         std::memset(o, 0, sizeof(*o));
         o->density = dens;
         const ReqState &S = hs[i];
-        const int nl = problems[i].L + 1;
+        Derived di;
+        validate(&problems[i], &di);
+        const int nl = di.J;
         o->estimate = S.estimate;
         o->variance = S.variance;
         o->n_levels = nl;
@@ -926,6 +934,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
 struct ServerReq {
     mlkd_problem p;
     std::vector<int64_t> n_fixed;
+    std::vector<int32_t> level_set;
     double t_submit = 0.0, t_done = 0.0;
     int slot = -1;
     int state = 0;              // 0 waiting, 1 admitted, 2 done, 3 cancel requested
@@ -1002,7 +1011,9 @@ static mlkd_status server_collect(Server *S, int slot)
     MLKD_CUDA(cudaStreamSynchronize(S->stream));
     mlkd_result &o = q.result;
     std::memset(&o, 0, sizeof(o));
-    const int nl = q.p.L + 1;
+    Derived dq;
+    validate(&q.p, &dq);
+    const int nl = dq.J;
     o.estimate = st.estimate;
     o.variance = st.variance;
     o.n_levels = nl;
@@ -1148,7 +1159,7 @@ void server_release(mlkd_context *ctx)
 static mlkd_status server_start(mlkd_context *ctx, const mlkd_server_config *cfg)
 {
     if (!ctx || !cfg || !batch_cfg_ok(&cfg->batch)) return MLKD_EINVAL;
-    if (cfg->precision < MLKD_PREC_FP64 || cfg->precision > MLKD_PREC_FP32_COMP) return MLKD_EINVAL;
+    if (cfg->precision < MLKD_PREC_FP64 || cfg->precision > MLKD_PREC_FP64_U24) return MLKD_EINVAL;
     if (cfg->max_pending < 1) return MLKD_EINVAL;
     if (ctx->server) return MLKD_EBUSY;
     const BatchLayout BL = batch_layout(&cfg->batch);
@@ -1160,7 +1171,7 @@ static mlkd_status server_start(mlkd_context *ctx, const mlkd_server_config *cfg
     S->cfg = *cfg;
     S->BL = BL;
     S->mode = cfg->precision;
-    S->ppt = S->mode == kModeFP64 ? 1 : cfg->batch.pairs_per_thread;
+    S->ppt = (S->mode == kModeFP64 || S->mode == kModeFP64U24) ? 1 : cfg->batch.pairs_per_thread;
     S->slot_req.assign(cfg->batch.max_requests, 0);
     S->slot_status.assign(cfg->batch.max_requests, 0);
     S->t0 = std::chrono::steady_clock::now();
@@ -1290,8 +1301,12 @@ mlkd_status mlkd_submit(mlkd_context *ctx, const mlkd_problem *problem, uint64_t
     ServerReq &q = S->reqs[id];
     q.p = *problem;
     if (problem->n_fixed) {
-        q.n_fixed.assign(problem->n_fixed, problem->n_fixed + problem->L + 1);
+        q.n_fixed.assign(problem->n_fixed, problem->n_fixed + d.J);
         q.p.n_fixed = q.n_fixed.data();
+    }
+    if (problem->n_set > 0) {
+        q.level_set.assign(problem->level_set, problem->level_set + problem->n_set);
+        q.p.level_set = q.level_set.data();
     }
     q.t_submit = S->now();
     S->waiting.push_back(id);

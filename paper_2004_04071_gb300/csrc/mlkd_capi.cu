@@ -40,7 +40,7 @@ bool validate(const mlkd_problem *p, Derived *d)
     if (p->L < 0 || p->L >= MLKD_MAX_LEVELS) return false;
     if (p->qoi < MLKD_QOI_X2 || p->qoi > MLKD_QOI_DENSITY) return false;
     if (p->init != MLKD_INIT_ORIGIN && p->init != MLKD_INIT_COSINE) return false;
-    if (p->precision < MLKD_PREC_FP64 || p->precision > MLKD_PREC_FP32_COMP) return false;
+    if (p->precision < MLKD_PREC_FP64 || p->precision > MLKD_PREC_FP64_U24) return false;
     if (p->nbins < 0 || p->nbins > MLKD_MAX_BINS) return false;
     if (p->qoi == MLKD_QOI_DENSITY && p->nbins == 0) return false;
     const double r = p->T / p->dt0;
@@ -49,7 +49,8 @@ bool validate(const mlkd_problem *p, Derived *d)
     // finest level: n0 * M^L fine steps; FP32 state needs exact step indices
     double nmax = n0;
     for (int l = 0; l < p->L; ++l) nmax *= p->M;
-    const double cap = p->precision == MLKD_PREC_FP64 ? 1073741824.0 : 16777216.0;
+    const bool fp64_state = p->precision == MLKD_PREC_FP64 || p->precision == MLKD_PREC_FP64_U24;
+    const double cap = fp64_state ? 1073741824.0 : 16777216.0;
     if (nmax > cap) return false;
     const double R = 1.0 / (p->eps * p->eps);
     if (!std::isfinite(R) || R <= 0.0) return false;
@@ -68,6 +69,31 @@ bool validate(const mlkd_problem *p, Derived *d)
         d->hi = p->hi;
     }
     d->h = p->nbins > 0 ? (d->hi - d->lo) / p->nbins : 1.0;
+    // estimator levels: all of 0..L, or a level set ending at L (Sec. 4.2)
+    if (p->n_set == 0) {
+        d->J = p->L + 1;
+        for (int j = 0; j <= p->L; ++j) {
+            d->lev[j] = j;
+            d->Mj[j] = p->M;
+        }
+    } else {
+        if (p->n_set < 1 || p->n_set > p->L + 1 || !p->level_set) return false;
+        d->J = p->n_set;
+        for (int j = 0; j < p->n_set; ++j) {
+            const int l = p->level_set[j];
+            if (l < 0 || l > p->L) return false;
+            if (j > 0 && l <= p->level_set[j - 1]) return false;
+            d->lev[j] = l;
+            d->Mj[j] = p->M;
+            if (j > 0) {
+                double mj = 1.0;
+                for (int g = p->level_set[j - 1]; g < l; ++g) mj *= p->M;
+                if (mj > 1048576.0) return false;
+                d->Mj[j] = (int)mj;
+            }
+        }
+        if (p->level_set[p->n_set - 1] != p->L) return false;
+    }
     return true;
 }
 
@@ -83,10 +109,11 @@ long long ipow(long long b, int e)
 namespace mlkd {
 
 // Fills the kernel parameters of pairs [first, first+count) of `level`.
-void fill_launch(const mlkd_problem *p, const Derived &d, int level, uint64_t first, uint64_t count,
+void fill_launch(const mlkd_problem *p, const Derived &d, int j, uint64_t first, uint64_t count,
                  PairLaunch *P)
 {
     std::memset(P, 0, sizeof(*P));
+    const int level = d.lev[j];                  // fine level of estimator level j
     const long long Ml = ipow(p->M, level);
     P->R = d.R;
     P->mu = d.mu;
@@ -96,7 +123,7 @@ void fill_launch(const mlkd_problem *p, const Derived &d, int level, uint64_t fi
     P->hi = d.hi;
     P->h = d.h;
     P->n = (int32_t)(d.n0 * Ml);
-    P->M = p->M;
+    P->M = d.Mj[j];
     P->periodic = d.periodic ? 1 : 0;
     P->init = p->init;
     P->nbins = p->nbins;
@@ -308,6 +335,43 @@ void mlkd_context_destroy(mlkd_context *ctx)
     delete ctx;
 }
 
+mlkd_status mlkd_level_select(const double *V, const double *Vd, int L, int32_t *set_out, int32_t *n_out)
+{
+    if (!V || !Vd || !set_out || !n_out || L < 1 || L >= MLKD_MAX_LEVELS) return MLKD_EINVAL;
+    // Alg. 3: the first level whose difference variance falls below its own
+    // variance, and the level below it
+    int l = 1;
+    while (l <= L && Vd[l] > V[l]) ++l;
+    int n = 0;
+    if (l > L) {                      // no decay anywhere: single-level estimate on L
+        set_out[n++] = L;
+        *n_out = n;
+        return MLKD_OK;
+    }
+    set_out[n++] = l - 1;
+    set_out[n++] = l;
+    double vmin = Vd[l];
+    for (int k = l + 1; k <= L; ++k) {
+        if (Vd[k] < vmin / 2.0) {
+            set_out[n++] = k;
+            vmin = Vd[k];
+        }
+    }
+    if (set_out[n - 1] != L) set_out[n++] = L;   // the estimator's finest level
+    *n_out = n;
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_debug_transforms(const uint32_t *words, uint64_t n, float *log_u, float *sin_2pi_u,
+                                  float *cos_2pi_u, void *stream)
+{
+    if (!words && n > 0) return MLKD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    MLKD_CUDA(launch_debug_transforms(words, n, log_u, sin_2pi_u, cos_2pi_u, s));
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    return MLKD_OK;
+}
+
 mlkd_status mlkd_context_set_timing(mlkd_context *ctx, int enable)
 {
     if (!ctx) return MLKD_EINVAL;
@@ -348,7 +412,7 @@ mlkd_status mlkd_run_level(mlkd_context *ctx, const mlkd_problem *problem, int l
 {
     Derived d;
     if (!ctx || !out || !validate(problem, &d)) return MLKD_EINVAL;
-    if (level < 0 || level > problem->L) return MLKD_EINVAL;
+    if (level < 0 || level >= d.J) return MLKD_EINVAL;
     if (first_pair + n_pairs < first_pair) return MLKD_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     MLKD_CUDA(cudaSetDevice(ctx->device));
@@ -376,7 +440,7 @@ mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int
 {
     Derived d;
     if (!ctx || !validate(problem, &d)) return MLKD_EINVAL;
-    if (level < 0 || level > problem->L) return MLKD_EINVAL;
+    if (level < 0 || level >= d.J) return MLKD_EINVAL;
     if (!xf && (xc || kf || kc)) return MLKD_EINVAL;   // xf gates the per-pair writes
     cudaStream_t s = (cudaStream_t)stream;
     MLKD_CUDA(cudaSetDevice(ctx->device));
@@ -398,7 +462,7 @@ mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *
     const auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = (cudaStream_t)stream;
     MLKD_CUDA(cudaSetDevice(ctx->device));
-    const int nl = problem->L + 1;
+    const int nl = d.J;
     const int nb = problem->nbins;
     MLKD_CUDA(cudaMemsetAsync(ctx->acc_stats, 0, nl * sizeof(DevLevelStats), s));
     if (nb > 0)
@@ -528,7 +592,7 @@ extern "C" mlkd_status mlkd_run_level_noalloc(const mlkd_problem *problem, int l
 {
     Derived d;
     if (!out || !validate(problem, &d)) return MLKD_EINVAL;
-    if (level < 0 || level > problem->L) return MLKD_EINVAL;
+    if (level < 0 || level >= d.J) return MLKD_EINVAL;
     if (first_pair + n_pairs < first_pair) return MLKD_EINVAL;
     if (problem->nbins > MLKD_NOALLOC_MAX_BINS) return MLKD_ENOMEM;
     int device = 0;

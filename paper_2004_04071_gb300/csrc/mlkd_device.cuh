@@ -199,19 +199,99 @@ template <typename Real>
 __device__ __forceinline__ Draw<Real> draw(uint32_t k, uint32_t pair_lo, uint32_t word2,
                                            uint32_t request, const PhiloxKeys &rk);
 
+// FP64 arithmetic on the 24-bit stream of the FP32 modes: one Philox block
+// per fine event, u = ((w >> 8) + 1) 2^-24 (exact in FP64).
+__device__ __forceinline__ Draw<double> draw_u24_fp64(uint32_t k, uint32_t pair_lo, uint32_t word2,
+                                                      uint32_t request, const PhiloxKeys &rk)
+{
+    const uint4 w = philox4x32_10(make_uint4(k, pair_lo, word2, request), rk);
+    const double u1 = (double)((w.x >> 8) + 1u) * 0x1p-24;
+    const double u2 = (double)((w.y >> 8) + 1u) * 0x1p-24;
+    const double u3 = (double)((w.z >> 8) + 1u) * 0x1p-24;
+    const double r = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    Draw<double> d;
+    d.nu = r * c;
+    d.chi = r * s;
+    d.E = -log(u3);
+    d.u4 = (double)((w.w >> 8) + 1u) * 0x1p-24;
+    return d;
+}
+
+// Draw of mode RECIPE: 0 the precision's own stream, 1 the 24-bit stream in FP64.
+template <typename Real, int RECIPE>
+__device__ __forceinline__ Draw<Real> draw_r(uint32_t k, uint32_t pair_lo, uint32_t word2,
+                                             uint32_t request, const PhiloxKeys &rk)
+{
+    if constexpr (RECIPE == 1) return draw_u24_fp64(k, pair_lo, word2, request, rk);
+    else return draw<Real>(k, pair_lo, word2, request, rk);
+}
+
+// log u for the 24-bit uniform u = n 2^-24, n = (w >> 8) + 1 in [1, 2^24].
+// Exponent from the leading zero count, mantissa m in [sqrt(1/2), sqrt(2)),
+// and the series log m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9),
+// s = (m - 1)/(m + 1), |s| <= 0.1716 (truncation below 1e-9).
+__device__ __forceinline__ float log_unit24(uint32_t w)
+{
+    const uint32_t n = (w >> 8) + 1u;
+    const int lz = __clz(n);
+    int e = 31 - lz;                                          // floor(log2 n)
+    float m = __uint_as_float(0x3F800000u | (((n << lz) << 1) >> 9));
+    if (m > 1.41421356f) {
+        m *= 0.5f;
+        e += 1;
+    }
+    const float s = __fdividef(m - 1.0f, m + 1.0f);
+    const float s2 = s * s;
+    float p = fmaf(s2, 0.111111111f, 0.142857143f);
+    p = fmaf(p, s2, 0.2f);
+    p = fmaf(p, s2, 0.333333333f);
+    const float lm = fmaf(2.0f * s * s2, p, 2.0f * s);
+    // log u = (e - 24) ln 2 + log m, with ln 2 split into two floats
+    const float k = (float)(e - 24);
+    return fmaf(k, 0.693145752f, fmaf(k, 1.42860677e-06f, lm));
+}
+
+// sin and cos of 2 pi u, u = n 2^-24: 4u = k + f with k the nearest quarter
+// turn (exact integer arithmetic), z = (pi/2) f in [-pi/4, pi/4], Taylor
+// polynomials through z^9 (sin) and z^10 (cos), then the quarter-turn
+// rotation.
+__device__ __forceinline__ void sincos_2pi_unit24(uint32_t w, float *sn, float *cs)
+{
+    const uint32_t n = (w >> 8) + 1u;
+    const uint32_t k = (n + (1u << 21)) >> 22;
+    const int r = (int)n - (int)(k << 22);
+    const float z = (float)r * 3.74507033e-07f;               // (pi/2) / 2^22
+    const float z2 = z * z;
+    float sp = fmaf(z2, 2.75573192e-06f, -1.98412698e-04f);
+    sp = fmaf(sp, z2, 8.33333333e-03f);
+    sp = fmaf(sp, z2, -1.66666667e-01f);
+    const float sz = fmaf(sp * z2, z, z);
+    float cp = fmaf(z2, -2.75573192e-07f, 2.48015873e-05f);
+    cp = fmaf(cp, z2, -1.38888889e-03f);
+    cp = fmaf(cp, z2, 4.16666667e-02f);
+    cp = fmaf(cp, z2, -0.5f);
+    const float cz = fmaf(cp, z2, 1.0f);
+    const uint32_t q = k & 3u;
+    const float a = (q & 1u) ? cz : sz;                       // |sin| part
+    const float b = (q & 1u) ? sz : cz;                       // |cos| part
+    *sn = (q & 2u) ? -a : a;
+    *cs = ((q + 1u) & 2u) ? -b : b;
+}
+
 template <>
 __device__ __forceinline__ Draw<float> draw<float>(uint32_t k, uint32_t pair_lo, uint32_t word2,
                                                    uint32_t request, const PhiloxKeys &rk)
 {
     const uint4 w = philox4x32_10(make_uint4(k, pair_lo, word2, request), rk);
-    const float u1 = unit24(w.x), u2 = unit24(w.y), u3 = unit24(w.z);
-    const float r = sqrtf(-2.0f * logf(u1));
+    const float r = sqrtf(-2.0f * log_unit24(w.x));
     float s, c;
-    sincospif(2.0f * u2, &s, &c);
+    sincos_2pi_unit24(w.y, &s, &c);
     Draw<float> d;
     d.nu = r * c;
     d.chi = r * s;
-    d.E = -logf(u3);
+    d.E = -log_unit24(w.z);
     d.u4 = unit24(w.w);
     return d;
 }

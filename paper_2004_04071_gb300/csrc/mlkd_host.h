@@ -32,6 +32,9 @@ struct Derived {
     int mode;
     bool periodic;
     double lo, hi, h;
+    int J;                 // estimator levels
+    int lev[MLKD_MAX_LEVELS];   // fine level of estimator level j
+    int Mj[MLKD_MAX_LEVELS];    // coarsening to the previous estimator level (j >= 1)
 };
 
 size_t align_up(size_t v);

@@ -13,7 +13,10 @@ constexpr int kThreads = 128;          // threads per block of the pair kernel
 constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int kPartialWords = 8;       // sy, sy2, sqf, sqf2, sqc, sqc2, ev_f, ev_c
 
-enum Mode { kModeFP64 = 0, kModeFP32DY64 = 1, kModeFP32Comp = 2 };
+enum Mode { kModeFP64 = 0, kModeFP32DY64 = 1, kModeFP32Comp = 2, kModeFP64U24 = 3 };
+
+// Random-number recipe of a mode: 1 = 24-bit uniforms in FP64 arithmetic.
+template <int MODE> struct ModeRecipe { static constexpr int value = MODE == kModeFP64U24 ? 1 : 0; };
 
 // Device copy of one level's sums; same layout as mlkd_level_stats.
 struct DevLevelStats {
@@ -82,6 +85,10 @@ struct DevControl {
 cudaError_t launch_controller(const DevLevelStats *acc, const unsigned long long *hist_acc,
                               int n_levels, int nbins, double h, int density_qoi, double tol,
                               DevControl *out, cudaStream_t stream);
+
+// FP32 variate transforms of n words (validation).
+cudaError_t launch_debug_transforms(const uint32_t *words, unsigned long long n, float *log_u,
+                                    float *sn, float *cs, cudaStream_t stream);
 
 // Adds hist [3*nbins] into acc [3*nbins] (integer).
 cudaError_t launch_hist_accumulate(const unsigned long long *hist, unsigned long long *acc,

@@ -116,7 +116,7 @@ pair_kernel(const __grid_constant__ PairLaunch P)
             if (!active && cand < w_end) {
                 pair = cand;
                 active = true;
-                if (pair_start<Real, CPL>(st, cand, L, P.keys, COUPLED)) finish_pair();
+                if (pair_start<Real, CPL, ModeRecipe<MODE>::value>(st, cand, L, P.keys, COUPLED)) finish_pair();
             }
             next += __popc(idle);
             if (next > w_end) next = w_end;
@@ -126,7 +126,7 @@ pair_kernel(const __grid_constant__ PairLaunch P)
             continue;
         }
         if (!active) continue;
-        if (pair_event<Real, CPL>(st, L, P.keys, COUPLED)) finish_pair();
+        if (pair_event<Real, CPL, ModeRecipe<MODE>::value>(st, L, P.keys, COUPLED)) finish_pair();
     }
 
     // ---- block reduction of the sums (fixed order) ----
@@ -205,6 +205,20 @@ finalize_kernel(const double *__restrict__ partials, int nblocks, long long n_pa
             acc->events_f += s.events_f;
             acc->events_c += s.events_c;
         }
+    }
+}
+
+__global__ void debug_transforms_kernel(const uint32_t *words, unsigned long long n, float *log_u,
+                                        float *sn, float *cs)
+{
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint32_t w = words[i];
+        if (log_u) log_u[i] = log_unit24(w);
+        float a, b;
+        sincos_2pi_unit24(w, &a, &b);
+        if (sn) sn[i] = a;
+        if (cs) cs[i] = b;
     }
 }
 
@@ -293,6 +307,9 @@ PairKernelFn pick(int mode, bool coupled)
     case kModeFP32DY64:
         return coupled ? pair_kernel<float, kModeFP32DY64, true>
                        : pair_kernel<float, kModeFP32DY64, false>;
+    case kModeFP64U24:
+        return coupled ? pair_kernel<double, kModeFP64U24, true>
+                       : pair_kernel<double, kModeFP64U24, false>;
     default:
         return coupled ? pair_kernel<float, kModeFP32Comp, true>
                        : pair_kernel<float, kModeFP32Comp, false>;
@@ -332,6 +349,15 @@ cudaError_t launch_controller(const DevLevelStats *acc, const unsigned long long
 {
     controller_kernel<<<1, 256, 0, stream>>>(acc, hist_acc, n_levels, nbins, h, density_qoi, tol,
                                              out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_debug_transforms(const uint32_t *words, unsigned long long n, float *log_u,
+                                    float *sn, float *cs, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned long long blocks = (n + 255) / 256;
+    debug_transforms_kernel<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, stream>>>(words, n, log_u, sn, cs);
     return cudaGetLastError();
 }
 

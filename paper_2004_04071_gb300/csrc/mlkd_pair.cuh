@@ -41,7 +41,7 @@ template <typename Real, int CPL>
 __device__ __forceinline__ bool pair_is_coupled(bool runtime) { return CPL == 2 ? runtime : CPL == 1; }
 
 // Returns true if the pair has no collision before T (already finished).
-template <typename Real, int CPL>
+template <typename Real, int CPL, int RECIPE = 0>
 __device__ __forceinline__ bool pair_start(PairState<Real> &st, unsigned long long p,
                                            const LevelCtx<Real> &L, const PhiloxKeys &keys,
                                            bool coupled_rt)
@@ -49,7 +49,7 @@ __device__ __forceinline__ bool pair_start(PairState<Real> &st, unsigned long lo
     const bool coupled = pair_is_coupled<Real, CPL>(coupled_rt);
     st.pair_lo = (uint32_t)p;
     st.word2 = L.word2 ^ (uint32_t)(p >> 32);
-    const Draw<Real> d0 = draw<Real>(0u, st.pair_lo, st.word2, L.request, keys);
+    const Draw<Real> d0 = draw_r<Real, RECIPE>(0u, st.pair_lo, st.word2, L.request, keys);
     const Real x0 = L.init ? cosine_inverse<Real>(d0.u4) : Real(0);
     st.xf = x0;
     st.vf = L.bg.mu + L.bg.sigma * d0.nu;
@@ -71,14 +71,14 @@ __device__ __forceinline__ bool pair_start(PairState<Real> &st, unsigned long lo
 }
 
 // One fine event; returns true when the pair has reached T.
-template <typename Real, int CPL>
+template <typename Real, int CPL, int RECIPE = 0>
 __device__ __forceinline__ bool pair_event(PairState<Real> &st, const LevelCtx<Real> &L,
                                            const PhiloxKeys &keys, bool coupled_rt)
 {
     typedef Arith<Real> A;
     const bool coupled = pair_is_coupled<Real, CPL>(coupled_rt);
     const Background<Real> &bg = L.bg;
-    const Draw<Real> d = draw<Real>(st.k + 1u, st.pair_lo, st.word2, L.request, keys);
+    const Draw<Real> d = draw_r<Real, RECIPE>(st.k + 1u, st.pair_lo, st.word2, L.request, keys);
     const int sq = (int)st.qf;                                  // floor: qf >= 0
     const Real theta = bg.dt * ((Real)(sq + 1) - st.qf);        // eq. diffusive-time
     const Real dv = bg.sigma * d.nu;                            // v_{k+1} - mu
@@ -210,6 +210,8 @@ template <> struct PairSums<kModeFP32DY64> {
     }
     __device__ double value(int j) const { return j == 0 ? sy : j == 1 ? sy2 : q[j - 2].value(); }
 };
+
+template <> struct PairSums<kModeFP64U24> : PairSums<kModeFP64> {};
 
 template <> struct PairSums<kModeFP32Comp> {
     CompF q[6];

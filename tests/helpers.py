@@ -12,6 +12,8 @@ def oracle_problem(orc, d, recipe=None, **over):
         kw["n_fixed"] = list(d["n_fixed"])
     if recipe is not None:
         kw["recipe"] = recipe
+    if d.get("level_set"):
+        kw["level_set"] = list(d["level_set"])
     return orc.Problem(**kw)
 
 
@@ -20,6 +22,8 @@ def gpu_problem(mk, d, precision=0, **over):
     kw = {k: d[k] for k in ORACLE_KEYS if k in d}
     if "n_fixed" in d:
         kw["n_fixed"] = d["n_fixed"]
+    if d.get("level_set"):
+        kw["level_set"] = d["level_set"]
     return mk.make_problem(precision=precision, **kw)
 
 

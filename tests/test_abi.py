@@ -55,8 +55,8 @@ def test_binding_names_match_header(built):
 
 def test_struct_layouts_match_header(built):
     import paper_2004_04071_gb300 as mk
-    # mlkd_problem: 4 doubles, 6 int32, 3 doubles, 2 x 32-bit, u64, pointer
-    assert ctypes.sizeof(mk.Problem) == 4 * 8 + 6 * 4 + 3 * 8 + 8 + 8 + 8
+    # mlkd_problem: 4 doubles, 6 int32, 3 doubles, 2 x 32-bit, u64, pointer, 2 int32, pointer
+    assert ctypes.sizeof(mk.Problem) == 4 * 8 + 6 * 4 + 3 * 8 + 8 + 8 + 8 + 8 + 8
     assert ctypes.sizeof(mk.LevelStats) == 8 + 6 * 8 + 2 * 8
 
 
@@ -80,3 +80,17 @@ def test_status_strings(built):
     import paper_2004_04071_gb300 as mk
     assert mk.status_string(0) == "ok"
     assert mk.status_string(mk.MLKD_EINVAL) == "invalid argument"
+
+
+def test_level_set_validation(built):
+    import paper_2004_04071_gb300 as mk
+    base = dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=6)
+    assert mk.workspace_bytes(mk.make_problem(level_set=[2, 4, 6], **base)) > 0
+    assert mk.workspace_bytes(mk.make_problem(level_set=[6], **base)) > 0
+    for bad in ([2, 4], [4, 2, 6], [2, 2, 6], [-1, 6], [0, 1, 2, 3, 4, 5, 6, 7]):
+        assert mk.workspace_bytes(mk.make_problem(level_set=bad, **base)) == 0, bad
+    # a gap may coarsen by at most 2^20
+    assert mk.workspace_bytes(mk.make_problem(eps=0.1, T=1.0, dt0=0.5, M=4, L=11,
+                                              level_set=[0, 11])) == 0
+    assert mk.workspace_bytes(mk.make_problem(eps=0.1, T=1.0, dt0=0.5, M=4, L=11,
+                                              level_set=[0, 5, 11])) > 0

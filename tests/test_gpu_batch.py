@@ -172,3 +172,17 @@ def test_autotune_picks_from_grid(mk, ctx):
     assert all(s > 0 for s in secs)
     assert min(secs) == pytest.approx(secs[[1, 2, 4, 8].index(best.pairs_per_thread) * 4 +
                                           [16, 64, 256, 0].index(best.substeps_per_launch)])
+
+
+def test_batch_with_level_sets(mk, ctx):
+    """Requests over level sets in the batched form equal the per-level form."""
+    ds = [dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=6, qoi=1, init=1, nbins=0, tol=0.004,
+               n_warmup=100, seed=5, request=10, level_set=[2, 4, 5, 6]),
+          dict(eps=0.5, T=0.5, dt0=0.1, M=2, L=3, qoi=0, init=0, nbins=0, tol=0.01,
+               n_warmup=100, seed=5, request=11, level_set=[0, 3])]
+    probs = [gpu_problem(mk, d, precision=mk.PREC_FP64) for d in ds]
+    rb = ctx.estimate_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))
+    for p, b in zip(probs, rb):
+        r = ctx.estimate(p)
+        assert [lv["n"] for lv in b.levels] == [lv["n"] for lv in r.levels]
+        assert b.estimate == pytest.approx(r.estimate, rel=1e-12, abs=1e-14)

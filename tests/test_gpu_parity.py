@@ -178,3 +178,37 @@ def test_large_launch_sampled(orc, mk, ctx):
         a = orc.pairs(po, level, int(j), 1)
         assert kf[j] == a[2][0] and kc[j] == a[3][0]
         assert fp64_close(xf[j], a[0][0]) and fp64_close(xc[j], a[1][0])
+
+
+@pytest.mark.parametrize("name", ["two_level", "diffusive", "periodic", "kinetic"])
+def test_fp64_on_24bit_stream_matches_oracle(orc, mk, ctx, name):
+    """FP64 state on the FP32 modes' random numbers against the oracle on the
+    same 24-bit stream: the same 1e-12 bar as the FP64 mode."""
+    d = REGIMES[name]
+    for level in sorted({0, 1, d["L"]}):
+        po = oracle_problem(orc, d, recipe=orc.RECIPE_24)
+        xf_o, xc_o, kf_o, kc_o = orc.pairs(po, level, 5, 2000, threads=8)
+        xf_g, xc_g, kf_g, kc_g = ctx.debug_pairs(gpu_problem(mk, d, precision=mk.PREC_FP64_U24),
+                                                 level, 5, 2000)
+        assert np.array_equal(kf_g, kf_o) and np.array_equal(kc_g, kc_o)
+        assert fp64_close(xf_g, xf_o).all() and fp64_close(xc_g, xc_o).all()
+
+
+def test_level_set_pairs_and_estimate(orc, mk, ctx):
+    """Estimator levels coupling non-adjacent levels (Sec. 4.2): per pair and
+    as a fixed-count estimate, against the oracle."""
+    d = dict(eps=0.2, T=1.0, dt0=0.5, M=2, L=6, qoi=1, init=1, nbins=32, lo=0.0, hi=1.0, seed=8,
+             level_set=[1, 2, 4, 6], n_fixed=[40000, 20000, 8000, 3000])
+    po = oracle_problem(orc, d)
+    po.level_set = d["level_set"]
+    pg = mk.make_problem(precision=0, **{k: v for k, v in d.items()})
+    for j in range(4):
+        a = orc.pairs(po, j, 0, 1500, threads=8)
+        b = ctx.debug_pairs(pg, j, 0, 1500)
+        assert np.array_equal(b[2], a[2]) and np.array_equal(b[3], a[3])
+        assert fp64_close(b[0], a[0]).all() and fp64_close(b[1], a[1]).all()
+    ro = orc.estimate(po, threads=8)
+    rg = ctx.estimate(pg)
+    assert [lv["n"] for lv in rg.levels] == d["n_fixed"]
+    assert rg.estimate == pytest.approx(ro.estimate, rel=1e-12)
+    np.testing.assert_allclose(rg.density, ro.density, rtol=1e-12, atol=1e-12)
