@@ -578,7 +578,9 @@ def run_serving(args):
            "data": "synthetic", "precision": args.precision, "requests": len(stream),
            "rate": args.rate, "completed": len(done), "unfinished_at_limit": len(pending),
            "latency_p50_s": q(0.5), "latency_p99_s": q(0.99), "wall_s": wall,
-           "events_per_s": ev / wall, "met_tolerance": ok, "server": st,
+           "events_per_s": st["events"] / wall,
+           "events_per_busy_s": st["events"] / st["busy_seconds"] if st["busy_seconds"] else None,
+           "completed_events_per_s": ev / wall, "met_tolerance": ok, "server": st,
            "note": "a 64-bin density at RMSE tol needs about 128/tol^2 level-0 samples under "
                    "the per-bin reading; tight tolerances dominate the load"}
     print(json.dumps(out), flush=True)

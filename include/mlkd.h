@@ -172,6 +172,18 @@ MLKD_API mlkd_status mlkd_run_level(mlkd_context *ctx, const mlkd_problem *probl
 MLKD_API mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *stream,
                           mlkd_result *out);
 
+/* Resumable form of mlkd_estimate.  Runs at most max_rounds sample-count
+ * rounds after the warm-up (mlkd_estimate uses 64) and stops; out and
+ * hist_out (host, J*3*nbins counts per level: fine, coarse, both; or NULL)
+ * are then a checkpoint.  Passing them back as resume / hist_in continues the
+ * same estimate: pair p of a level always uses the same stream, so a run that
+ * is stopped and resumed ends exactly as an uninterrupted one.  out->rounds
+ * counts the rounds so far. */
+MLKD_API mlkd_status mlkd_estimate_resumable(mlkd_context *ctx, const mlkd_problem *problem,
+                                             const mlkd_result *resume, const uint64_t *hist_in,
+                                             int max_rounds, void *stream, mlkd_result *out,
+                                             uint64_t *hist_out);
+
 /* Per-pair results of pairs [first_pair, first_pair + n_pairs) of `level`:
  * device arrays of n_pairs entries for the final fine and coarse positions
  * (xc = 0 on level 0) and the fine and coarse KD event counts.  Any of the
@@ -231,6 +243,8 @@ typedef struct {
     int32_t use_graph;           /* 1: one CUDA graph with a device-side loop                 */
     int32_t max_requests;        /* request slots of the batch region (<= 4096)             */
     int32_t max_nbins;           /* histogram bins per request (<= 256)                      */
+    int32_t refill_min;          /* a warp sums and restarts finished pairs once this many of
+                                    its lanes are idle (1..32; 0: library default)           */
 } mlkd_batch_config;
 
 /* Arena bytes a context needs for the batched and serving forms with this
@@ -279,6 +293,8 @@ typedef struct {
     uint64_t submitted, admitted, completed, cancelled, rejected;
     uint64_t iterations;         /* scheduler / pair-slice iterations run                 */
     double busy_seconds;         /* wall time spent in iterations                         */
+    uint64_t events;             /* fine + coarse KD events merged into request sums, all
+                                    requests (finished, running or cancelled)             */
 } mlkd_server_stats;
 
 /* Starts the server (arena must hold mlkd_batch_workspace_bytes(&cfg->batch)). */

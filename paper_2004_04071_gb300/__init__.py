@@ -36,7 +36,7 @@ EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_context_get_timing", "mlkd_run_level_noalloc", "mlkd_batch_workspace_bytes",
             "mlkd_estimate_batch", "mlkd_autotune_batch", "mlkd_server_start", "mlkd_submit",
             "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop",
-            "mlkd_debug_transforms", "mlkd_level_select"]
+            "mlkd_debug_transforms", "mlkd_level_select", "mlkd_estimate_resumable"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -83,17 +83,17 @@ class Result(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("pairs_per_thread", ctypes.c_int32), ("substeps_per_launch", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("max_requests", ctypes.c_int32),
-                ("max_nbins", ctypes.c_int32)]
+                ("max_nbins", ctypes.c_int32), ("refill_min", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def batch_config(pairs_per_thread=1, substeps_per_launch=256, use_graph=1, max_requests=64,
-                 max_nbins=128) -> BatchConfig:
+                 max_nbins=128, refill_min=0) -> BatchConfig:
     c = BatchConfig()
     c.pairs_per_thread, c.substeps_per_launch, c.use_graph = pairs_per_thread, substeps_per_launch, use_graph
-    c.max_requests, c.max_nbins = max_requests, max_nbins
+    c.max_requests, c.max_nbins, c.refill_min = max_requests, max_nbins, refill_min
     return c
 
 
@@ -106,7 +106,7 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
                 ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
                 ("rejected", ctypes.c_uint64), ("iterations", ctypes.c_uint64),
-                ("busy_seconds", ctypes.c_double)]
+                ("busy_seconds", ctypes.c_double), ("events", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -178,6 +178,9 @@ def lib():
         L.mlkd_level_select.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int,
                                         P(ctypes.c_int32), P(ctypes.c_int32)]
         L.mlkd_level_select.restype = ctypes.c_int
+        L.mlkd_estimate_resumable.argtypes = [vp, P(Problem), P(Result), P(ctypes.c_uint64), ctypes.c_int,
+                                              vp, P(Result), P(ctypes.c_uint64)]
+        L.mlkd_estimate_resumable.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -409,6 +412,38 @@ class Context:
     def server_stop(self):
         _check(lib().mlkd_server_stop(self.handle), "mlkd_server_stop")
 
+    # -- mlkd_estimate_resumable ----------------------------------------------
+    def estimate_resumable(self, problem: Problem, resume=None, hist_in=None, max_rounds=64,
+                           stream=None):
+        """Returns (EstimateResult, histogram counts [J*3*nbins] or None): a
+        checkpoint that resume/hist_in continue exactly."""
+        r = Result()
+        dens = None
+        hist = None
+        hp = None
+        if problem.nbins > 0:
+            dens = np.zeros(problem.nbins, np.float64)
+            r.density = dens.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            J = problem.n_set if problem.n_set > 0 else problem.L + 1
+            hist = np.zeros(J * 3 * problem.nbins, np.uint64)
+            hp = hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        rs = None
+        hin = None
+        if resume is not None:
+            rs = _result_struct(resume)
+            if hist_in is not None:
+                hin_arr = np.ascontiguousarray(hist_in, np.uint64)
+                hin = hin_arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        _check(lib().mlkd_estimate_resumable(self.handle, ctypes.byref(problem),
+                                             ctypes.byref(rs) if rs is not None else None, hin,
+                                             max_rounds, _stream_handle(stream), ctypes.byref(r), hp),
+               "mlkd_estimate_resumable")
+        n = r.n_levels
+        er = EstimateResult(r.estimate, r.variance, r.rounds, [r.lv[l].as_dict() for l in range(n)],
+                            [r.var_level[l] for l in range(n)], [r.cost_level[l] for l in range(n)],
+                            dens, r.seconds)
+        return er, hist
+
     # -- mlkd_estimate -----------------------------------------------------
     def estimate(self, problem: Problem, stream=None):
         r = Result()
@@ -443,6 +478,37 @@ def run_level_noalloc(problem: Problem, level: int, first_pair: int, n_pairs: in
         nb = problem.nbins
         out["hist_f"], out["hist_c"], out["hist_both"] = hist[:nb], hist[nb:2 * nb], hist[2 * nb:]
     return out
+
+
+def _result_struct(er) -> Result:
+    """mlkd_result holding the level sums and round count of an EstimateResult."""
+    r = Result()
+    r.estimate, r.variance = er.estimate, er.variance
+    r.n_levels, r.rounds = len(er.levels), er.rounds
+    for l, lv in enumerate(er.levels):
+        for k, _ in LevelStats._fields_:
+            setattr(r.lv[l], k, lv[k])
+        r.var_level[l] = er.var_level[l]
+        r.cost_level[l] = er.cost_level[l]
+    return r
+
+
+def checkpoint_to_json(er, hist=None) -> str:
+    """Text form of a checkpoint (exact: floats round-trip through repr)."""
+    import json
+    return json.dumps({"rounds": er.rounds, "levels": er.levels,
+                       "hist": None if hist is None else [int(v) for v in hist]})
+
+
+def checkpoint_from_json(text: str):
+    """(EstimateResult, hist) from checkpoint_to_json's text."""
+    import json
+    d = json.loads(text)
+    levels = d["levels"]
+    n = len(levels)
+    er = EstimateResult(0.0, 0.0, d["rounds"], levels, [0.0] * n, [0.0] * n, None, 0.0)
+    hist = None if d["hist"] is None else np.array(d["hist"], np.uint64)
+    return er, hist
 
 
 @dataclass

@@ -73,6 +73,7 @@ struct BatchCtl {
     unsigned long long q_head, q_tail;
     int32_t live;
     int32_t iterations;         // loop iterations run (three kernel launches each)
+    unsigned long long events;  // fine + coarse events merged into request sums so far
 };
 
 // Persisted state of one warp between slices: the chunk it is working on.
@@ -97,7 +98,7 @@ struct BatchLaunch {
     int32_t max_nbins;
     int32_t slice_iters;
     int32_t n_slots;
-    int32_t pad_;
+    int32_t refill_min;          // idle lanes a warp gathers before it restarts them together
     PhiloxKeys keys;
 };
 
@@ -146,11 +147,21 @@ template <> __device__ __forceinline__ const BgParams<double> &req_params<double
 // them.  Slicing changes no arithmetic and no order: results are the same for
 // every slice length.
 // ---------------------------------------------------------------------------
+// A lane's running sums of its current chunk.  They change only when a pair
+// finishes, so they live in shared memory rather than in registers that the
+// event loop needs; 72 bytes per lane keeps bank conflicts at two-way.
+template <int MODE> struct LaneSums {
+    PairSums<MODE> mom;
+    unsigned long long ev_f, ev_c;
+    uint32_t pad_[2];
+};
+
 template <typename Real, int MODE, int PPT>
 __global__ void __launch_bounds__(kThreads, (BatchMinBlocks<Real, PPT>::value))
 batch_pair_kernel(const __grid_constant__ BatchLaunch B)
 {
     extern __shared__ unsigned int s_hist_all[];        // [warps][3 * max_nbins]
+    __shared__ LaneSums<MODE> s_sums[kThreads];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const size_t gw = (size_t)blockIdx.x * kWarpsPerBlock + warp;
@@ -172,9 +183,11 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     int nbins = 0;
     unsigned long long end = 0;
     PairState<Real> st[PPT];
-    bool active[PPT];
-    PairSums<MODE> mom;
-    unsigned long long ev_f_sum = 0, ev_c_sum = 0;
+    bool active[PPT];           // the lane's pair has events left
+    bool done[PPT];             // the lane holds a pair that reached T but is not yet summed
+    PairSums<MODE> &mom = s_sums[threadIdx.x].mom;
+    unsigned long long &ev_f_sum = s_sums[threadIdx.x].ev_f;
+    unsigned long long &ev_c_sum = s_sums[threadIdx.x].ev_c;
 
     auto load_chunk = [&]() {
         ch = B.queue[c & B.cap_mask];
@@ -192,6 +205,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         L.bg.inv_Rdt = bp.inv_Rdt;
         L.n = D->n_level[level];
         L.M = D->M_level[level];
+        L.m_shift = (L.M & (L.M - 1)) == 0 ? __ffs(L.M) - 1 : -1;
         L.init = D->init;
         L.word2 = (uint32_t)D->level_of[level] << 24;
         L.request = D->request;
@@ -234,7 +248,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                 if (bc >= 0 && bc == bf) atomicAdd(&wh[2 * nbins + bf], 1u);
             }
         }
-        active[j] = false;
+        done[j] = false;
     };
 
     if (valid) {                                      // resume the stored chunk
@@ -248,7 +262,10 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         uint32_t bits;
         get_words(bits, lw, stride, w);
 #pragma unroll
-        for (int j = 0; j < PPT; ++j) active[j] = (bits >> j) & 1u;
+        for (int j = 0; j < PPT; ++j) {
+            active[j] = (bits >> j) & 1u;
+            done[j] = (bits >> (kMaxPPT + j)) & 1u;
+        }
     }
 
     for (;;) {
@@ -275,6 +292,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
                 active[j] = false;
+                done[j] = false;
                 st[j].fresh = true;
             }
             valid = 1;
@@ -284,25 +302,37 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             // the budget is checked before the refill, so a resumed slice runs
             // exactly the sequence an unsliced run would
             if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+            // Lanes whose pair reached T wait, idle, until refill_min of
+            // them (or the whole warp) can be summed and restarted in one
+            // pass: the summation and the start of a pair then run once for
+            // many lanes instead of once per finishing lane.
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
                 const unsigned idle = __ballot_sync(kFullMask, !active[j]);
-                if (idle != 0u && next < end) {
-                    const unsigned rank = __popc(idle & ((1u << lane) - 1u));
-                    const unsigned long long cand = next + rank;
-                    if (!active[j] && cand < end) {
-                        active[j] = true;
-                        if (pair_start<Real, 2, ModeRecipe<MODE>::value>(st[j], cand, L, B.keys, coupled)) finish(j);
+                if (idle != 0u && (__popc(idle) >= B.refill_min || idle == kFullMask)) {
+                    if (done[j]) finish(j);
+                    if (next < end) {
+                        const unsigned rank = __popc(idle & ((1u << lane) - 1u));
+                        const unsigned long long cand = next + rank;
+                        if (!active[j] && cand < end) {
+                            if (pair_start<Real, 2, ModeRecipe<MODE>::value>(st[j], cand, L, B.keys, coupled))
+                                done[j] = true;
+                            else
+                                active[j] = true;
+                        }
+                        next += __popc(idle);
+                        if (next > end) next = end;
                     }
-                    next += __popc(idle);
-                    if (next > end) next = end;
                 }
             }
-            bool any_local = false;
+            bool any_local = false, any_done = false;
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) any_local |= active[j];
+            for (int j = 0; j < PPT; ++j) {
+                any_local |= active[j];
+                any_done |= done[j];
+            }
             if (!__any_sync(kFullMask, any_local)) {
-                if (next >= end) {
+                if (next >= end && !__any_sync(kFullMask, any_done)) {
                     chunk_done = true;
                     break;
                 }
@@ -310,7 +340,10 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             }
 #pragma unroll
             for (int j = 0; j < PPT; ++j)
-                if (active[j] && pair_event<Real, 2, ModeRecipe<MODE>::value>(st[j], L, B.keys, coupled)) finish(j);
+                if (active[j] && pair_event<Real, 2, ModeRecipe<MODE>::value>(st[j], L, B.keys, coupled)) {
+                    active[j] = false;
+                    done[j] = true;
+                }
             ++iters;
         }
         if (!chunk_done) {
@@ -323,7 +356,8 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             put_words(ev_c_sum, lw, stride, w);
             uint32_t bits = 0;
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) bits |= (active[j] ? 1u : 0u) << j;
+            for (int j = 0; j < PPT; ++j)
+                bits |= ((active[j] ? 1u : 0u) << j) | ((done[j] ? 1u : 0u) << (kMaxPPT + j));
             put_words(bits, lw, stride, w);
             flush_hist();
             if (lane == 0) {
@@ -438,6 +472,7 @@ __global__ void __launch_bounds__(kSchedThreads) batch_sched_kernel(const BatchL
                 a.sqc2 += v[5];
                 a.events_f += (unsigned long long)llrint(v[6]);
                 a.events_c += (unsigned long long)llrint(v[7]);
+                atomicAdd(&B.ctl->events, (unsigned long long)llrint(v[6]) + (unsigned long long)llrint(v[7]));
                 S.job_nch[l] = 0;
                 S.job_count[l] = 0;
             }
@@ -603,6 +638,7 @@ static bool batch_cfg_ok(const mlkd_batch_config *c)
     if (c->pairs_per_thread != 1 && c->pairs_per_thread != 2 && c->pairs_per_thread != 4 &&
         c->pairs_per_thread != 8) return false;
     if (c->substeps_per_launch < 0) return false;
+    if (c->refill_min < 0 || c->refill_min > 32) return false;
     if (c->max_requests < 1 || c->max_requests > 4096) return false;
     if (c->max_nbins < 0 || c->max_nbins > 256) return false;
     return true;
@@ -724,6 +760,7 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->cap_mask = BL.cap - 1;
     B->max_nbins = cfg->max_nbins > 0 ? cfg->max_nbins : 1;
     B->slice_iters = cfg->substeps_per_launch;
+    B->refill_min = cfg->refill_min > 0 ? cfg->refill_min : kRefillMin;
     B->n_slots = n_slots;
     fill_keys(seed, &B->keys);
 }
@@ -1092,9 +1129,12 @@ static void server_loop(Server *S)
             }
         }
         const double t_it = S->now();
+        unsigned long long events = 0;
         if (cudaGraphLaunch(S->exec, S->stream) != cudaSuccess ||
             cudaMemcpyAsync(S->slot_status.data(), S->B.status_out, n * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
+            cudaMemcpyAsync(&events, &S->B.ctl->events, sizeof(events), cudaMemcpyDeviceToHost,
+                            S->stream) != cudaSuccess ||
             cudaStreamSynchronize(S->stream) != cudaSuccess) {
             std::lock_guard<std::mutex> lk(S->mu);
             S->error = MLKD_ECUDA;
@@ -1105,6 +1145,7 @@ static void server_loop(Server *S)
         std::lock_guard<std::mutex> lk(S->mu);
         S->stats.iterations += 1;
         S->stats.busy_seconds += S->now() - t_it;
+        S->stats.events = events;
         bool any_done = false;
         for (int slot = 0; slot < n; ++slot) {
             const uint64_t id = S->slot_req[slot];

@@ -452,11 +452,16 @@ mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int
     return harvest_timing(ctx);
 }
 
-mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *stream,
-                          mlkd_result *out)
+}  // extern "C"
+
+// Adaptive MLMC (Sec. 4.1) with an optional starting state and a round limit.
+static mlkd_status estimate_impl(mlkd_context *ctx, const mlkd_problem *problem,
+                                 const mlkd_result *resume, const uint64_t *hist_in, int max_rounds,
+                                 void *stream, mlkd_result *out, uint64_t *hist_out)
 {
     Derived d;
     if (!ctx || !out || !validate(problem, &d)) return MLKD_EINVAL;
+    if (max_rounds < 0) return MLKD_EINVAL;
     if (!problem->n_fixed && !(problem->tol > 0.0)) return MLKD_EINVAL;
     if (!problem->n_fixed && problem->n_warmup < 2) return MLKD_EINVAL;
     const auto t0 = std::chrono::steady_clock::now();
@@ -471,6 +476,32 @@ mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *
     const int density = problem->qoi == MLKD_QOI_DENSITY ? 1 : 0;
     DevControl ctl;
     int rounds = 0;
+    if (resume) {
+        // restart from a saved state: the level sums and pair counts (pair p
+        // always uses the same stream, so the run continues where it stopped)
+        if (resume->n_levels != nl || (nb > 0 && !hist_in)) return MLKD_EINVAL;
+        DevLevelStats init[MLKD_MAX_LEVELS];
+        for (int l = 0; l < nl; ++l) {
+            const mlkd_level_stats &r = resume->lv[l];
+            if (r.n < 0) return MLKD_EINVAL;
+            init[l].n = r.n;
+            init[l].sy = r.sy;
+            init[l].sy2 = r.sy2;
+            init[l].sqf = r.sqf;
+            init[l].sqf2 = r.sqf2;
+            init[l].sqc = r.sqc;
+            init[l].sqc2 = r.sqc2;
+            init[l].events_f = r.events_f;
+            init[l].events_c = r.events_c;
+            have[l] = r.n;
+        }
+        MLKD_CUDA(cudaMemcpyAsync(ctx->acc_stats, init, nl * sizeof(DevLevelStats), cudaMemcpyHostToDevice, s));
+        if (nb > 0)
+            MLKD_CUDA(cudaMemcpyAsync(ctx->acc_hist, hist_in, (size_t)nl * 3 * nb * sizeof(unsigned long long),
+                                      cudaMemcpyHostToDevice, s));
+        MLKD_CUDA(cudaStreamSynchronize(s));
+        rounds = resume->rounds;
+    }
 
     auto run = [&](int l, long long target) -> mlkd_status {
         if (target <= have[l]) return MLKD_OK;
@@ -497,10 +528,12 @@ mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *
         }
         if ((st = control()) != MLKD_OK) return st;
     } else {
-        for (int l = 0; l < nl; ++l)
-            if ((st = run(l, problem->n_warmup)) != MLKD_OK) return st;
+        if (!resume)
+            for (int l = 0; l < nl; ++l)
+                if ((st = run(l, problem->n_warmup)) != MLKD_OK) return st;
         for (;;) {
             if ((st = control()) != MLKD_OK) return st;
+            if (rounds >= max_rounds) break;           // stop; resumable from here
             bool grew = false;
             for (int l = 0; l < nl; ++l) {
                 if (ctl.target[l] > have[l]) {
@@ -509,7 +542,7 @@ mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *
                 }
             }
             if (!grew) break;
-            if (++rounds > 64) break;
+            ++rounds;
         }
     }
     DevLevelStats acc[MLKD_MAX_LEVELS];
@@ -518,17 +551,21 @@ mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *
     double *dens = out->density;
     std::memset(out, 0, sizeof(*out));
     out->density = dens;
-    if (dens && nb > 0) {
-        for (int i = 0; i < nb; ++i) dens[i] = 0.0;
+    if ((dens || hist_out) && nb > 0) {
+        if (dens)
+            for (int i = 0; i < nb; ++i) dens[i] = 0.0;
         MLKD_CUDA(cudaStreamSynchronize(s));
         for (int l = 0; l < nl; ++l) {
             MLKD_CUDA(cudaMemcpy(hacc, ctx->acc_hist + (size_t)l * 3 * nb, 3 * (size_t)nb * sizeof(unsigned long long),
                                  cudaMemcpyDeviceToHost));
-            if (acc[l].n > 0)
+            if (hist_out)
+                for (int b = 0; b < 3 * nb; ++b) hist_out[(size_t)l * 3 * nb + b] = hacc[b];
+            if (dens && acc[l].n > 0)
                 for (int b = 0; b < nb; ++b)
                     dens[b] += ((double)hacc[b] - (double)hacc[nb + b]) / (double)acc[l].n;
         }
-        for (int b = 0; b < nb; ++b) dens[b] /= d.h;
+        if (dens)
+            for (int b = 0; b < nb; ++b) dens[b] /= d.h;
     }
     MLKD_CUDA(cudaStreamSynchronize(s));
     out->estimate = ctl.estimate;
@@ -542,6 +579,22 @@ mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *
     }
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return harvest_timing(ctx);
+}
+
+extern "C" {
+
+mlkd_status mlkd_estimate(mlkd_context *ctx, const mlkd_problem *problem, void *stream,
+                          mlkd_result *out)
+{
+    return estimate_impl(ctx, problem, nullptr, nullptr, 64, stream, out, nullptr);
+}
+
+mlkd_status mlkd_estimate_resumable(mlkd_context *ctx, const mlkd_problem *problem,
+                                    const mlkd_result *resume, const uint64_t *hist_in,
+                                    int max_rounds, void *stream, mlkd_result *out,
+                                    uint64_t *hist_out)
+{
+    return estimate_impl(ctx, problem, resume, hist_in, max_rounds, stream, out, hist_out);
 }
 
 }  // extern "C"

@@ -29,11 +29,11 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &rk)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi_a = __umulhi(kPhiloxMulA, c.x);
-        const uint32_t lo_a = kPhiloxMulA * c.x;
-        const uint32_t hi_b = __umulhi(kPhiloxMulB, c.z);
-        const uint32_t lo_b = kPhiloxMulB * c.z;
-        c = make_uint4(hi_b ^ c.y ^ rk.k0[r], lo_b, hi_a ^ c.w ^ rk.k1[r], lo_a);
+        // one 32x32 -> 64-bit product per multiplier gives both halves
+        const unsigned long long pa = (unsigned long long)kPhiloxMulA * c.x;
+        const unsigned long long pb = (unsigned long long)kPhiloxMulB * c.z;
+        c = make_uint4((uint32_t)(pb >> 32) ^ c.y ^ rk.k0[r], (uint32_t)pb,
+                       (uint32_t)(pa >> 32) ^ c.w ^ rk.k1[r], (uint32_t)pa);
     }
     return c;
 }
@@ -50,45 +50,45 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    // sqrt of x >= 0 as x * rsqrt(x) (relative error about 2^-22, inside the
+    // FP32 modes' per-event bound); 0 for x <= 0.
+    static __device__ __forceinline__ float sqrt_pos_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
     static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
     static __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
     static __device__ __forceinline__ float sinpi_(float x) { return sinpif(x); }
     static __device__ __forceinline__ float floor_(float x) { return floorf(x); }
 
-    // (f(s)/s^3, g(s)/s^3, h(s)/s^2) for 0 <= s < 1 from their Taylor series:
+    // (f(s)/s^3, g(s)/s^3, h(s)/s^2) for 0 <= s < 1, where
     //   f(s) = 2(e^{-s}-1) + s(e^{-s}+1) = sum_{n>=3} (-1)^n (2-n)     s^n/n!
     //   g(s) = 1 - 2 s e^{-s} - e^{-2s}   = sum_{n>=3} (-1)^n (2n-2^n) s^n/n!
     //   h(s) = e^{-s} + s - 1             = sum_{n>=2} (-1)^n          s^n/n!
-    // truncated where the next term is below 2^-24 of the leading one at s = 1.
+    // as Chebyshev interpolants on [0, 1] (degrees 6, 9, 6; FP32 Horner error
+    // at most 2.2, 2.7 and 1.2 x 2^-24 relative), written by
+    // gen_series_fp32.py beside this file.
     static __device__ __forceinline__ float f_series(float s)
     {
-        float p = 1.76649482e-09f;
-        p = fmaf(p, s, -2.0876757e-08f);  p = fmaf(p, s, 2.25468975e-07f);
-        p = fmaf(p, s, -2.20458554e-06f); p = fmaf(p, s, 1.92901235e-05f);
-        p = fmaf(p, s, -0.000148809524f); p = fmaf(p, s, 0.000992063492f);
-        p = fmaf(p, s, -0.00555555556f);  p = fmaf(p, s, 0.025f);
-        p = fmaf(p, s, -0.0833333333f);   p = fmaf(p, s, 0.166666667f);
+        float p = 1.301975954e-05f;
+        p = fmaf(p, s, -1.407892123e-04f); p = fmaf(p, s, 9.867830668e-04f);
+        p = fmaf(p, s, -5.553742871e-03f); p = fmaf(p, s, 2.499970049e-02f);
+        p = fmaf(p, s, -8.333331347e-02f); p = fmaf(p, s, 1.666666716e-01f);
         return p;
     }
     static __device__ __forceinline__ float g_series(float s)
     {
-        float p = 2.50352846e-08f;
-        p = fmaf(p, s, -1.87615515e-07f); p = fmaf(p, s, 1.31138152e-06f);
-        p = fmaf(p, s, -8.50101545e-06f); p = fmaf(p, s, 5.07555716e-05f);
-        p = fmaf(p, s, -0.000276675485f); p = fmaf(p, s, 0.00136133157f);
-        p = fmaf(p, s, -0.00595238095f);  p = fmaf(p, s, 0.0226190476f);
-        p = fmaf(p, s, -0.0722222222f);   p = fmaf(p, s, 0.183333333f);
-        p = fmaf(p, s, -0.333333333f);    p = fmaf(p, s, 0.333333333f);
+        float p = -4.008331416e-06f;
+        p = fmaf(p, s, 4.246406752e-05f);  p = fmaf(p, s, -2.675861761e-04f);
+        p = fmaf(p, s, 1.355129993e-03f);  p = fmaf(p, s, -5.949722603e-03f);
+        p = fmaf(p, s, 2.261834778e-02f);  p = fmaf(p, s, -7.222211361e-02f);
+        p = fmaf(p, s, 1.833333224e-01f);  p = fmaf(p, s, -3.333333433e-01f);
+        p = fmaf(p, s, 3.333333433e-01f);
         return p;
     }
     static __device__ __forceinline__ float h_series(float s)
     {
-        float p = -2.50521084e-08f;
-        p = fmaf(p, s, 2.75573192e-07f);  p = fmaf(p, s, -2.75573192e-06f);
-        p = fmaf(p, s, 2.48015873e-05f);  p = fmaf(p, s, -0.000198412698f);
-        p = fmaf(p, s, 0.00138888889f);   p = fmaf(p, s, -0.00833333333f);
-        p = fmaf(p, s, 0.0416666667f);    p = fmaf(p, s, -0.166666667f);
-        p = fmaf(p, s, 0.5f);
+        float p = 1.692812657e-05f;
+        p = fmaf(p, s, -1.883247605e-04f); p = fmaf(p, s, 1.382241608e-03f);
+        p = fmaf(p, s, -8.331050165e-03f); p = fmaf(p, s, 4.166629165e-02f);
+        p = fmaf(p, s, -1.666666418e-01f); p = fmaf(p, s, 5.000000000e-01f);
         return p;
     }
     // z - sin z = z^3 S(z^2) with S = sum_{n>=1} (-1)^{n+1} z^{2n-2}/(2n+1)!,
@@ -101,7 +101,7 @@ template <> struct Arith<float> {
         p = fmaf(p, z2, 0.166666667f);
         return p;
     }
-    static constexpr int kNewtonIters = 5;
+    static constexpr int kHalleySteps = 2;
 };
 
 template <> struct Arith<double> {
@@ -111,6 +111,7 @@ template <> struct Arith<double> {
     static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double sqrt_pos_(double x) { return x > 0.0 ? sqrt(x) : 0.0; }
     static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
     static __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }
     static __device__ __forceinline__ double sinpi_(double x) { return sinpi(x); }
@@ -171,7 +172,7 @@ template <> struct Arith<double> {
         p = fma(p, z2, -0.0083333333333333332);  p = fma(p, z2, 0.16666666666666666);
         return p;
     }
-    static constexpr int kNewtonIters = 7;
+    static constexpr int kHalleySteps = 3;
 };
 
 // ---------------------------------------------------------------------------
@@ -285,7 +286,7 @@ __device__ __forceinline__ Draw<float> draw<float>(uint32_t k, uint32_t pair_lo,
                                                    uint32_t request, const PhiloxKeys &rk)
 {
     const uint4 w = philox4x32_10(make_uint4(k, pair_lo, word2, request), rk);
-    const float r = sqrtf(-2.0f * log_unit24(w.x));
+    const float r = Arith<float>::sqrt_pos_(-2.0f * log_unit24(w.x));
     float s, c;
     sincos_2pi_unit24(w.y, &s, &c);
     Draw<float> d;
@@ -354,7 +355,7 @@ template <typename Real> struct Background {
         a = mu * theta + dv * om * invR;
         const Real dvR = dv * invR;
         const Real d2 = two_c2 * f + dvR * dvR * g;
-        d = d2 > Real(0) ? A::sqrt_(d2) : Real(0);
+        d = A::sqrt_pos_(d2);
     }
 
     // Dimensionless beta weight (Sec. 3.2, eq. weights-beta) of a diffusive
@@ -372,33 +373,41 @@ template <typename Real> struct Background {
 
 // ---------------------------------------------------------------------------
 // Initial position with density 1 + cos(2 pi x) on [0, 1): solve
-// G(y) = y - sin(2 pi y)/(2 pi) = u - 1/2 for y in [-1/2, 1/2] by Newton from
-// the small-|y| inverse y0 = cbrt(6 g/(2 pi)^2), with G' = 2 sin^2(pi y);
-// x = y + 1/2 wrapped into [0, 1).
+// G(y) = y - sin(2 pi y)/(2 pi) = u - 1/2 for y in [-1/2, 1/2], x = y + 1/2
+// wrapped into [0, 1).  Start from the small-|y| inverse
+// y0 = cbrt(6 g/(2 pi)^2) (error below 0.08 everywhere) and take Halley
+// steps, y <- y - 2 r G' / (2 G'^2 - r G''), r = G(y) - g, with
+// G' = 2 sin^2(pi y) and G'' = 4 pi sin(pi y) cos(pi y) from one sincospi.
+// Convergence is cubic: two steps reach FP32 rounding, three FP64 rounding.
 // ---------------------------------------------------------------------------
-template <typename Real> __device__ __forceinline__ Real cosine_G(Real y)
-{
-    typedef Arith<Real> A;
-    const Real two_pi = Real(6.283185307179586476925286766559);
-    if (y < Real(-0.125) || y > Real(0.125)) return y - A::sinpi_(Real(2) * y) / two_pi;
-    const Real z = two_pi * y;
-    const Real z2 = z * z;
-    return z2 * z * A::zms_series(z2) / two_pi;
-}
-
 template <typename Real> __device__ __forceinline__ Real cosine_inverse(Real u)
 {
     typedef Arith<Real> A;
-    const Real two_pi_sq_over6 = Real(6.5797362673929057);   // (2 pi)^2 / 6
+    const Real two_pi = Real(6.283185307179586476925286766559);
+    const Real four_pi = Real(12.566370614359172953850573533118);
+    const Real inv_pi = Real(0.31830988618379067153776752674503);
+    const Real inv_two_pi = Real(0.15915494309189533576888376337251);
+    const Real six_over_two_pi_sq = Real(0.15198177546350666);   // 6 / (2 pi)^2
     const Real g = u - Real(0.5);
-    Real y = A::cbrt_(g / two_pi_sq_over6);
+    Real y = A::cbrt_(g * six_over_two_pi_sq);
     y = A::min_(A::max_(y, Real(-0.5)), Real(0.5));
-#pragma unroll 1
-    for (int it = 0; it < A::kNewtonIters; ++it) {
-        const Real sp = A::sinpi_(y);
-        const Real gp = Real(2) * sp * sp;
-        if (!(gp > Real(0))) break;
-        y = y - (cosine_G(y) - g) / gp;
+#pragma unroll
+    for (int it = 0; it < A::kHalleySteps; ++it) {
+        Real sp, cp;
+        A::sincospi_(y, &sp, &cp);
+        Real Gy;
+        if (y < Real(-0.125) || y > Real(0.125)) {
+            Gy = y - sp * cp * inv_pi;                         // sin(2 pi y)/(2 pi) = s c / pi
+        } else {
+            const Real z = two_pi * y;                         // no cancellation near 0
+            const Real z2 = z * z;
+            Gy = z2 * z * A::zms_series(z2) * inv_two_pi;
+        }
+        const Real r = Gy - g;
+        const Real g1 = Real(2) * sp * sp;
+        const Real g2 = four_pi * sp * cp;
+        const Real den = Real(2) * g1 * g1 - r * g2;
+        if (den > Real(0)) y = y - Real(2) * r * g1 / den;
         y = A::min_(A::max_(y, Real(-0.5)), Real(0.5));
     }
     Real x = y + Real(0.5);

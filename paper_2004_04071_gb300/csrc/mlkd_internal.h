@@ -35,6 +35,10 @@ template <typename Real> struct BgParams {
 };
 
 // Parameters of one pair-kernel launch (passed by value as __grid_constant__).
+// Idle lanes a warp of the pair kernels gathers before it sums their finished
+// pairs and starts new ones in one pass (the batched form can override it).
+constexpr int kRefillMin = 8;
+
 struct PairLaunch {
     double R, mu, sigma, dt;   // background and fine step of this level
     double lo, hi, h;          // histogram range [lo, hi) and bin width

@@ -50,6 +50,7 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     L.bg.inv_Rdt = bp.inv_Rdt;
     L.n = P.n;
     L.M = P.M;
+    L.m_shift = (P.M & (P.M - 1)) == 0 ? __ffs(P.M) - 1 : -1;
     L.init = P.init;
     L.word2 = P.word2;
     L.request = P.request;
@@ -74,7 +75,8 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     if (w_end > end_all) w_end = end_all;
     unsigned long long next = w_begin;                 // warp-uniform
 
-    bool active = false;
+    bool active = false;        // the lane's pair has events left
+    bool done = false;          // the lane holds a finished pair not yet summed
     unsigned long long pair = 0;
     PairState<Real> st;
     st.fresh = true;
@@ -104,29 +106,38 @@ pair_kernel(const __grid_constant__ PairLaunch P)
             if (P.dbg_kf) P.dbg_kf[j] = (int32_t)st.k;
             if (P.dbg_kc) P.dbg_kc[j] = (int32_t)st.evc;
         }
-        active = false;
+        done = false;
     };
 
     for (;;) {
-        // refill idle lanes from the warp's chunk
+        // Lanes whose pair reached T stay idle until kRefillMin of them (or
+        // the whole warp) can be summed and restarted from the warp's chunk
+        // in one pass.
         const unsigned idle = __ballot_sync(kFullMask, !active);
-        if (idle != 0u && next < w_end) {
-            const unsigned rank = __popc(idle & ((1u << lane) - 1u));
-            const unsigned long long cand = next + rank;
-            if (!active && cand < w_end) {
-                pair = cand;
-                active = true;
-                if (pair_start<Real, CPL, ModeRecipe<MODE>::value>(st, cand, L, P.keys, COUPLED)) finish_pair();
+        if (idle != 0u && (__popc(idle) >= kRefillMin || idle == kFullMask)) {
+            if (done) finish_pair();
+            if (next < w_end) {
+                const unsigned rank = __popc(idle & ((1u << lane) - 1u));
+                const unsigned long long cand = next + rank;
+                if (!active && cand < w_end) {
+                    pair = cand;
+                    if (pair_start<Real, CPL, ModeRecipe<MODE>::value>(st, cand, L, P.keys, COUPLED))
+                        done = true;
+                    else
+                        active = true;
+                }
+                next += __popc(idle);
+                if (next > w_end) next = w_end;
             }
-            next += __popc(idle);
-            if (next > w_end) next = w_end;
         }
         if (!__any_sync(kFullMask, active)) {
-            if (next >= w_end) break;
+            if (next >= w_end && !__any_sync(kFullMask, done)) break;
             continue;
         }
-        if (!active) continue;
-        if (pair_event<Real, CPL, ModeRecipe<MODE>::value>(st, L, P.keys, COUPLED)) finish_pair();
+        if (active && pair_event<Real, CPL, ModeRecipe<MODE>::value>(st, L, P.keys, COUPLED)) {
+            active = false;
+            done = true;
+        }
     }
 
     // ---- block reduction of the sums (fixed order) ----

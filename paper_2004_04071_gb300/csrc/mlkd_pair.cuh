@@ -31,10 +31,21 @@ template <typename Real> struct LevelCtx {
     Background<Real> bg;
     int n;                      // fine steps to T on this level
     int M;                      // refinement factor
+    int m_shift;                // log2 M if M is a power of two, else -1
     int init;                   // 0: x0 = 0; 1: cosine density
     uint32_t word2;             // level << 24
     uint32_t request;
 };
+
+// End of the coarse step that contains fine-step position base + steps + f
+// (0 <= f < 1), with base on the coarse grid: base + M (steps / M + 1).
+// A power-of-two M (the usual case) divides by a shift.
+template <typename Real>
+__device__ __forceinline__ int next_coarse_end(const LevelCtx<Real> &L, int base, int steps)
+{
+    const int q = L.m_shift >= 0 ? steps >> L.m_shift : steps / L.M;
+    return base + L.M * (q + 1);
+}
 
 // CPL: 0 = level 0 (single path), 1 = coupled pair, 2 = decided at run time.
 template <typename Real, int CPL>
@@ -65,7 +76,7 @@ __device__ __forceinline__ bool pair_start(PairState<Real> &st, unsigned long lo
         st.num = Real(0);
         st.den = Real(0);
         st.fresh = true;
-        if (st.qf < (Real)L.n) st.Ec = L.M * ((int)st.qf / L.M + 1);
+        if (st.qf < (Real)L.n) st.Ec = next_coarse_end(L, 0, (int)st.qf);
     }
     return !(st.qf < (Real)L.n);
 }
@@ -99,7 +110,7 @@ __device__ __forceinline__ bool pair_event(PairState<Real> &st, const LevelCtx<R
             st.chi_first = d.chi;
             st.fresh = false;
         }
-        st.num += A::sqrt_(bh2) * d.chi;
+        st.num += A::sqrt_pos_(bh2) * d.chi;
         st.den += bh2;
         if (st.qf < (Real)(st.Ec - st.i_f)) {
             const Real ah = st.qf * bg.Rdt + om;                  // R tau' = R tau + R zeta
@@ -118,7 +129,7 @@ __device__ __forceinline__ bool pair_event(PairState<Real> &st, const LevelCtx<R
             st.ic = st.Ec;
             st.vc = v1;
             ++st.evc;
-            if (st.qc < (Real)(L.n - st.ic)) st.Ec = L.M * ((st.ic + (int)st.qc) / L.M + 1);
+            if (st.qc < (Real)(L.n - st.ic)) st.Ec = next_coarse_end(L, st.ic, (int)st.qc);
             st.num = Real(0);
             st.den = Real(0);
             st.fresh = true;

@@ -11,9 +11,10 @@ pairs (2^22 for the level-0 case), on the periodic problem of the benchmark:
 Device memory held: the 0.7 MB context arena.
 
 Batched form: the benchmark's three periodic estimates (eps = 1, 0.1, 1e-3)
-with fixed sample counts scaled by 1/8 in one batched call with unbounded
-slices and no graph, so that the pair work is one batch_pair_kernel launch.
-Device memory held: the batch arena (about 0.3 GB).
+with fixed sample counts scaled by 1/8 (by 2^scale / 8 with --scale) in one
+batched call with unbounded slices and no graph, so that the pair work is one
+batch_pair_kernel launch.  Device memory held: the batch arena (about 0.3 GB)
+at any scale.
 """
 import argparse
 import os
@@ -42,6 +43,7 @@ def main():
         fixed = [[44000, 22700],
                  [1125000, 380000, 320000, 393000, 318000, 250000, 198000, 169000, 100000],
                  [785000, 100, 100, 100, 100, 100, 100, 100, 100, 100, 2290, 2430, 2600]]
+        fixed = [[max(1, x << a.scale) for x in n] for n in fixed]
         probs = [mk.make_problem(precision=prec, n_fixed=n, request=i, **dict(W.periodic_problem(e)))
                  for i, (e, n) in enumerate(zip(W.PERIODIC_EPS, fixed))]
         rs = ctx.estimate_batch(probs, cfg)

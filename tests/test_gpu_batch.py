@@ -149,12 +149,15 @@ def test_batch_rejects_invalid(mk, ctx):
         ctx.estimate_batch([d], small)
 
 
-def test_slice_length_changes_nothing(mk, ctx):
-    """A chunk stored at the end of a slice and resumed in the next gives the
-    same sums bit for bit, whatever the slice length."""
+@pytest.mark.parametrize("refill_min", [1, 8])
+def test_slice_length_changes_nothing(mk, ctx, refill_min):
+    """A chunk stored at the end of a slice and resumed in the next (active
+    and finished-but-unsummed lanes included) gives the same sums bit for
+    bit, whatever the slice length."""
     probs = [gpu_problem(mk, d, precision=1) for d in mixed_problems(1, seed=17)]
     runs = [ctx.estimate_batch(probs, mk.batch_config(pairs_per_thread=2, substeps_per_launch=S,
-                                                      max_requests=64, max_nbins=128))
+                                                      max_requests=64, max_nbins=128,
+                                                      refill_min=refill_min))
             for S in (0, 7, 64, 1000)]
     for rs in runs[1:]:
         for x, y in zip(runs[0], rs):
@@ -186,3 +189,24 @@ def test_batch_with_level_sets(mk, ctx):
         r = ctx.estimate(p)
         assert [lv["n"] for lv in b.levels] == [lv["n"] for lv in r.levels]
         assert b.estimate == pytest.approx(r.estimate, rel=1e-12, abs=1e-14)
+
+
+def test_refill_threshold_changes_only_sum_order(mk, ctx):
+    """Restarting finished lanes one at a time or sixteen at a time runs the
+    same pairs on the same streams: event counts equal, estimates equal to
+    FP64 rounding of the sums (FP64 mode)."""
+    probs = [gpu_problem(mk, d, precision=mk.PREC_FP64) for d in mixed_problems(0, seed=19)]
+    cfg = dict(max_requests=64, max_nbins=128)
+    fixed = [[lv["n"] for lv in r.levels] for r in ctx.estimate_batch(probs, mk.batch_config(**cfg))]
+    probs = [gpu_problem(mk, dict(d, n_fixed=n, tol=0.0), precision=mk.PREC_FP64)
+             for d, n in zip(mixed_problems(0, seed=19), fixed)]
+    a = ctx.estimate_batch(probs, mk.batch_config(refill_min=1, **cfg))
+    b = ctx.estimate_batch(probs, mk.batch_config(refill_min=16, **cfg))
+    for x, y in zip(a, b):
+        for lx, ly in zip(x.levels, y.levels):
+            assert lx["n"] == ly["n"]
+            assert lx["events_f"] == ly["events_f"] and lx["events_c"] == ly["events_c"]
+            assert lx["sy2"] == pytest.approx(ly["sy2"], rel=1e-12)
+        assert x.estimate == pytest.approx(y.estimate, rel=1e-12, abs=1e-15)
+        if x.density is not None:
+            np.testing.assert_allclose(x.density, y.density, rtol=1e-12, atol=1e-12)

@@ -79,6 +79,10 @@ def test_result_same_alone_and_in_the_mix(mk):
             assert results[i].variance <= d["tol"] ** 2 / 2 * (1 + 1e-6)
         st = ctx.server_stats()
         assert st["completed"] == 13 and st["submitted"] == 13
+        # the device event counter covers exactly the merged work of all requests
+        ev = sum(lv["events_f"] + lv["events_c"] for r in [alone] + list(results.values())
+                 for lv in r.levels)
+        assert st["events"] == ev
     finally:
         ctx.server_stop()
         ctx.close()
