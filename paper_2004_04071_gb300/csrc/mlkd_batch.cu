@@ -31,7 +31,8 @@ namespace mlkd {
 constexpr int kBL = MLKD_MAX_LEVELS;            // levels per request
 constexpr int kMaxChunksPerJob = 2048;           // chunks per (request, level, round)
 constexpr int kChunkQuantum = 32;                // chunk sizes are multiples of one pair per lane
-constexpr int kTargetIters = 2048;               // target warp iterations per chunk
+constexpr int kTargetIters = 1024;               // target warp iterations per chunk
+constexpr double kPairStartIters = 2.0;          // start + summation of a pair, in event iterations
 constexpr long long kMaxChunkPairs = 1LL << 22;  // pairs per chunk at most
 constexpr int kSchedThreads = 256;
 
@@ -66,11 +67,13 @@ struct ReqState {
 struct Chunk {
     int32_t req, level;
     unsigned long long first;
-    int32_t count, pad_;
+    int32_t count;
+    int32_t listed;             // 1: also in the long-chunk list, taken from there
 };
 
 struct BatchCtl {
     unsigned long long q_head, q_tail;
+    unsigned long long l_head, l_tail;   // long-chunk list (chunk ids), drained first
     int32_t live;
     int32_t iterations;         // loop iterations run (three kernel launches each)
     unsigned long long events;  // fine + coarse events merged into request sums so far
@@ -94,6 +97,7 @@ struct BatchLaunch {
     WarpHdr *hdr;                // [grid warps]
     int32_t *status_out;         // [slots]: status after the scheduler (host-readable copy)
     uint32_t *lane_words;        // [words][grid lanes]: pair states and sums per lane
+    unsigned long long *long_ids;  // [cap]: ring of ids of chunks longer than a target slice
     unsigned long long cap_mask;
     int32_t max_nbins;
     int32_t slice_iters;
@@ -131,8 +135,12 @@ template <typename Real, int MODE, int PPT> constexpr int lane_words()
     return (int)((PPT * sizeof(PairState<Real>) + sizeof(PairSums<MODE>) + 2 * sizeof(unsigned long long)) / 4) + 1;
 }
 
-// Blocks per SM of the batched pair kernel by pair states per lane.
-template <typename Real, int PPT> struct BatchMinBlocks { static constexpr int value = PPT == 1 ? 6 : PPT == 2 ? 4 : PPT == 4 ? 2 : 1; };
+// Blocks per SM of the batched pair kernel by pair states per lane.  Five
+// 128-thread blocks (96 registers) rather than six: the deep levels' chunks
+// are chains of up to 12 288 serial events, and a warp that shares its
+// scheduler with fewer warps finishes its chain sooner; measured on the
+// periodic benchmark, five balances that against latency hiding best.
+template <typename Real, int PPT> struct BatchMinBlocks { static constexpr int value = PPT == 1 ? 5 : PPT == 2 ? 4 : PPT == 4 ? 2 : 1; };
 template <int PPT> struct BatchMinBlocks<double, PPT> { static constexpr int value = 1; };
 
 template <typename Real> __device__ __forceinline__ const BgParams<Real> &req_params(const ReqDesc &D, int l);
@@ -194,31 +202,33 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         D = &B.req[ch.req];
         const int level = ch.level;
         coupled = level > 0;
-        const BgParams<Real> &bp = req_params<Real>(*D, level);
-        L.bg.R = bp.R;
-        L.bg.invR = bp.invR;
-        L.bg.mu = bp.mu;
-        L.bg.sigma = bp.sigma;
-        L.bg.two_c2 = bp.two_c2;
-        L.bg.dt = bp.dt;
-        L.bg.Rdt = bp.Rdt;
-        L.bg.inv_Rdt = bp.inv_Rdt;
-        L.n = D->n_level[level];
-        L.M = D->M_level[level];
-        L.m_shift = (L.M & (L.M - 1)) == 0 ? __ffs(L.M) - 1 : -1;
-        L.init = D->init;
-        L.word2 = (uint32_t)D->level_of[level] << 24;
-        L.request = D->request;
         per = D->periodic != 0;
         nbins = D->nbins;
-        bins.lo = D->bd[level].lo;
-        bins.hi = D->bd[level].hi;
-        bins.h = D->h;
-        bins.lo_f = D->bf[level].lo;
-        bins.hi_f = D->bf[level].hi;
-        bins.inv_h_f = D->bf[level].inv_h;
-        bins.nbins = nbins;
-        bins.periodic = per;
+        {
+            const BgParams<Real> &bp = req_params<Real>(*D, level);
+            L.bg.R = bp.R;
+            L.bg.invR = bp.invR;
+            L.bg.mu = bp.mu;
+            L.bg.sigma = bp.sigma;
+            L.bg.two_c2 = bp.two_c2;
+            L.bg.dt = bp.dt;
+            L.bg.Rdt = bp.Rdt;
+            L.bg.inv_Rdt = bp.inv_Rdt;
+            L.n = D->n_level[level];
+            L.M = D->M_level[level];
+            L.m_shift = (L.M & (L.M - 1)) == 0 ? __ffs(L.M) - 1 : -1;
+            L.init = D->init;
+            L.word2 = (uint32_t)D->level_of[level] << 24;
+            L.request = D->request;
+            bins.lo = D->bd[level].lo;
+            bins.hi = D->bd[level].hi;
+            bins.h = D->h;
+            bins.lo_f = D->bf[level].lo;
+            bins.hi_f = D->bf[level].hi;
+            bins.inv_h_f = D->bf[level].inv_h;
+            bins.nbins = nbins;
+            bins.periodic = per;
+        }
         end = ch.first + (unsigned long long)ch.count;
         for (int i = lane; i < 3 * nbins; i += 32) wh[i] = 0u;
         __syncwarp();
@@ -271,14 +281,30 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     for (;;) {
         if (!valid) {
             if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+            // Chunks whose single pairs outlast a target slice (deep levels)
+            // come from their own list first, so that the longest work
+            // starts earliest; the queue copy of such a chunk is skipped.
             unsigned long long cn = 0;
-            if (lane == 0) cn = atomicAdd(&B.ctl->q_head, 1ull);
+            int from_list = 0;
+            if (lane == 0) {
+                if (*(volatile unsigned long long *)&B.ctl->l_head <
+                    *(volatile unsigned long long *)&B.ctl->l_tail) {
+                    const unsigned long long li = atomicAdd(&B.ctl->l_head, 1ull);
+                    if (li < *(volatile unsigned long long *)&B.ctl->l_tail) {
+                        cn = B.long_ids[li & B.cap_mask];
+                        from_list = 1;
+                    }
+                }
+                if (!from_list) cn = atomicAdd(&B.ctl->q_head, 1ull);
+            }
             cn = __shfl_sync(kFullMask, cn, 0);
-            if (cn >= *(volatile unsigned long long *)&B.ctl->q_tail) break;
+            from_list = __shfl_sync(kFullMask, from_list, 0);
+            if (!from_list && cn >= *(volatile unsigned long long *)&B.ctl->q_tail) break;
             c = cn;
             {
-                // a chunk of a cancelled request is dropped unprocessed
                 const Chunk peek = B.queue[c & B.cap_mask];
+                if (!from_list && peek.listed) continue;
+                // a chunk of a cancelled request is dropped unprocessed
                 if (B.state[peek.req].status == 4) {
                     if (lane == 0) atomicSub(&B.state[peek.req].pending, 1);
                     continue;
@@ -393,7 +419,10 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
 // ---------------------------------------------------------------------------
 __device__ long long chunk_size(long long count, double events_per_pair)
 {
-    double ch = 32.0 * kTargetIters / (events_per_pair > 1.0 ? events_per_pair : 1.0);
+    // a pair costs its events plus its start (draw, initial position) and
+    // its summation, about two event iterations together
+    const double per_pair = (events_per_pair > 1.0 ? events_per_pair : 1.0) + kPairStartIters;
+    double ch = 32.0 * kTargetIters / per_pair;
     long long c = (long long)ch / kChunkQuantum * kChunkQuantum;
     if (c < kChunkQuantum) c = kChunkQuantum;
     if (c > kMaxChunkPairs) c = kMaxChunkPairs;
@@ -558,6 +587,7 @@ __global__ void __launch_bounds__(kSchedThreads) batch_sched_kernel(const BatchL
     __shared__ long long s_cb[kBL];
     __shared__ long long s_ch[kBL];
     __shared__ int s_nch[kBL];
+    __shared__ long long s_lb[kBL];
     if (t == 0) {
         int total_chunks = 0;
         for (int l = nl - 1; l >= 0; --l) {
@@ -581,6 +611,9 @@ __global__ void __launch_bounds__(kSchedThreads) batch_sched_kernel(const BatchL
             s_ch[l] = ch;
             s_nch[l] = nch;
             s_cb[l] = (long long)atomicAdd(&B.ctl->q_tail, (unsigned long long)nch);
+            // one pair per lane already exceeds a target slice: list the chunks
+            s_lb[l] = epp > (double)kTargetIters
+                          ? (long long)atomicAdd(&B.ctl->l_tail, (unsigned long long)nch) : -1;
             S.job_cb[l] = s_cb[l];
             S.job_nch[l] = nch;
             S.job_count[l] = count;
@@ -603,8 +636,10 @@ __global__ void __launch_bounds__(kSchedThreads) batch_sched_kernel(const BatchL
             c.level = l;
             c.first = (unsigned long long)first;
             c.count = (int32_t)cnt;
-            c.pad_ = 0;
+            c.listed = s_lb[l] >= 0 ? 1 : 0;
             B.queue[(unsigned long long)(s_cb[l] + i) & B.cap_mask] = c;
+            if (s_lb[l] >= 0)
+                B.long_ids[(unsigned long long)(s_lb[l] + i) & B.cap_mask] = (unsigned long long)(s_cb[l] + i);
         }
     }
     __syncthreads();
@@ -617,6 +652,7 @@ __global__ void __launch_bounds__(kSchedThreads) batch_sched_kernel(const BatchL
 __global__ void batch_post_kernel(BatchCtl *ctl, int *live_out, cudaGraphConditionalHandle h, int use_graph)
 {
     if (ctl->q_head > ctl->q_tail) ctl->q_head = ctl->q_tail;
+    if (ctl->l_head > ctl->l_tail) ctl->l_head = ctl->l_tail;
     ctl->iterations += 1;
     const int live = ctl->live;
     ctl->live = 0;
@@ -628,7 +664,7 @@ __global__ void batch_post_kernel(BatchCtl *ctl, int *live_out, cudaGraphConditi
 // Host side.
 // ---------------------------------------------------------------------------
 struct BatchLayout {
-    size_t desc, state, queue, rows, hist, ctl, live, hdr, lanes, status, total;
+    size_t desc, state, queue, longq, rows, hist, ctl, live, hdr, lanes, status, total;
     unsigned long long cap;
 };
 
@@ -655,6 +691,7 @@ static BatchLayout batch_layout(const mlkd_batch_config *c)
     B.desc = off;  off = align_up(off + (size_t)c->max_requests * sizeof(ReqDesc));
     B.state = off; off = align_up(off + (size_t)c->max_requests * sizeof(ReqState));
     B.queue = off; off = align_up(off + (size_t)cap * sizeof(Chunk));
+    B.longq = off; off = align_up(off + (size_t)cap * sizeof(unsigned long long));
     B.rows = off;  off = align_up(off + (size_t)cap * kPartialWords * sizeof(double));
     B.hist = off;  off = align_up(off + (size_t)c->max_requests * kBL * 3 * (size_t)(c->max_nbins > 0 ? c->max_nbins : 1) * sizeof(unsigned long long));
     B.ctl = off;   off = align_up(off + sizeof(BatchCtl));
@@ -756,6 +793,7 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->ctl = (BatchCtl *)(ctx->arena + BL.ctl);
     B->hdr = (WarpHdr *)(ctx->arena + BL.hdr);
     B->lane_words = (uint32_t *)(ctx->arena + BL.lanes);
+    B->long_ids = (unsigned long long *)(ctx->arena + BL.longq);
     B->status_out = (int32_t *)(ctx->arena + BL.status);
     B->cap_mask = BL.cap - 1;
     B->max_nbins = cfg->max_nbins > 0 ? cfg->max_nbins : 1;
