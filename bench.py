@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--time-limit", type=float, default=60.0,
                     help="serving: stop waiting for results after this many seconds")
+    ap.add_argument("--slots", type=int, default=512,
+                    help="serving: request slots of the batch region (the HBM budget)")
+    ap.add_argument("--substeps", type=int, default=1024,
+                    help="serving: event iterations per warp per pair-kernel launch")
     return ap.parse_args()
 
 
@@ -215,6 +219,14 @@ def run_gpu(args):
         step()
     ttt = sorted(ttt_once(adaptive)[0] for _ in range(3))[1]
 
+    # the same adaptive estimates in plain FP64, one per-level call per
+    # estimate (the comparison the metric names), after one warm-up call
+    fp64 = [mk.make_problem(precision=mk.PREC_FP64, **d) for d in dicts]
+    ctx.estimate(fp64[0], stream)
+    t = time.perf_counter()
+    r64 = [ctx.estimate(p, stream) for p in fp64]
+    ttt_fp64 = time.perf_counter() - t
+
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     ctx.get_timing(reset=True)
     sampler = ClockSampler(local)
@@ -285,6 +297,9 @@ def run_gpu(args):
                    "autotune": tune,  # seconds over ppt {1,2,4,8} x substeps {16,64,256,unbounded}
                    "events_per_step": ev / args.steps / world,
                    "time_to_tolerance_s": ttt, "time_to_tolerance_first_call_s": ttt_first,
+                   "time_to_tolerance_plain_fp64_s": ttt_fp64,
+                   "time_to_tolerance_speedup_vs_plain_fp64": ttt_fp64 / ttt,
+                   "estimates_plain_fp64": [r.estimate for r in r64],
                    "estimates": [r.estimate for r in last],
                    "variances": [r.variance for r in last],
                    "l2": "flushed (256 MB write) between timed steps; no input arrays"},
@@ -538,7 +553,7 @@ def run_serving(args):
     estimates with adaptive N_l, admitted into request slots as they free
     up; latency from submit to result, p50/p99, estimates/s.  Requests still
     running at the time limit are reported, not waited for."""
-    torch, mk, ctx, cfg = _gpu_setup(args, slots=64, nbins=64, substeps=2048)
+    torch, mk, ctx, cfg = _gpu_setup(args, slots=args.slots, nbins=64, substeps=args.substeps)
     prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
     stream = W.serving_stream(args.requests, rate=args.rate, seed=0)
     ctx.server_start(mk.server_config(cfg, precision=prec, seed=0, max_pending=1 << 20))
@@ -576,10 +591,13 @@ def run_serving(args):
     out = {"metric": "serving: p50/p99 latency and estimates/s (Poisson arrivals)",
            "value": len(done) / wall, "unit": "estimates/s", "higher_is_better": True,
            "data": "synthetic", "precision": args.precision, "requests": len(stream),
-           "rate": args.rate, "completed": len(done), "unfinished_at_limit": len(pending),
+           "rate": args.rate, "slots": args.slots, "substeps_per_launch": args.substeps,
+           "arena_bytes": mk.batch_workspace_bytes(cfg),
+           "completed": len(done), "unfinished_at_limit": len(pending),
            "latency_p50_s": q(0.5), "latency_p99_s": q(0.99), "wall_s": wall,
-           "events_per_s": st["events"] / wall,
-           "events_per_busy_s": st["events"] / st["busy_seconds"] if st["busy_seconds"] else None,
+           "events_per_s": st["events_processed"] / wall,
+           "events_per_busy_s": st["events_processed"] / st["busy_seconds"] if st["busy_seconds"] else None,
+           "merged_events_per_s": st["events"] / wall,
            "completed_events_per_s": ev / wall, "met_tolerance": ok, "server": st,
            "note": "a 64-bin density at RMSE tol needs about 128/tol^2 level-0 samples under "
                    "the per-bin reading; tight tolerances dominate the load"}

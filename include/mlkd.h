@@ -295,6 +295,8 @@ typedef struct {
     double busy_seconds;         /* wall time spent in iterations                         */
     uint64_t events;             /* fine + coarse KD events merged into request sums, all
                                     requests (finished, running or cancelled)             */
+    uint64_t events_processed;   /* fine + coarse KD events of every finished chunk, merged
+                                    or not yet (the device's work so far)                 */
 } mlkd_server_stats;
 
 /* Starts the server (arena must hold mlkd_batch_workspace_bytes(&cfg->batch)). */

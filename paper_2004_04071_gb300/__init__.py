@@ -106,7 +106,8 @@ class ServerStats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_uint64), ("admitted", ctypes.c_uint64),
                 ("completed", ctypes.c_uint64), ("cancelled", ctypes.c_uint64),
                 ("rejected", ctypes.c_uint64), ("iterations", ctypes.c_uint64),
-                ("busy_seconds", ctypes.c_double), ("events", ctypes.c_uint64)]
+                ("busy_seconds", ctypes.c_double), ("events", ctypes.c_uint64),
+                ("events_processed", ctypes.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

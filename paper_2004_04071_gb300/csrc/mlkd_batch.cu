@@ -29,12 +29,18 @@
 namespace mlkd {
 
 constexpr int kBL = MLKD_MAX_LEVELS;            // levels per request
-constexpr int kMaxChunksPerJob = 2048;           // chunks per (request, level, round)
+constexpr int kMaxChunksPerJob = 2048;           // chunks per level and round, on average
 constexpr int kChunkQuantum = 32;                // chunk sizes are multiples of one pair per lane
 constexpr int kTargetIters = 1024;               // target warp iterations per chunk
 constexpr double kPairStartIters = 2.0;          // start + summation of a pair, in event iterations
 constexpr long long kMaxChunkPairs = 1LL << 22;  // pairs per chunk at most
-constexpr int kSchedThreads = 256;
+constexpr long long kMaxChunkGrow = 4;           // chunk enlargement to fit a round, at most
+constexpr long long kRoundChunks = (long long)kBL * kMaxChunksPerJob;  // chunks of one request per round
+// chunk ids owned by one request slot: a round's chunks, plus one per level
+// where a proportional cut rounds a level's share up
+constexpr long long kSlotChunks = kRoundChunks + kBL;
+constexpr int kPublishSpins = 1 << 22;           // bounded wait for earlier reservations to publish
+constexpr int kIdleSpins = 4096;                 // bounded wait for new work: sleeps of up to 64 us, about 0.25 s
 
 struct ReqDesc {
     BgParams<double> bd[kBL];
@@ -62,22 +68,38 @@ struct ReqState {
     double estimate, variance;
     double var_level[kBL], cost_level[kBL];
     long long target[kBL];
+    long long job_ch[kBL];      // pairs per chunk of this round's job per level
+    int32_t job_long[kBL];      // 1: the level's chunks go to the long-chunk queue
+    long long plan_want[kBL];   // planning scratch: pairs wanted per level
+    double plan_epp[kBL];       // planning scratch: events per pair per level
+    int32_t counted;            // 1: counted in BatchCtl::running
+    int32_t pad2_;
 };
 
 struct Chunk {
     int32_t req, level;
     unsigned long long first;
-    int32_t count;
-    int32_t listed;             // 1: also in the long-chunk list, taken from there
+    int32_t count, pad_;
 };
 
+// Work queues are rings of chunk ids.  A producer reserves places at *_resv,
+// writes the ids, publishes them by moving *_tail in reservation order, and
+// then adds them to *_avail.  A consumer first takes one unit of *_avail (so
+// that it never runs past the published ids), then its place from *_head;
+// both are plain atomic adds, which stay fast with thousands of claimers.
 struct BatchCtl {
-    unsigned long long q_head, q_tail;
-    unsigned long long l_head, l_tail;   // long-chunk list (chunk ids), drained first
+    unsigned long long q_head, q_tail, q_resv;
+    unsigned long long l_head, l_tail, l_resv;   // chunks longer than a target slice, drained first
+    int32_t q_avail, l_avail;   // published ids not yet claimed
     int32_t live;
     int32_t iterations;         // loop iterations run (three kernel launches each)
     unsigned long long events;  // fine + coarse events merged into request sums so far
+    unsigned long long events_done;  // fine + coarse events of finished chunks so far
+    int32_t running;            // requests with a round in flight
+    int32_t error;              // 1: a publication wait ran out
 };
+// the server reads events .. error in one copy
+static_assert(offsetof(BatchCtl, error) == offsetof(BatchCtl, events) + 20, "BatchCtl tail layout");
 
 // Persisted state of one warp between slices: the chunk it is working on.
 struct WarpHdr {
@@ -90,15 +112,16 @@ struct WarpHdr {
 struct BatchLaunch {
     const ReqDesc *req;
     ReqState *state;
-    Chunk *queue;
-    double *rows;
+    Chunk *chunks;               // [slots][kSlotChunks]
+    double *rows;                // [slots][kSlotChunks][kPartialWords]
     unsigned long long *hist;
     BatchCtl *ctl;
     WarpHdr *hdr;                // [grid warps]
     int32_t *status_out;         // [slots]: status after the scheduler (host-readable copy)
     uint32_t *lane_words;        // [words][grid lanes]: pair states and sums per lane
-    unsigned long long *long_ids;  // [cap]: ring of ids of chunks longer than a target slice
-    unsigned long long cap_mask;
+    unsigned long long *q_ids;   // [ring]: queue of chunk ids
+    unsigned long long *l_ids;   // [ring]: queue of long chunks' ids
+    unsigned long long ring_mask;
     int32_t max_nbins;
     int32_t slice_iters;
     int32_t n_slots;
@@ -155,6 +178,297 @@ template <> __device__ __forceinline__ const BgParams<double> &req_params<double
 // them.  Slicing changes no arithmetic and no order: results are the same for
 // every slice length.
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// Rounds of one request, run by one warp: finalize (the round's chunk rows
+// into the request's sums, in chunk order), the FP64 controller (eqs.
+// Nopt1/Noptj) and the plan of the next round.  The warp that finishes a
+// round's last chunk runs them inside the pair kernel, so a request's next
+// round starts while other requests' work goes on; the scheduler kernel runs
+// the same functions for admissions.  Every decision depends only on the
+// request's own sums, so its results are the same alone and in any mix.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long vload64(const unsigned long long *p)
+{
+    return *(volatile const unsigned long long *)p;
+}
+
+// Target chunk size of a level: a multiple of 32 pairs sized for about
+// kTargetIters warp iterations.
+__device__ long long chunk_target(double events_per_pair)
+{
+    // a pair costs its events plus its start (draw, initial position) and
+    // its summation, about two event iterations together
+    const double per_pair = (events_per_pair > 1.0 ? events_per_pair : 1.0) + kPairStartIters;
+    double ch = 32.0 * kTargetIters / per_pair;
+    long long c = (long long)ch / kChunkQuantum * kChunkQuantum;
+    if (c < kChunkQuantum) c = kChunkQuantum;
+    if (c > kMaxChunkPairs) c = kMaxChunkPairs;
+    return c;
+}
+
+// Appends chunk ids [id0, id0 + n) to a queue (whole warp): reserve, write,
+// publish in reservation order.  The wait for earlier reservations is
+// bounded; running out sets BatchCtl::error, which ends the loop.
+__device__ void push_ids(const BatchLaunch &B, unsigned long long *ring, unsigned long long *resv,
+                         unsigned long long *tail, int32_t *avail, unsigned long long id0, int n, int lane)
+{
+    if (n <= 0) return;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(resv, (unsigned long long)n);
+    base = __shfl_sync(kFullMask, base, 0);
+    for (int i = lane; i < n; i += 32) ring[(base + i) & B.ring_mask] = id0 + (unsigned long long)i;
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) {
+        int k = 0;
+        while (atomicCAS(tail, base, base + (unsigned long long)n) != base) {
+            if (++k >= kPublishSpins) {
+                atomicExch(&B.ctl->error, 1);
+                break;
+            }
+            __nanosleep(32);
+        }
+        atomicAdd(avail, n);
+    }
+    __syncwarp();
+}
+
+// Claims the next published id of a queue (one lane); false if there is none.
+__device__ bool claim_id(const BatchLaunch &B, int32_t *avail, unsigned long long *head,
+                         const unsigned long long *ring, unsigned long long *id)
+{
+    if (*(volatile int32_t *)avail <= 0) return false;
+    if (atomicSub(avail, 1) <= 0) {
+        atomicAdd(avail, 1);
+        return false;
+    }
+    const unsigned long long h = atomicAdd(head, 1ull);
+    __threadfence();
+    *id = vload64(&ring[h & B.ring_mask]);
+    return true;
+}
+
+__device__ __noinline__ void warp_finalize(const BatchLaunch &B, int r, int lane)
+{
+    ReqState &S = B.state[r];
+    const int nl = B.req[r].L + 1;
+    for (int l = 0; l < nl; ++l) {
+        const int nch = S.job_nch[l];
+        if (nch == 0) continue;
+        double v[kPartialWords];
+#pragma unroll
+        for (int j = 0; j < kPartialWords; ++j) v[j] = 0.0;
+        for (int i = lane; i < nch; i += 32) {
+            const double *row = B.rows + (size_t)(S.job_cb[l] + i) * kPartialWords;
+#pragma unroll
+            for (int j = 0; j < kPartialWords; ++j) v[j] += row[j];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int j = 0; j < kPartialWords; ++j) v[j] += __shfl_down_sync(kFullMask, v[j], off);
+        __syncwarp();
+        if (lane == 0) {
+            DevLevelStats &a = S.acc[l];
+            a.n += S.job_count[l];
+            a.sy += v[0];
+            a.sy2 += v[1];
+            a.sqf += v[2];
+            a.sqf2 += v[3];
+            a.sqc += v[4];
+            a.sqc2 += v[5];
+            const unsigned long long ef = (unsigned long long)llrint(v[6]);
+            const unsigned long long ec = (unsigned long long)llrint(v[7]);
+            a.events_f += ef;
+            a.events_c += ec;
+            atomicAdd(&B.ctl->events, ef + ec);
+            S.job_nch[l] = 0;
+            S.job_count[l] = 0;
+        }
+        __syncwarp();
+    }
+}
+
+// Controller after a completed round.  Returns true if another round is
+// needed (targets in S.target), false when the request is done.
+__device__ __noinline__ bool warp_controller(const BatchLaunch &B, int r, int lane)
+{
+    ReqState &S = B.state[r];
+    const ReqDesc &D = B.req[r];
+    const int nl = D.L + 1;
+    for (int l = 0; l < nl; ++l) {
+        const double n = (double)S.acc[l].n;
+        double v = 0.0;
+        if (D.density && D.nbins > 0) {
+            // sup over bins of the bin indicators' level variance
+            const unsigned long long *H = B.hist + ((size_t)r * kBL + l) * 3 * B.max_nbins;
+            double m = 0.0;
+            for (int b = lane; b < D.nbins; b += 32) {
+                const double sy = (double)H[b] - (double)H[D.nbins + b];
+                const double sy2 = (double)H[b] + (double)H[D.nbins + b] - 2.0 * (double)H[2 * D.nbins + b];
+                const double vb = n >= 2.0 ? (sy2 - sy * sy / n) / (n - 1.0) : 0.0;
+                m = fmax(m, vb);
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) m = fmax(m, __shfl_xor_sync(kFullMask, m, off));
+            v = m / (D.h * D.h);
+        } else if (n >= 2.0) {
+            v = (S.acc[l].sy2 - S.acc[l].sy * S.acc[l].sy / n) / (n - 1.0);
+        }
+        if (lane == 0) {
+            S.var_level[l] = v > 0.0 ? v : 0.0;
+            S.cost_level[l] = n > 0.0 ? (double)(S.acc[l].events_f + S.acc[l].events_c) / n : 0.0;
+        }
+    }
+    __syncwarp();
+    int more = 0;
+    if (lane == 0) {
+        double est = 0.0, var = 0.0, total = 0.0;
+        for (int l = 0; l < nl; ++l) {
+            const double n = (double)S.acc[l].n;
+            if (n > 0.0) {
+                est += S.acc[l].sy / n;
+                var += S.var_level[l] / n;
+            }
+            total += sqrt(S.var_level[l] * S.cost_level[l]);
+        }
+        S.estimate = est;
+        S.variance = var;
+        bool grow = false;
+        for (int l = 0; l < nl; ++l) {
+            long long target = 0;
+            const double vl = S.var_level[l], cl = S.cost_level[l];
+            if (!D.use_fixed && vl > 0.0 && cl > 0.0 && D.tol > 0.0) {
+                const double tg = ceil(2.0 / (D.tol * D.tol) * sqrt(vl / cl) * total);
+                target = tg < 1e15 ? (long long)tg : 1000000000000000LL;
+            }
+            S.target[l] = target;
+            if (target > S.have[l]) grow = true;
+        }
+        if (!grow || D.use_fixed || S.rounds >= 64) {
+            S.status = 3;
+            B.status_out[r] = 3;
+            if (atomicExch(&S.counted, 0) == 1) atomicSub(&B.ctl->running, 1);
+        } else {
+            S.rounds += 1;
+            more = 1;
+        }
+    }
+    return __shfl_sync(kFullMask, more, 0) != 0;
+}
+
+// Plans the next round toward S.target, finest level first, and publishes
+// its chunks in the request's own chunk-id range.  A round holds at most
+// kRoundChunks chunks: chunks grow (the same factor on every level, at most
+// kMaxChunkGrow) until it fits; a request that still needs more gets every
+// level's share cut in proportion, and the next round continues with the
+// same targets, so that no chunk holds a warp much longer than a target
+// slice however many pairs a request asks for.
+__device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
+{
+    ReqState &S = B.state[r];
+    const ReqDesc &D = B.req[r];
+    const int nl = D.L + 1;
+    const unsigned long long slot0 = (unsigned long long)r * kSlotChunks;
+    if (lane == 0) {
+        long long *want = S.plan_want, *tch = S.job_ch;
+        double *epps = S.plan_epp;
+        for (int l = 0; l < nl; ++l) {
+            want[l] = S.target[l] - S.have[l];
+            if (want[l] < 0) want[l] = 0;
+            double epp = 1.0;
+            if (S.acc[l].n > 0) {
+                epp = (double)(S.acc[l].events_f + S.acc[l].events_c) / (double)S.acc[l].n;
+            } else {
+                const double nf = (double)D.n_level[l];
+                const double coll = (double)D.bd[l].Rdt * nf + 1.0;
+                epp = (coll < nf ? coll : nf) * (l > 0 ? 1.5 : 1.0);
+            }
+            epps[l] = epp;
+            tch[l] = chunk_target(epp);
+        }
+        long long grow = 1, chunks = 0;
+        for (;;) {
+            chunks = 0;
+            for (int l = 0; l < nl; ++l) chunks += (want[l] + grow * tch[l] - 1) / (grow * tch[l]);
+            if (chunks <= kRoundChunks || grow >= kMaxChunkGrow) break;
+            grow *= 2;
+        }
+        int total = 0;
+        for (int l = nl - 1; l >= 0; --l) {
+            S.job_nch[l] = 0;
+            S.job_count[l] = 0;
+            long long count = want[l];
+            if (count <= 0) continue;
+            const long long ch = grow * tch[l];
+            tch[l] = ch;
+            long long nch = (count + ch - 1) / ch;
+            if (chunks > kRoundChunks) {
+                nch = nch * kRoundChunks / chunks;
+                if (nch < 1) nch = 1;
+                if (count > nch * ch) count = nch * ch;
+            }
+            S.job_cb[l] = (long long)(slot0 + (unsigned long long)total);
+            S.job_nch[l] = (int32_t)nch;
+            S.job_count[l] = count;
+            // one pair per lane already exceeds a target slice: the long queue
+            S.job_long[l] = epps[l] > (double)kTargetIters ? 1 : 0;
+            total += (int)nch;
+        }
+        S.pending = total;
+        S.status = 2;
+    }
+    __syncwarp();
+    // chunk descriptors, then the ids in the queues (published last)
+    for (int l = nl - 1; l >= 0; --l) {
+        const int nch = S.job_nch[l];
+        const long long ch = S.job_ch[l];
+        const long long have = S.have[l];
+        for (int i = lane; i < nch; i += 32) {
+            const long long first = have + (long long)i * ch;
+            long long cnt = have + S.job_count[l] - first;
+            if (cnt > ch) cnt = ch;
+            Chunk c;
+            c.req = r;
+            c.level = l;
+            c.first = (unsigned long long)first;
+            c.count = (int32_t)cnt;
+            c.pad_ = 0;
+            B.chunks[S.job_cb[l] + i] = c;
+        }
+    }
+    __syncwarp();
+    if (lane == 0)
+        for (int l = 0; l < nl; ++l) S.have[l] += S.job_count[l];
+    __threadfence();
+    __syncwarp();
+    for (int l = nl - 1; l >= 0; --l) {
+        const int nch = S.job_nch[l];
+        if (nch == 0) continue;
+        if (S.job_long[l])
+            push_ids(B, B.l_ids, &B.ctl->l_resv, &B.ctl->l_tail, &B.ctl->l_avail,
+                     (unsigned long long)S.job_cb[l], nch, lane);
+        else
+            push_ids(B, B.q_ids, &B.ctl->q_resv, &B.ctl->q_tail, &B.ctl->q_avail,
+                     (unsigned long long)S.job_cb[l], nch, lane);
+    }
+}
+
+// A round whose last chunk has finished: merge it, then continue a cut round,
+// or run the controller and plan the next round (or finish the request).
+__device__ __noinline__ void warp_round_complete(const BatchLaunch &B, int r, int lane)
+{
+    ReqState &S = B.state[r];
+    const int nl = B.req[r].L + 1;
+    warp_finalize(B, r, lane);
+    int cont = 0;
+    if (lane == 0)
+        for (int l = 0; l < nl; ++l)
+            if (S.have[l] < S.target[l]) cont = 1;
+    cont = __shfl_sync(kFullMask, cont, 0);
+    if (cont || warp_controller(B, r, lane)) warp_plan(B, r, lane);
+}
+
 // A lane's running sums of its current chunk.  They change only when a pair
 // finishes, so they live in shared memory rather than in registers that the
 // event loop needs; 72 bytes per lane keeps bank conflicts at two-way.
@@ -182,6 +496,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     unsigned long long c = hdr->c;
     unsigned long long next = hdr->next;                 // warp-uniform
     int iters = 0;
+    int idle = 0;
 
     Chunk ch;
     const ReqDesc *D = nullptr;
@@ -198,7 +513,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     unsigned long long &ev_c_sum = s_sums[threadIdx.x].ev_c;
 
     auto load_chunk = [&]() {
-        ch = B.queue[c & B.cap_mask];
+        ch = B.chunks[c];
         D = &B.req[ch.req];
         const int level = ch.level;
         coupled = level > 0;
@@ -282,30 +597,37 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         if (!valid) {
             if (B.slice_iters > 0 && iters >= B.slice_iters) break;
             // Chunks whose single pairs outlast a target slice (deep levels)
-            // come from their own list first, so that the longest work
-            // starts earliest; the queue copy of such a chunk is skipped.
+            // come from their own queue first, so that the longest work
+            // starts earliest.  With nothing published, a warp of an
+            // unbounded launch waits (a bounded time) while some request
+            // still has a round in flight: the warp finishing that round
+            // publishes the next one.  In a sliced launch it leaves at once;
+            // the next slice picks up what was published meanwhile.
             unsigned long long cn = 0;
-            int from_list = 0;
+            int got = 0;
             if (lane == 0) {
-                if (*(volatile unsigned long long *)&B.ctl->l_head <
-                    *(volatile unsigned long long *)&B.ctl->l_tail) {
-                    const unsigned long long li = atomicAdd(&B.ctl->l_head, 1ull);
-                    if (li < *(volatile unsigned long long *)&B.ctl->l_tail) {
-                        cn = B.long_ids[li & B.cap_mask];
-                        from_list = 1;
-                    }
-                }
-                if (!from_list) cn = atomicAdd(&B.ctl->q_head, 1ull);
+                got = claim_id(B, &B.ctl->l_avail, &B.ctl->l_head, B.l_ids, &cn);
+                if (!got) got = claim_id(B, &B.ctl->q_avail, &B.ctl->q_head, B.q_ids, &cn);
             }
-            cn = __shfl_sync(kFullMask, cn, 0);
-            from_list = __shfl_sync(kFullMask, from_list, 0);
-            if (!from_list && cn >= *(volatile unsigned long long *)&B.ctl->q_tail) break;
-            c = cn;
+            got = __shfl_sync(kFullMask, got, 0);
+            if (!got) {
+                int stop = 0;
+                ++idle;
+                if (lane == 0)
+                    stop = B.slice_iters > 0 || *(volatile int32_t *)&B.ctl->running == 0 ||
+                           *(volatile int32_t *)&B.ctl->error != 0 || idle >= kIdleSpins;
+                if (__shfl_sync(kFullMask, stop, 0)) break;
+                // back off to sleeps of 64 us, so that waiting warps take
+                // almost no issue slots from the warps still at work
+                __nanosleep(1000u << (idle < 6 ? idle : 6));
+                continue;
+            }
+            idle = 0;
+            c = __shfl_sync(kFullMask, cn, 0);
             {
-                const Chunk peek = B.queue[c & B.cap_mask];
-                if (!from_list && peek.listed) continue;
                 // a chunk of a cancelled request is dropped unprocessed
-                if (B.state[peek.req].status == 4) {
+                const Chunk peek = B.chunks[c];
+                if (*(volatile int32_t *)&B.state[peek.req].status == 4) {
                     if (lane == 0) atomicSub(&B.state[peek.req].pending, 1);
                     continue;
                 }
@@ -401,260 +723,92 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             ev_c_sum += __shfl_down_sync(kFullMask, ev_c_sum, off);
         }
         if (lane == 0) {
-            double *row = B.rows + (size_t)(c & B.cap_mask) * kPartialWords;
+            double *row = B.rows + (size_t)c * kPartialWords;
 #pragma unroll
             for (int j = 0; j < 6; ++j) row[j] = mom.value(j);
             row[6] = (double)ev_f_sum;
             row[7] = (double)ev_c_sum;
+            atomicAdd(&B.ctl->events_done, ev_f_sum + ev_c_sum);
         }
         flush_hist();
-        if (lane == 0) atomicSub(&B.state[ch.req].pending, 1);
+        // the row and the histogram counts are visible before the count
+        // drops; the warp that takes it to zero completes the round
+        __threadfence();
+        int last = 0;
+        if (lane == 0) last = atomicSub(&B.state[ch.req].pending, 1) == 1;
+        if (__shfl_sync(kFullMask, last, 0)) {
+            __threadfence();
+            if (*(volatile int32_t *)&B.state[ch.req].status == 2) warp_round_complete(B, ch.req, lane);
+        }
         valid = 0;
     }
     if (lane == 0) hdr->valid = 0;
 }
 
 // ---------------------------------------------------------------------------
-// Scheduler: one block per request slot.
+// Scheduler kernel: one warp per request slot.  Admits requests (their first
+// round), frees cancelled ones once drained, and completes any round that no
+// pair-kernel warp completed (normally the warp that finishes a round's last
+// chunk completes it inside the pair kernel).
 // ---------------------------------------------------------------------------
-__device__ long long chunk_size(long long count, double events_per_pair)
-{
-    // a pair costs its events plus its start (draw, initial position) and
-    // its summation, about two event iterations together
-    const double per_pair = (events_per_pair > 1.0 ? events_per_pair : 1.0) + kPairStartIters;
-    double ch = 32.0 * kTargetIters / per_pair;
-    long long c = (long long)ch / kChunkQuantum * kChunkQuantum;
-    if (c < kChunkQuantum) c = kChunkQuantum;
-    if (c > kMaxChunkPairs) c = kMaxChunkPairs;
-    const long long min_for_cap = (count + kMaxChunksPerJob - 1) / kMaxChunksPerJob;
-    if (c < min_for_cap) c = (min_for_cap + kChunkQuantum - 1) / kChunkQuantum * kChunkQuantum;
-    return c;
-}
-
-__global__ void __launch_bounds__(kSchedThreads) batch_sched_kernel(const BatchLaunch B)
+__global__ void __launch_bounds__(32) batch_sched_kernel(const BatchLaunch B)
 {
     const int r = blockIdx.x;
     if (r >= B.n_slots) return;
     ReqState &S = B.state[r];
     const ReqDesc &D = B.req[r];
-    const int t = threadIdx.x;
-    const int lane = t & 31, warp = t >> 5;
-    __shared__ int s_status, s_pending;
-    __shared__ double s_var[kBL], s_cost[kBL];
-    __shared__ double s_max[kSchedThreads];
-    __shared__ long long s_target[kBL];
-    if (t == 0) {
-        s_status = S.status;
-        s_pending = S.pending;
-    }
-    __syncthreads();
-    const int status = s_status;
+    const int lane = threadIdx.x;
+    const int status = *(volatile int32_t *)&S.status;
+    const int pending = *(volatile int32_t *)&S.pending;
     if (status == 0 || status == 3) {
-        if (t == 0) B.status_out[r] = status;
+        if (lane == 0) B.status_out[r] = status;
         return;
     }
     if (status == 4) {                    // cancelled: free once its chunks have drained
-        if (t == 0) {
-            if (s_pending > 0) {
+        if (lane == 0) {
+            if (pending > 0) {
                 atomicAdd(&B.ctl->live, 1);
                 B.status_out[r] = 4;
             } else {
                 S.status = 0;
                 B.status_out[r] = 0;
+                if (atomicExch(&S.counted, 0) == 1) atomicSub(&B.ctl->running, 1);
             }
         }
         return;
     }
-    if (status == 2 && s_pending > 0) {
-        if (t == 0) {
+    if (status == 2 && pending > 0) {
+        if (lane == 0) {
             atomicAdd(&B.ctl->live, 1);
             B.status_out[r] = 2;
         }
         return;
     }
-    const int nl = D.L + 1;
     if (status == 2) {
-        // finalize: fixed-order sums of each level's chunk rows (one warp per level)
-        for (int l = warp; l < nl; l += kSchedThreads / 32) {
-            const int nch = S.job_nch[l];
-            if (nch == 0) continue;
-            double v[kPartialWords];
-#pragma unroll
-            for (int j = 0; j < kPartialWords; ++j) v[j] = 0.0;
-            for (int i = lane; i < nch; i += 32) {
-                const double *row = B.rows + (size_t)((S.job_cb[l] + i) & B.cap_mask) * kPartialWords;
-#pragma unroll
-                for (int j = 0; j < kPartialWords; ++j) v[j] += row[j];
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-                for (int j = 0; j < kPartialWords; ++j) v[j] += __shfl_down_sync(kFullMask, v[j], off);
-            if (lane == 0) {
-                DevLevelStats &a = S.acc[l];
-                a.n += S.job_count[l];
-                a.sy += v[0];
-                a.sy2 += v[1];
-                a.sqf += v[2];
-                a.sqf2 += v[3];
-                a.sqc += v[4];
-                a.sqc2 += v[5];
-                a.events_f += (unsigned long long)llrint(v[6]);
-                a.events_c += (unsigned long long)llrint(v[7]);
-                atomicAdd(&B.ctl->events, (unsigned long long)llrint(v[6]) + (unsigned long long)llrint(v[7]));
-                S.job_nch[l] = 0;
-                S.job_count[l] = 0;
-            }
-        }
-        __syncthreads();
-        // controller (eqs. Nopt1/Noptj), FP64
-        for (int l = 0; l < nl; ++l) {
-            const double n = (double)S.acc[l].n;
-            double v = 0.0;
-            if (D.density && D.nbins > 0) {
-                const unsigned long long *H = B.hist + ((size_t)r * kBL + l) * 3 * B.max_nbins;
-                double m = 0.0;
-                for (int b = t; b < D.nbins; b += kSchedThreads) {
-                    const double sy = (double)H[b] - (double)H[D.nbins + b];
-                    const double sy2 = (double)H[b] + (double)H[D.nbins + b] - 2.0 * (double)H[2 * D.nbins + b];
-                    const double vb = n >= 2.0 ? (sy2 - sy * sy / n) / (n - 1.0) : 0.0;
-                    m = fmax(m, vb);
-                }
-                s_max[t] = m;
-                __syncthreads();
-                for (int stride = kSchedThreads / 2; stride > 0; stride >>= 1) {
-                    if (t < stride) s_max[t] = fmax(s_max[t], s_max[t + stride]);
-                    __syncthreads();
-                }
-                v = s_max[0] / (D.h * D.h);
-                __syncthreads();
-            } else if (n >= 2.0) {
-                v = (S.acc[l].sy2 - S.acc[l].sy * S.acc[l].sy / n) / (n - 1.0);
-            }
-            if (t == 0) {
-                s_var[l] = v > 0.0 ? v : 0.0;
-                s_cost[l] = n > 0.0 ? (double)(S.acc[l].events_f + S.acc[l].events_c) / n : 0.0;
-            }
-        }
-        __syncthreads();
-        if (t == 0) {
-            double est = 0.0, var = 0.0, total = 0.0;
-            for (int l = 0; l < nl; ++l) {
-                const double n = (double)S.acc[l].n;
-                if (n > 0.0) {
-                    est += S.acc[l].sy / n;
-                    var += s_var[l] / n;
-                }
-                total += sqrt(s_var[l] * s_cost[l]);
-                S.var_level[l] = s_var[l];
-                S.cost_level[l] = s_cost[l];
-            }
-            S.estimate = est;
-            S.variance = var;
-            bool grow = false;
-            for (int l = 0; l < nl; ++l) {
-                long long target = 0;
-                if (!D.use_fixed && s_var[l] > 0.0 && s_cost[l] > 0.0 && D.tol > 0.0) {
-                    const double tg = ceil(2.0 / (D.tol * D.tol) * sqrt(s_var[l] / s_cost[l]) * total);
-                    target = tg < 1e15 ? (long long)tg : 1000000000000000LL;
-                }
-                S.target[l] = target;
-                s_target[l] = target;
-                if (target > S.have[l]) grow = true;
-            }
-            if (!grow || D.use_fixed || S.rounds >= 64) {
-                S.status = 3;
-                s_status = 3;
-            } else {
-                S.rounds += 1;
-            }
-        }
-        __syncthreads();
-        if (s_status == 3) {
-            if (t == 0) B.status_out[r] = 3;
-            return;
-        }
-    } else if (t == 0) {
+        warp_round_complete(B, r, lane);
+    } else {
         // admitted: warm-up round (or the fixed counts)
-        for (int l = 0; l < nl; ++l) {
-            const long long tg = D.use_fixed ? D.n_fixed[l] : (long long)D.n_warmup;
-            S.target[l] = tg;
-            s_target[l] = tg;
+        if (lane == 0) {
+            for (int l = 0; l <= D.L; ++l) S.target[l] = D.use_fixed ? D.n_fixed[l] : (long long)D.n_warmup;
+            S.counted = 1;
+            atomicAdd(&B.ctl->running, 1);
         }
+        __syncwarp();
+        warp_plan(B, r, lane);
     }
-    __syncthreads();
-    // plan: append this request's next round, finest level first
-    __shared__ long long s_cb[kBL];
-    __shared__ long long s_ch[kBL];
-    __shared__ int s_nch[kBL];
-    __shared__ long long s_lb[kBL];
-    if (t == 0) {
-        int total_chunks = 0;
-        for (int l = nl - 1; l >= 0; --l) {
-            s_nch[l] = 0;
-            long long count = s_target[l] - S.have[l];
-            if (count <= 0) continue;
-            // a round schedules at most kMaxChunksPerJob chunks of at most
-            // kMaxChunkPairs pairs per level; the next round continues
-            const long long round_cap = (long long)kMaxChunksPerJob * kMaxChunkPairs;
-            if (count > round_cap) count = round_cap;
-            double epp = 1.0;
-            if (S.acc[l].n > 0) {
-                epp = (double)(S.acc[l].events_f + S.acc[l].events_c) / (double)S.acc[l].n;
-            } else {
-                const double nf = (double)D.n_level[l];
-                const double coll = (double)D.bd[l].Rdt * nf + 1.0;
-                epp = (coll < nf ? coll : nf) * (l > 0 ? 1.5 : 1.0);
-            }
-            const long long ch = chunk_size(count, epp);
-            const int nch = (int)((count + ch - 1) / ch);
-            s_ch[l] = ch;
-            s_nch[l] = nch;
-            s_cb[l] = (long long)atomicAdd(&B.ctl->q_tail, (unsigned long long)nch);
-            // one pair per lane already exceeds a target slice: list the chunks
-            s_lb[l] = epp > (double)kTargetIters
-                          ? (long long)atomicAdd(&B.ctl->l_tail, (unsigned long long)nch) : -1;
-            S.job_cb[l] = s_cb[l];
-            S.job_nch[l] = nch;
-            S.job_count[l] = count;
-            total_chunks += nch;
-        }
-        S.pending = total_chunks;
-        S.status = 2;
-        B.status_out[r] = 2;
-        atomicAdd(&B.ctl->live, 1);
+    if (lane == 0) {
+        const int st = *(volatile int32_t *)&S.status;
+        B.status_out[r] = st;
+        if (st == 2) atomicAdd(&B.ctl->live, 1);
     }
-    __syncthreads();
-    for (int l = 0; l < nl; ++l) {
-        const int nch = s_nch[l];
-        for (int i = t; i < nch; i += kSchedThreads) {
-            const long long first = S.have[l] + (long long)i * s_ch[l];
-            long long cnt = S.have[l] + S.job_count[l] - first;
-            if (cnt > s_ch[l]) cnt = s_ch[l];
-            Chunk c;
-            c.req = r;
-            c.level = l;
-            c.first = (unsigned long long)first;
-            c.count = (int32_t)cnt;
-            c.listed = s_lb[l] >= 0 ? 1 : 0;
-            B.queue[(unsigned long long)(s_cb[l] + i) & B.cap_mask] = c;
-            if (s_lb[l] >= 0)
-                B.long_ids[(unsigned long long)(s_lb[l] + i) & B.cap_mask] = (unsigned long long)(s_cb[l] + i);
-        }
-    }
-    __syncthreads();
-    if (t == 0)
-        for (int l = 0; l < nl; ++l)
-            if (s_nch[l] > 0) S.have[l] += S.job_count[l];
 }
 
-// Trims the queue head after a slice and publishes the loop condition.
+// Counts the loop iteration and publishes the loop condition (no request
+// live, or a bounded wait ran out).
 __global__ void batch_post_kernel(BatchCtl *ctl, int *live_out, cudaGraphConditionalHandle h, int use_graph)
 {
-    if (ctl->q_head > ctl->q_tail) ctl->q_head = ctl->q_tail;
-    if (ctl->l_head > ctl->l_tail) ctl->l_head = ctl->l_tail;
     ctl->iterations += 1;
-    const int live = ctl->live;
+    const int live = ctl->error ? 0 : ctl->live;
     ctl->live = 0;
     if (live_out) *live_out = live;
     if (use_graph) cudaGraphSetConditional(h, live > 0 ? 1u : 0u);
@@ -664,8 +818,8 @@ __global__ void batch_post_kernel(BatchCtl *ctl, int *live_out, cudaGraphConditi
 // Host side.
 // ---------------------------------------------------------------------------
 struct BatchLayout {
-    size_t desc, state, queue, longq, rows, hist, ctl, live, hdr, lanes, status, total;
-    unsigned long long cap;
+    size_t desc, state, chunks, rows, qids, lids, hist, ctl, live, hdr, lanes, status, total;
+    unsigned long long ring;
 };
 
 static bool batch_cfg_ok(const mlkd_batch_config *c)
@@ -683,16 +837,21 @@ static bool batch_cfg_ok(const mlkd_batch_config *c)
 static BatchLayout batch_layout(const mlkd_batch_config *c)
 {
     BatchLayout B;
-    unsigned long long need = (unsigned long long)c->max_requests * kBL * kMaxChunksPerJob;
-    unsigned long long cap = 1024;
-    while (cap < need) cap <<= 1;
-    B.cap = cap;
+    // Each request slot owns kSlotChunks chunk ids (a request has at most one
+    // round outstanding).  The id queues hold at most every slot's ids at
+    // once; twice that keeps a claimed id's ring cell from being reused
+    // before its claimer has read it.
+    const unsigned long long ids = (unsigned long long)c->max_requests * kSlotChunks;
+    unsigned long long ring = 1024;
+    while (ring < 2 * ids) ring <<= 1;
+    B.ring = ring;
     size_t off = arena_layout().total;
     B.desc = off;  off = align_up(off + (size_t)c->max_requests * sizeof(ReqDesc));
     B.state = off; off = align_up(off + (size_t)c->max_requests * sizeof(ReqState));
-    B.queue = off; off = align_up(off + (size_t)cap * sizeof(Chunk));
-    B.longq = off; off = align_up(off + (size_t)cap * sizeof(unsigned long long));
-    B.rows = off;  off = align_up(off + (size_t)cap * kPartialWords * sizeof(double));
+    B.chunks = off; off = align_up(off + (size_t)ids * sizeof(Chunk));
+    B.rows = off;  off = align_up(off + (size_t)ids * kPartialWords * sizeof(double));
+    B.qids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
+    B.lids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
     B.hist = off;  off = align_up(off + (size_t)c->max_requests * kBL * 3 * (size_t)(c->max_nbins > 0 ? c->max_nbins : 1) * sizeof(unsigned long long));
     B.ctl = off;   off = align_up(off + sizeof(BatchCtl));
     B.live = off;  off = align_up(off + sizeof(int));
@@ -787,15 +946,16 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     std::memset(B, 0, sizeof(*B));
     B->req = (const ReqDesc *)(ctx->arena + BL.desc);
     B->state = (ReqState *)(ctx->arena + BL.state);
-    B->queue = (Chunk *)(ctx->arena + BL.queue);
+    B->chunks = (Chunk *)(ctx->arena + BL.chunks);
     B->rows = (double *)(ctx->arena + BL.rows);
     B->hist = (unsigned long long *)(ctx->arena + BL.hist);
     B->ctl = (BatchCtl *)(ctx->arena + BL.ctl);
     B->hdr = (WarpHdr *)(ctx->arena + BL.hdr);
     B->lane_words = (uint32_t *)(ctx->arena + BL.lanes);
-    B->long_ids = (unsigned long long *)(ctx->arena + BL.longq);
+    B->q_ids = (unsigned long long *)(ctx->arena + BL.qids);
+    B->l_ids = (unsigned long long *)(ctx->arena + BL.lids);
     B->status_out = (int32_t *)(ctx->arena + BL.status);
-    B->cap_mask = BL.cap - 1;
+    B->ring_mask = BL.ring - 1;
     B->max_nbins = cfg->max_nbins > 0 ? cfg->max_nbins : 1;
     B->slice_iters = cfg->substeps_per_launch;
     B->refill_min = cfg->refill_min > 0 ? cfg->refill_min : kRefillMin;
@@ -808,7 +968,7 @@ static mlkd_status enqueue_body(mlkd_context *ctx, const BatchLaunch &B, int mod
                                 cudaGraphConditionalHandle h, int use_graph, int *live_dev,
                                 cudaStream_t s)
 {
-    batch_sched_kernel<<<B.n_slots, kSchedThreads, 0, s>>>(B);
+    batch_sched_kernel<<<B.n_slots, 32, 0, s>>>(B);
     MLKD_CUDA(cudaGetLastError());
     const size_t smem = (size_t)kWarpsPerBlock * 3 * B.max_nbins * sizeof(unsigned int);
     // host-loop form: the pair slice is timed like the per-level kernel
@@ -952,6 +1112,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         MLKD_CUDA(cudaMemcpyAsync(hh.data(), ctx->arena + BL.hist, hist_bytes, cudaMemcpyDeviceToHost, s));
     }
     MLKD_CUDA(cudaStreamSynchronize(s));
+    if (hctl.error) return MLKD_ETIMEDOUT;
     if (cfg->use_graph) {
         ctx->launches += (unsigned long long)hctl.iterations;
         ctx->other_launches += 2ull * (unsigned long long)hctl.iterations;
@@ -1167,11 +1328,14 @@ static void server_loop(Server *S)
             }
         }
         const double t_it = S->now();
-        unsigned long long events = 0;
+        struct {
+            unsigned long long events, events_done;
+            int32_t running, error;
+        } tail = {0, 0, 0, 0};
         if (cudaGraphLaunch(S->exec, S->stream) != cudaSuccess ||
             cudaMemcpyAsync(S->slot_status.data(), S->B.status_out, n * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, S->stream) != cudaSuccess ||
-            cudaMemcpyAsync(&events, &S->B.ctl->events, sizeof(events), cudaMemcpyDeviceToHost,
+            cudaMemcpyAsync(&tail, &S->B.ctl->events, sizeof(tail), cudaMemcpyDeviceToHost,
                             S->stream) != cudaSuccess ||
             cudaStreamSynchronize(S->stream) != cudaSuccess) {
             std::lock_guard<std::mutex> lk(S->mu);
@@ -1183,7 +1347,14 @@ static void server_loop(Server *S)
         std::lock_guard<std::mutex> lk(S->mu);
         S->stats.iterations += 1;
         S->stats.busy_seconds += S->now() - t_it;
-        S->stats.events = events;
+        S->stats.events = tail.events;
+        S->stats.events_processed = tail.events_done;
+        if (tail.error) {
+            S->error = MLKD_ETIMEDOUT;
+            S->stop = true;
+            S->cv_done.notify_all();
+            break;
+        }
         bool any_done = false;
         for (int slot = 0; slot < n; ++slot) {
             const uint64_t id = S->slot_req[slot];
@@ -1273,7 +1444,7 @@ static mlkd_status server_start(mlkd_context *ctx, const mlkd_server_config *cfg
     // one iteration as a graph: scheduler, pair slice, bookkeeping
     if (cudaStreamBeginCapture(S->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(MLKD_ECUDA);
     int *live_dev = (int *)(ctx->arena + BL.live);
-    batch_sched_kernel<<<n, kSchedThreads, 0, S->stream>>>(S->B);
+    batch_sched_kernel<<<n, 32, 0, S->stream>>>(S->B);
     const size_t smem = (size_t)kWarpsPerBlock * 3 * S->B.max_nbins * sizeof(unsigned int);
     pick_batch(S->mode, S->ppt)<<<S->grid, kThreads, smem, S->stream>>>(S->B);
     batch_post_kernel<<<1, 1, 0, S->stream>>>(S->B.ctl, live_dev, 0, 0);

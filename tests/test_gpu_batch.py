@@ -210,3 +210,20 @@ def test_refill_threshold_changes_only_sum_order(mk, ctx):
         assert x.estimate == pytest.approx(y.estimate, rel=1e-12, abs=1e-15)
         if x.density is not None:
             np.testing.assert_allclose(x.density, y.density, rtol=1e-12, atol=1e-12)
+
+
+def test_round_cut_by_chunk_capacity_continues(mk, ctx):
+    """A level needing more pairs than one round's chunk budget (at most four
+    times the target chunk size) is split over several rounds with the same
+    targets: pair and event counts equal those of the per-level form, which
+    runs each level in one launch."""
+    d = dict(eps=1e-3, T=1.0, dt0=0.5, M=2, L=9, qoi=1, init=1, nbins=0, seed=7, request=3,
+             n_fixed=[1000] * 9 + [300_000])
+    p = gpu_problem(mk, d, precision=mk.PREC_FP32_DY64)
+    (b,) = ctx.estimate_batch([p], mk.batch_config(max_requests=64, max_nbins=128))
+    r = ctx.estimate(p)
+    assert [lv["n"] for lv in b.levels] == d["n_fixed"] == [lv["n"] for lv in r.levels]
+    for lb, lr in zip(b.levels, r.levels):
+        assert lb["events_f"] == lr["events_f"] and lb["events_c"] == lr["events_c"]
+        assert lb["sy"] == pytest.approx(lr["sy"], rel=1e-9, abs=1e-9)
+    assert b.estimate == pytest.approx(r.estimate, rel=1e-9, abs=1e-12)

@@ -83,6 +83,7 @@ def test_result_same_alone_and_in_the_mix(mk):
         ev = sum(lv["events_f"] + lv["events_c"] for r in [alone] + list(results.values())
                  for lv in r.levels)
         assert st["events"] == ev
+        assert st["events_processed"] == ev          # every chunk finished and merged
     finally:
         ctx.server_stop()
         ctx.close()
