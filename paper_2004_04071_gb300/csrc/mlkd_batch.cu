@@ -29,16 +29,15 @@
 namespace mlkd {
 
 constexpr int kBL = MLKD_MAX_LEVELS;            // levels per request
-constexpr int kMaxChunksPerJob = 2048;           // chunks per level and round, on average
+constexpr int kMaxChunksPerJob = 2048;           // chunks per level and round, at most
 constexpr int kChunkQuantum = 32;                // chunk sizes are multiples of one pair per lane
 constexpr int kTargetIters = 1024;               // target warp iterations per chunk
 constexpr double kPairStartIters = 2.0;          // start + summation of a pair, in event iterations
 constexpr long long kMaxChunkPairs = 1LL << 22;  // pairs per chunk at most
-constexpr long long kMaxChunkGrow = 4;           // chunk enlargement to fit a round, at most
+constexpr long long kMaxChunkGrow = 8;           // chunk enlargement to fit a round, at most
 constexpr long long kRoundChunks = (long long)kBL * kMaxChunksPerJob;  // chunks of one request per round
-// chunk ids owned by one request slot: a round's chunks, plus one per level
-// where a proportional cut rounds a level's share up
-constexpr long long kSlotChunks = kRoundChunks + kBL;
+// chunk ids owned by one request slot: one round's chunks
+constexpr long long kSlotChunks = kRoundChunks;
 constexpr int kPublishSpins = 1 << 22;           // bounded wait for earlier reservations to publish
 constexpr int kIdleSpins = 4096;                 // bounded wait for new work: sleeps of up to 64 us, about 0.25 s
 
@@ -359,11 +358,11 @@ __device__ __noinline__ bool warp_controller(const BatchLaunch &B, int r, int la
 
 // Plans the next round toward S.target, finest level first, and publishes
 // its chunks in the request's own chunk-id range.  A round holds at most
-// kRoundChunks chunks: chunks grow (the same factor on every level, at most
-// kMaxChunkGrow) until it fits; a request that still needs more gets every
-// level's share cut in proportion, and the next round continues with the
-// same targets, so that no chunk holds a warp much longer than a target
-// slice however many pairs a request asks for.
+// kMaxChunksPerJob chunks per level: a level that needs more target-size
+// chunks gets chunks up to kMaxChunkGrow times larger, and beyond that its
+// round is cut and the next round continues with the same targets, so that
+// no chunk holds a warp much longer than a target slice however many pairs a
+// request asks for.
 __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
 {
     ReqState &S = B.state[r];
@@ -387,27 +386,25 @@ __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
             epps[l] = epp;
             tch[l] = chunk_target(epp);
         }
-        long long grow = 1, chunks = 0;
-        for (;;) {
-            chunks = 0;
-            for (int l = 0; l < nl; ++l) chunks += (want[l] + grow * tch[l] - 1) / (grow * tch[l]);
-            if (chunks <= kRoundChunks || grow >= kMaxChunkGrow) break;
-            grow *= 2;
-        }
         int total = 0;
         for (int l = nl - 1; l >= 0; --l) {
             S.job_nch[l] = 0;
             S.job_count[l] = 0;
             long long count = want[l];
             if (count <= 0) continue;
-            const long long ch = grow * tch[l];
-            tch[l] = ch;
+            long long ch = tch[l];
             long long nch = (count + ch - 1) / ch;
-            if (chunks > kRoundChunks) {
-                nch = nch * kRoundChunks / chunks;
-                if (nch < 1) nch = 1;
-                if (count > nch * ch) count = nch * ch;
+            if (nch > kMaxChunksPerJob) {
+                long long g = (nch + kMaxChunksPerJob - 1) / kMaxChunksPerJob;
+                if (g > kMaxChunkGrow) g = kMaxChunkGrow;
+                ch *= g;
+                nch = (count + ch - 1) / ch;
+                if (nch > kMaxChunksPerJob) {
+                    nch = kMaxChunksPerJob;
+                    count = nch * ch;
+                }
             }
+            tch[l] = ch;
             S.job_cb[l] = (long long)(slot0 + (unsigned long long)total);
             S.job_nch[l] = (int32_t)nch;
             S.job_count[l] = count;

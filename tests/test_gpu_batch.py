@@ -213,12 +213,13 @@ def test_refill_threshold_changes_only_sum_order(mk, ctx):
 
 
 def test_round_cut_by_chunk_capacity_continues(mk, ctx):
-    """A level needing more pairs than one round's chunk budget (at most four
-    times the target chunk size) is split over several rounds with the same
-    targets: pair and event counts equal those of the per-level form, which
-    runs each level in one launch."""
+    """A level needing more pairs than one round holds (2048 chunks of at
+    most eight times the target size: 2048 * 8 * 32 pairs at this level,
+    where one pair per lane already fills a chunk) is split over several
+    rounds with the same targets: pair and event counts equal those of the
+    per-level form, which runs each level in one launch."""
     d = dict(eps=1e-3, T=1.0, dt0=0.5, M=2, L=9, qoi=1, init=1, nbins=0, seed=7, request=3,
-             n_fixed=[1000] * 9 + [300_000])
+             n_fixed=[1000] * 9 + [600_000])
     p = gpu_problem(mk, d, precision=mk.PREC_FP32_DY64)
     (b,) = ctx.estimate_batch([p], mk.batch_config(max_requests=64, max_nbins=128))
     r = ctx.estimate(p)
