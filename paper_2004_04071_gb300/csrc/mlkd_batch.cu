@@ -39,6 +39,7 @@ constexpr long long kRoundChunks = (long long)kBL * kMaxChunksPerJob;  // chunks
 // chunk ids owned by one request slot: one round's chunks
 constexpr long long kSlotChunks = kRoundChunks;
 constexpr int kPublishSpins = 1 << 22;           // bounded wait for earlier reservations to publish
+constexpr double kSmallRoundEvents = 2e8;        // predicted KD events of a round that goes first (about 2 ms)
 constexpr int kIdleSpins = 4096;                 // bounded wait for new work: sleeps of up to 64 us, about 0.25 s
 
 struct ReqDesc {
@@ -68,7 +69,7 @@ struct ReqState {
     double var_level[kBL], cost_level[kBL];
     long long target[kBL];
     long long job_ch[kBL];      // pairs per chunk of this round's job per level
-    int32_t job_long[kBL];      // 1: the level's chunks go to the long-chunk queue
+    int32_t job_queue[kBL];     // queue of the level's chunks: 0 main, 1 long chunks, 2 small rounds
     long long plan_want[kBL];   // planning scratch: pairs wanted per level
     double plan_epp[kBL];       // planning scratch: events per pair per level
     int32_t counted;            // 1: counted in BatchCtl::running
@@ -88,8 +89,10 @@ struct Chunk {
 // both are plain atomic adds, which stay fast with thousands of claimers.
 struct BatchCtl {
     unsigned long long q_head, q_tail, q_resv;
-    unsigned long long l_head, l_tail, l_resv;   // chunks longer than a target slice, drained first
+    unsigned long long l_head, l_tail, l_resv;   // chunks longer than a target slice
+    unsigned long long p_head, p_tail, p_resv;   // rounds of little predicted work, drained first
     int32_t q_avail, l_avail;   // published ids not yet claimed
+    int32_t p_avail, pad_;
     int32_t live;
     int32_t iterations;         // loop iterations run (three kernel launches each)
     unsigned long long events;  // fine + coarse events merged into request sums so far
@@ -120,6 +123,7 @@ struct BatchLaunch {
     uint32_t *lane_words;        // [words][grid lanes]: pair states and sums per lane
     unsigned long long *q_ids;   // [ring]: queue of chunk ids
     unsigned long long *l_ids;   // [ring]: queue of long chunks' ids
+    unsigned long long *p_ids;   // [ring]: queue of the chunks of small rounds
     unsigned long long ring_mask;
     int32_t max_nbins;
     int32_t slice_iters;
@@ -387,6 +391,7 @@ __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
             tch[l] = chunk_target(epp);
         }
         int total = 0;
+        double work = 0.0;
         for (int l = nl - 1; l >= 0; --l) {
             S.job_nch[l] = 0;
             S.job_count[l] = 0;
@@ -409,9 +414,16 @@ __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
             S.job_nch[l] = (int32_t)nch;
             S.job_count[l] = count;
             // one pair per lane already exceeds a target slice: the long queue
-            S.job_long[l] = epps[l] > (double)kTargetIters ? 1 : 0;
+            S.job_queue[l] = epps[l] > (double)kTargetIters ? 1 : 0;
+            work += (double)count * epps[l];
             total += (int)nch;
         }
+        // A round of little predicted work (a warm-up round, or a request
+        // near its tolerance) goes ahead of all other work: under load,
+        // cheap requests finish in about their own run time instead of
+        // sharing the GPU with every heavy request in flight.
+        if (work <= kSmallRoundEvents)
+            for (int l = 0; l < nl; ++l) S.job_queue[l] = 2;
         S.pending = total;
         S.status = 2;
     }
@@ -442,7 +454,10 @@ __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
     for (int l = nl - 1; l >= 0; --l) {
         const int nch = S.job_nch[l];
         if (nch == 0) continue;
-        if (S.job_long[l])
+        if (S.job_queue[l] == 2)
+            push_ids(B, B.p_ids, &B.ctl->p_resv, &B.ctl->p_tail, &B.ctl->p_avail,
+                     (unsigned long long)S.job_cb[l], nch, lane);
+        else if (S.job_queue[l] == 1)
             push_ids(B, B.l_ids, &B.ctl->l_resv, &B.ctl->l_tail, &B.ctl->l_avail,
                      (unsigned long long)S.job_cb[l], nch, lane);
         else
@@ -593,9 +608,9 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     for (;;) {
         if (!valid) {
             if (B.slice_iters > 0 && iters >= B.slice_iters) break;
-            // Chunks whose single pairs outlast a target slice (deep levels)
-            // come from their own queue first, so that the longest work
-            // starts earliest.  With nothing published, a warp of an
+            // Claim order: chunks of small rounds, then chunks whose single
+            // pairs outlast a target slice (deep levels, so that the longest
+            // serial work starts earliest), then the rest.  With nothing published, a warp of an
             // unbounded launch waits (a bounded time) while some request
             // still has a round in flight: the warp finishing that round
             // publishes the next one.  In a sliced launch it leaves at once;
@@ -603,7 +618,8 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             unsigned long long cn = 0;
             int got = 0;
             if (lane == 0) {
-                got = claim_id(B, &B.ctl->l_avail, &B.ctl->l_head, B.l_ids, &cn);
+                got = claim_id(B, &B.ctl->p_avail, &B.ctl->p_head, B.p_ids, &cn);
+                if (!got) got = claim_id(B, &B.ctl->l_avail, &B.ctl->l_head, B.l_ids, &cn);
                 if (!got) got = claim_id(B, &B.ctl->q_avail, &B.ctl->q_head, B.q_ids, &cn);
             }
             got = __shfl_sync(kFullMask, got, 0);
@@ -815,7 +831,7 @@ __global__ void batch_post_kernel(BatchCtl *ctl, int *live_out, cudaGraphConditi
 // Host side.
 // ---------------------------------------------------------------------------
 struct BatchLayout {
-    size_t desc, state, chunks, rows, qids, lids, hist, ctl, live, hdr, lanes, status, total;
+    size_t desc, state, chunks, rows, qids, lids, pids, hist, ctl, live, hdr, lanes, status, total;
     unsigned long long ring;
 };
 
@@ -849,6 +865,7 @@ static BatchLayout batch_layout(const mlkd_batch_config *c)
     B.rows = off;  off = align_up(off + (size_t)ids * kPartialWords * sizeof(double));
     B.qids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
     B.lids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
+    B.pids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
     B.hist = off;  off = align_up(off + (size_t)c->max_requests * kBL * 3 * (size_t)(c->max_nbins > 0 ? c->max_nbins : 1) * sizeof(unsigned long long));
     B.ctl = off;   off = align_up(off + sizeof(BatchCtl));
     B.live = off;  off = align_up(off + sizeof(int));
@@ -951,6 +968,7 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->lane_words = (uint32_t *)(ctx->arena + BL.lanes);
     B->q_ids = (unsigned long long *)(ctx->arena + BL.qids);
     B->l_ids = (unsigned long long *)(ctx->arena + BL.lids);
+    B->p_ids = (unsigned long long *)(ctx->arena + BL.pids);
     B->status_out = (int32_t *)(ctx->arena + BL.status);
     B->ring_mask = BL.ring - 1;
     B->max_nbins = cfg->max_nbins > 0 ? cfg->max_nbins : 1;

@@ -50,9 +50,19 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
-    // sqrt of x >= 0 as x * rsqrt(x) (relative error about 2^-22, inside the
-    // FP32 modes' per-event bound); 0 for x <= 0.
-    static __device__ __forceinline__ float sqrt_pos_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+    // sqrt of x >= 0 from y = x * rsqrt(x) and one Newton correction
+    // y + (x - y^2) rsqrt(x)/2 (Heron's step), without a branch; 0 for x <= 0.
+    // The raw product alone is biased by up to about 2^-22 relative, which
+    // shows in the fine-minus-coarse means; the corrected root does not.
+    static __device__ __forceinline__ float sqrt_pos_(float x)
+    {
+        const float r = rsqrtf(fmaxf(x, 1e-37f));
+        const float y = x * r;
+        const float z = fmaf(fmaf(-y, y, x), 0.5f * r, y);
+        return x > 0.0f ? z : 0.0f;
+    }
+    // the raw product, for uses whose bias cancels
+    static __device__ __forceinline__ float sqrt_pos_fast_(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
     static __device__ __forceinline__ float cbrt_(float x) { return cbrtf(x); }
     static __device__ __forceinline__ void sincospi_(float x, float *s, float *c) { sincospif(x, s, c); }
     static __device__ __forceinline__ float sinpi_(float x) { return sinpif(x); }
