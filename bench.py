@@ -43,6 +43,11 @@ TOL = 1e-3
 # the KD coefficients and position update, the aggregation weights.  Stated
 # with its derivation in the design notes; the ncu summary
 # profiles/pair_kernel_fp32_periodic.md gives the measured count.
+# DRAM bytes (read + written) of one full-size launch of the batched pair
+# kernel on this workload, from ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum; profiles/batch_pair_kernel_periodic.md).  A counter
+# taken for one build of the kernel: re-take it whenever the kernel changes.
+DRAM_BYTES_PER_LAUNCH = 1157120 + 4096
 INST_PER_FINE_EVENT = 190.0
 INST_PER_COARSE_EVENT = 50.0
 SMSP_PER_SM = 4
@@ -309,7 +314,9 @@ def run_gpu(args):
         "gpu_launches": int(timing["launches"] + timing["other_launches"]),
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                      "unit": "Ginst/s (lane instructions)",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None,
+                     "traffic": DRAM_BYTES_PER_LAUNCH if args.form == "batch" and args.precision == "fp32comp" else None,
+                     "traffic_unit": "bytes per launch that carries the step's pairs (ncu)",
                      "kernel": kname,
                      "launches_timed": rt["launches"],
                      "avg_launch_ms": rt["pair_kernel_ms"] / max(1, rt["launches"]),
