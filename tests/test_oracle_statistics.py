@@ -13,12 +13,18 @@
   run at dt_{l-1} (two-sample tests).
 * Telescoping (eq. telsum): sum of level means = finest-level mean.
 * Sample counts (eqs. Nopt1/Noptj) and the MLMC error bound (eq. mse).
+* Shape of the level-difference variance and cost in the homogeneous case
+  (Sec. 5.2): V_{l,l-1} grows as dt_l shrinks until a maximum near
+  dt_l = 1/R, then decays like dt_l^3; C_{l,l-1} grows linearly with 1/dt_l
+  until that point and is flat beyond it.
 """
 import math
 
 import numpy as np
 import pytest
 from scipy import stats
+
+from helpers import check_level_curve, level_curve
 
 
 def msd(eps, T, mu=0.0):
@@ -176,3 +182,14 @@ def test_density_counts_consistent(orc):
     assert np.all(s.hist_both <= np.minimum(s.hist_f, s.hist_c))
     # sum over pairs of Y_b^2 = f + c - 2 both >= |sum Y_b|
     assert np.all(s.hist_f + s.hist_c - 2 * s.hist_both >= np.abs(s.hist_f - s.hist_c))
+
+
+def test_level_variance_and_cost_curve(orc):
+    eps = 0.1
+    p = orc.Problem(eps=eps, T=1.0, dt0=0.5, M=2, L=12, qoi=0, init=0, nbins=0, seed=5)
+
+    def sums(level, n):
+        s = orc.run_level(p, level, 0, n, threads=8)
+        return s.sy, s.sy2, s.n, s.events_f + s.events_c
+
+    check_level_curve(level_curve(sums, 12, 6000), 1.0 / eps ** 2)
