@@ -227,19 +227,24 @@ MLKD_API mlkd_status mlkd_context_get_timing(mlkd_context *ctx, mlkd_kernel_timi
 
 /* ---------------------------------------------------------------------------
  * Batched form: many independent estimates (different eps, T, levels, QoI,
- * tolerances) advanced together by one persistent pair kernel that pulls
- * chunks of (request, level, pair range) from a device work queue.  Between
- * slices a scheduler kernel finalizes every request whose round is complete
- * (fixed-order FP64 sums of its chunk rows), runs the controller of Sec. 4.1
- * for it and appends its next round, so requests never wait for one another's
- * rounds.  With use_graph the whole loop is one CUDA graph whose device-side
- * while-node repeats [scheduler, pair slice, bookkeeping] until every request
- * has met its tolerance.
+ * tolerances) advanced together by one persistent pair kernel whose warps
+ * claim chunks of (request, level, pair range) from device queues: chunks of
+ * small rounds first, then chunks of deep levels, then the rest.  The warp
+ * that finishes the last chunk of a request's round finalizes it (fixed-order
+ * FP64 sums of its chunk rows), runs the controller of Sec. 4.1 for it and
+ * publishes its next round on the spot, so requests never wait for one
+ * another's rounds.  A scheduler kernel between slices admits requests and
+ * frees cancelled ones.  With use_graph the whole loop is one CUDA graph
+ * whose device-side while-node repeats [scheduler, pair slice, bookkeeping]
+ * until every request has met its tolerance.  Every wait on the device is
+ * bounded; one that runs out ends the call with MLKD_ETIMEDOUT.
  * ------------------------------------------------------------------------- */
 typedef struct {
     int32_t pairs_per_thread;    /* pair states per lane, advanced together: 1, 2, 4 or 8   */
     int32_t substeps_per_launch; /* event iterations per warp per pair-kernel launch; a chunk
-                                    in progress is stored and resumed (0: no limit)          */
+                                    in progress is stored and resumed (0: no limit: a launch
+                                    runs until every request is done, or until no work has
+                                    appeared for about 0.25 s)                              */
     int32_t use_graph;           /* 1: one CUDA graph with a device-side loop                 */
     int32_t max_requests;        /* request slots of the batch region (<= 4096)             */
     int32_t max_nbins;           /* histogram bins per request (<= 256)                      */
