@@ -228,3 +228,35 @@ def test_round_cut_by_chunk_capacity_continues(mk, ctx):
         assert lb["events_f"] == lr["events_f"] and lb["events_c"] == lr["events_c"]
         assert lb["sy"] == pytest.approx(lr["sy"], rel=1e-9, abs=1e-9)
     assert b.estimate == pytest.approx(r.estimate, rel=1e-9, abs=1e-12)
+
+
+def test_full_size_periodic_step_matches_per_level_form(mk):
+    """The benchmark's step at full size, in the configuration it times
+    (one pair per lane, unbounded slices, CUDA graph, compensated FP32):
+    N_l from the same adaptive pilot at tol 1e-3, then the three fixed-N
+    estimates batched against the per-level form, whose pairs are pinned to
+    the oracle one by one.  Pair counts equal; event counts, estimates and
+    densities equal to FP32 rounding (separate compilations may round a
+    flight's floor differently for a rare pair)."""
+    cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=0, use_graph=1, max_requests=16,
+                          max_nbins=128)
+    ctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
+    try:
+        dicts = [dict(W.periodic_problem(e, seed=0, tol=1e-3), request=i)
+                 for i, e in enumerate(W.PERIODIC_EPS)]
+        prec = mk.PREC_FP32_COMP
+        pilot = ctx.estimate_batch([mk.make_problem(precision=prec, **d) for d in dicts], cfg)
+        fixed = [[lv["n"] for lv in r.levels] for r in pilot]
+        assert sum(fixed[1]) > 2.5e7                       # the full size: about 9e6 level-0 pairs
+        probs = [mk.make_problem(precision=prec, n_fixed=n, **d) for d, n in zip(dicts, fixed)]
+        batched = ctx.estimate_batch(probs, cfg)
+        for p, n, b in zip(probs, fixed, batched):
+            r = ctx.estimate(p)
+            assert [lv["n"] for lv in b.levels] == n == [lv["n"] for lv in r.levels]
+            for lb, lr in zip(b.levels, r.levels):
+                for k in ("events_f", "events_c"):
+                    assert abs(lb[k] - lr[k]) <= 1e-6 * lr[k] + 2
+            assert b.estimate == pytest.approx(r.estimate, rel=1e-6, abs=1e-9)
+            np.testing.assert_allclose(b.density, r.density, rtol=0, atol=1e-3)
+    finally:
+        ctx.close()

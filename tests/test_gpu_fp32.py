@@ -87,3 +87,25 @@ def test_fp32_level_sums_close_to_fp64(orc, mk, ctx, precision):
         mo, mg = so.sy / so.n, sg["sy"] / sg["n"]
         vo = so.var()
         assert abs(mg - mo) < 3 * math.sqrt(vo / so.n) + 1e-6
+
+
+def test_fp32_full_launch_sampled(orc, mk, ctx):
+    """Full launch size of the benchmark's busiest coupled level (eps = 0.1,
+    level 8, about 8e5 pairs): 400 sampled pairs against the oracle on the
+    same 24-bit stream, one by one, within the FP32 bound."""
+    d = W.periodic_problem(0.1)
+    level, n = 8, 802_694
+    xf, xc, kf, kc = ctx.debug_pairs(gpu_problem(mk, d, precision=mk.PREC_FP32_COMP), level, 0, n)
+    rng = np.random.default_rng(1)
+    idx = np.sort(rng.choice(n, 400, replace=False))
+    po = oracle_problem(orc, d, recipe=orc.RECIPE_24)
+    flips = 0
+    for j in idx:
+        a = orc.pairs(po, level, int(j), 1)
+        if kf[j] != a[2][0] or kc[j] != a[3][0]:
+            flips += 1
+            continue
+        ev = a[2][0] + a[3][0] + 1
+        for x, ref in ((xf[j], a[0][0]), (xc[j], a[1][0])):
+            assert abs(x - ref) <= FP32_C * ev * 2.0 ** -24 * max(1.0, abs(ref))
+    assert flips <= 1
