@@ -48,6 +48,9 @@ TOL = 1e-3
 # dram__bytes_write.sum; profiles/batch_pair_kernel_periodic.md).  A counter
 # taken for one build of the kernel: re-take it whenever the kernel changes.
 DRAM_BYTES_PER_LAUNCH = 1157120 + 4096
+# From the same capture: warp instructions issued over (4 per SM per cycle x
+# elapsed cycles), i.e. the measured use of the FP32/INT issue slots.
+ISSUE_FRACTION_NCU = 0.757
 INST_PER_FINE_EVENT = 190.0
 INST_PER_COARSE_EVENT = 50.0
 SMSP_PER_SM = 4
@@ -317,6 +320,7 @@ def run_gpu(args):
                      "frac": achieved / peak if peak else None,
                      "traffic": DRAM_BYTES_PER_LAUNCH if args.form == "batch" and args.precision == "fp32comp" else None,
                      "traffic_unit": "bytes per launch that carries the step's pairs (ncu)",
+                     "issue_fraction_ncu": ISSUE_FRACTION_NCU if args.form == "batch" and args.precision == "fp32comp" else None,
                      "kernel": kname,
                      "launches_timed": rt["launches"],
                      "avg_launch_ms": rt["pair_kernel_ms"] / max(1, rt["launches"]),
