@@ -202,6 +202,28 @@ MLKD_API mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *pro
 MLKD_API mlkd_status mlkd_level_select(const double *V, const double *Vd, int L, int32_t *set_out,
                                        int32_t *n_out);
 
+/* Level selection by optimisation (Sec. 4.2, eqs. level_selection and
+ * integerLP): given V[i] = Var(F(x_i)) and C[i] (cost per path, here KD events)
+ * for i = 0..L, and rho[i] = corr(F(x_L), F(x_i)) for i = 0..L-1, writes the
+ * level set containing L that minimises
+ *     sqrt(V_{l1} C_{l1}) + sum_j sqrt(V_{lj,lj-1} C_{lj,lj-1}),
+ * with V_{i,j} from eq. V_approx (a negative root argument read as 0) and
+ * C_{i,j} = C_i + C_j.  The integer program of eq. integerLP describes a path
+ * through increasing levels ending at L; it is solved exactly as a shortest
+ * path by dynamic programming.  set_out needs room for L+1.  MLKD_EINVAL for
+ * a negative V or C or a rho outside [-1, 1].  Host only. */
+MLKD_API mlkd_status mlkd_level_select_opt(const double *V, const double *rho, const double *C, int L,
+                                           int32_t *set_out, int32_t *n_out);
+
+/* Pilot statistics for mlkd_level_select_opt (Sec. 4.2): n pairs coupling
+ * the finest level L with each level i < L (level sets {i, L}) give V[i] and
+ * C[i] from the coarse path, rho[i] from the pair, and V[L], C[L] from the
+ * fine path (the same pairs in every coupling).  Arrays of L+1, L and L+1
+ * doubles.  The QoI must be scalar (MLKD_EINVAL for a density) and L >= 1,
+ * n >= 2.  Runs L launches of the pair kernel.  Synchronous. */
+MLKD_API mlkd_status mlkd_level_pilot(mlkd_context *ctx, const mlkd_problem *problem, uint64_t n,
+                                      void *stream, double *V, double *rho, double *C);
+
 /* Validation aid: the FP32 variate transforms of the pair kernel applied to
  * n 32-bit Philox output words (device array `words`).  With the 24-bit
  * uniform u = ((w >> 8) + 1) 2^-24 of each word it writes log u, sin 2 pi u and

@@ -454,6 +454,65 @@ def level_select(V, Vd):
     return chosen
 
 
+def v_pair_approx(V_i, V_j, rho_Li, rho_Lj):
+    """Sec. 4.2, eq. V_approx: V_{i,j} ~ V_i + V_j - 2 sqrt((rho_{L,i}^2 +
+    rho_{L,j}^2 - 1) V_i V_j), rho_{i,j} taken as the geometric mean of its
+    bounds.  A negative argument of the root (the bounds admit rho_{i,j} = 0)
+    is read as 0: V_{i,j} = V_i + V_j."""
+    arg = (rho_Li * rho_Li + rho_Lj * rho_Lj - 1.0) * V_i * V_j
+    return V_i + V_j - 2.0 * math.sqrt(max(arg, 0.0))
+
+
+def level_set_cost(levels, V, rho, C):
+    """Cost of eq. level_selection for the level set `levels` (increasing,
+    ending at L): sqrt(V_{l1} C_{l1}) + sum_j sqrt(V_{lj,lj-1} C_{lj,lj-1}),
+    with V_{i,j} from eq. V_approx (rho_{L,L} = 1) and C_{i,j} = C_i + C_j
+    (cost measured in KD events of both paths of a pair)."""
+    L = len(V) - 1
+    r = list(rho) + [1.0]
+    total = math.sqrt(V[levels[0]] * C[levels[0]])
+    for a, b in zip(levels[:-1], levels[1:]):
+        total += math.sqrt(max(v_pair_approx(V[b], V[a], r[b], r[a]), 0.0) * (C[a] + C[b]))
+    return total
+
+
+def level_select_opt(V, rho, C):
+    """Sec. 4.2: the level set containing L with the smallest cost of eq.
+    level_selection, found by trying every subset of 0..L-1 (the plain
+    definition; the library solves the same problem as a shortest path)."""
+    L = len(V) - 1
+    best, best_set = None, None
+    for mask in range(1 << L):
+        levels = [i for i in range(L) if mask >> i & 1] + [L]
+        c = level_set_cost(levels, V, rho, C)
+        if best is None or c < best:
+            best, best_set = c, levels
+    return best_set
+
+
+def level_pilot(problem: Problem, n: int, threads: int = 1):
+    """Pilot statistics of Sec. 4.2 for a scalar QoI: n pairs coupling L
+    with each level i < L (level sets {i, L}; the fine path of pair p is the
+    same in every coupling).  Returns V[0..L] (variance of F on each level),
+    rho[0..L-1] (correlation of F(x_L) with F(x_i)) and C[0..L] (KD events per
+    path).  Level i comes from the coarse path of the (i, L) coupling, level L
+    from the fine path of the (L-1, L) one."""
+    L = problem.L
+    V, C, rho = [0.0] * (L + 1), [0.0] * (L + 1), [0.0] * L
+    for i in range(L):
+        q = Problem(**{**problem.__dict__, "level_set": [i, L], "n_fixed": []})
+        xf, xc, ef, ec = pairs(q, 1, 0, n, threads)
+        ff, fc = qoi_values(q, xf), qoi_values(q, xc)
+        cov = np.cov(ff, fc, ddof=1)
+        V[i] = float(cov[1, 1])
+        C[i] = float(np.mean(ec))
+        rho[i] = float(cov[0, 1] / math.sqrt(cov[0, 0] * cov[1, 1])) if cov[0, 0] * cov[1, 1] > 0 else 0.0
+        if i == L - 1:
+            V[L] = float(cov[0, 0])
+            C[L] = float(np.mean(ef))
+    return V, rho, C
+
+
 def optimal_counts(V, C, tol):
     """N_j = ceil(2/tol^2 sqrt(V_j/C_j) sum_i sqrt(V_i C_i))  (eqs. Nopt1/Noptj)."""
     total = sum(math.sqrt(v * c) for v, c in zip(V, C))

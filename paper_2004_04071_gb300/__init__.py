@@ -36,7 +36,8 @@ EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_context_get_timing", "mlkd_run_level_noalloc", "mlkd_batch_workspace_bytes",
             "mlkd_estimate_batch", "mlkd_autotune_batch", "mlkd_server_start", "mlkd_submit",
             "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop",
-            "mlkd_debug_transforms", "mlkd_level_select", "mlkd_estimate_resumable"]
+            "mlkd_debug_transforms", "mlkd_level_select", "mlkd_estimate_resumable",
+            "mlkd_level_select_opt", "mlkd_level_pilot"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -179,6 +180,13 @@ def lib():
         L.mlkd_level_select.argtypes = [P(ctypes.c_double), P(ctypes.c_double), ctypes.c_int,
                                         P(ctypes.c_int32), P(ctypes.c_int32)]
         L.mlkd_level_select.restype = ctypes.c_int
+        L.mlkd_level_select_opt.argtypes = [P(ctypes.c_double), P(ctypes.c_double),
+                                            P(ctypes.c_double), ctypes.c_int,
+                                            P(ctypes.c_int32), P(ctypes.c_int32)]
+        L.mlkd_level_select_opt.restype = ctypes.c_int
+        L.mlkd_level_pilot.argtypes = [vp, P(Problem), u64, vp, P(ctypes.c_double),
+                                       P(ctypes.c_double), P(ctypes.c_double)]
+        L.mlkd_level_pilot.restype = ctypes.c_int
         L.mlkd_estimate_resumable.argtypes = [vp, P(Problem), P(Result), P(ctypes.c_uint64), ctypes.c_int,
                                               vp, P(Result), P(ctypes.c_uint64)]
         L.mlkd_estimate_resumable.restype = ctypes.c_int
@@ -236,6 +244,20 @@ def level_select(V, Vd):
     out = (ctypes.c_int32 * (L + 1))()
     n = ctypes.c_int32()
     _check(lib().mlkd_level_select(v, vd, L, out, ctypes.byref(n)), "mlkd_level_select")
+    return [int(out[i]) for i in range(n.value)]
+
+
+def level_select_opt(V, rho, C):
+    """mlkd_level_select_opt (Sec. 4.2): the cost-optimal level set from
+    V_i = Var(F(x_i)), C_i (i = 0..L) and rho_i = corr(F(x_L), F(x_i))
+    (i = 0..L-1)."""
+    L = len(V) - 1
+    v = (ctypes.c_double * (L + 1))(*[float(x) for x in V])
+    r = (ctypes.c_double * max(L, 1))(*[float(x) for x in rho])
+    c = (ctypes.c_double * (L + 1))(*[float(x) for x in C])
+    out = (ctypes.c_int32 * (L + 1))()
+    n = ctypes.c_int32()
+    _check(lib().mlkd_level_select_opt(v, r, c, L, out, ctypes.byref(n)), "mlkd_level_select_opt")
     return [int(out[i]) for i in range(n.value)]
 
 
@@ -304,6 +326,17 @@ class Context:
                 "other_launches": int(t.other_launches)}
 
     # -- mlkd_run_level ----------------------------------------------------
+    def level_pilot(self, problem: Problem, n: int, stream=None):
+        """mlkd_level_pilot: (V[0..L], rho[0..L-1], C[0..L]) from n pairs per
+        coupling of L with each coarser level."""
+        L = problem.L
+        v = (ctypes.c_double * (L + 1))()
+        r = (ctypes.c_double * max(L, 1))()
+        c = (ctypes.c_double * (L + 1))()
+        _check(lib().mlkd_level_pilot(self.handle, ctypes.byref(problem), n, _stream_handle(stream),
+                                      v, r, c), "mlkd_level_pilot")
+        return list(v), list(r)[:L], list(c)
+
     def run_level(self, problem: Problem, level: int, first_pair: int, n_pairs: int, stream=None):
         st = LevelStats()
         hist = None

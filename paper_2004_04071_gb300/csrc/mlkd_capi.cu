@@ -362,6 +362,77 @@ mlkd_status mlkd_level_select(const double *V, const double *Vd, int L, int32_t 
     return MLKD_OK;
 }
 
+mlkd_status mlkd_level_select_opt(const double *V, const double *rho, const double *C, int L,
+                                  int32_t *set_out, int32_t *n_out)
+{
+    if (!V || !rho || !C || !set_out || !n_out || L < 1 || L >= MLKD_MAX_LEVELS) return MLKD_EINVAL;
+    for (int i = 0; i <= L; ++i)
+        if (!(V[i] >= 0.0) || !(C[i] >= 0.0) || (i < L && !(rho[i] >= -1.0 && rho[i] <= 1.0)))
+            return MLKD_EINVAL;
+    auto r = [&](int i) { return i == L ? 1.0 : rho[i]; };
+    // eq. V_approx, with a negative root argument read as 0
+    auto vpair = [&](int b, int a) {
+        const double arg = (r(b) * r(b) + r(a) * r(a) - 1.0) * V[b] * V[a];
+        const double v = V[b] + V[a] - 2.0 * std::sqrt(arg > 0.0 ? arg : 0.0);
+        return v > 0.0 ? v : 0.0;
+    };
+    // eq. integerLP is a shortest path through increasing levels ending at L:
+    // best[k] is the least cost of a set whose last level is k
+    double best[MLKD_MAX_LEVELS];
+    int prev[MLKD_MAX_LEVELS];
+    for (int k = 0; k <= L; ++k) {
+        best[k] = std::sqrt(V[k] * C[k]);
+        prev[k] = -1;
+        for (int i = 0; i < k; ++i) {
+            const double c = best[i] + std::sqrt(vpair(k, i) * (C[i] + C[k]));
+            if (c < best[k]) {
+                best[k] = c;
+                prev[k] = i;
+            }
+        }
+    }
+    int rev[MLKD_MAX_LEVELS], n = 0;
+    for (int k = L; k >= 0; k = prev[k]) rev[n++] = k;
+    for (int j = 0; j < n; ++j) set_out[j] = rev[n - 1 - j];
+    *n_out = n;
+    return MLKD_OK;
+}
+
+mlkd_status mlkd_level_pilot(mlkd_context *ctx, const mlkd_problem *problem, uint64_t n, void *stream,
+                             double *V, double *rho, double *C)
+{
+    Derived d;
+    if (!ctx || !problem || !V || !rho || !C || n < 2 || !validate(problem, &d)) return MLKD_EINVAL;
+    if (problem->qoi == MLKD_QOI_DENSITY || problem->L < 1) return MLKD_EINVAL;
+    const int L = problem->L;
+    for (int i = 0; i < L; ++i) {
+        // pairs coupling L with i; the fine path of pair p is the same in
+        // every coupling (its stream is keyed by level L)
+        mlkd_problem q = *problem;
+        const int32_t set[2] = {i, L};
+        q.level_set = set;
+        q.n_set = 2;
+        q.n_fixed = nullptr;
+        mlkd_level_stats st;
+        const mlkd_status s = mlkd_run_level(ctx, &q, 1, 0, n, stream, &st, nullptr);
+        if (s != MLKD_OK) return s;
+        const double nn = (double)st.n;
+        const double vf = (st.sqf2 - st.sqf * st.sqf / nn) / (nn - 1.0);
+        const double vc = (st.sqc2 - st.sqc * st.sqc / nn) / (nn - 1.0);
+        // sum F_f F_c from Y = F_f - F_c: (sum F_f^2 + sum F_c^2 - sum Y^2)/2
+        const double cov = (0.5 * (st.sqf2 + st.sqc2 - st.sy2) - st.sqf * st.sqc / nn) / (nn - 1.0);
+        V[i] = vc > 0.0 ? vc : 0.0;
+        C[i] = (double)st.events_c / nn;
+        double rr = vf > 0.0 && vc > 0.0 ? cov / std::sqrt(vf * vc) : 0.0;
+        rho[i] = rr > 1.0 ? 1.0 : rr < -1.0 ? -1.0 : rr;
+        if (i == L - 1) {
+            V[L] = vf > 0.0 ? vf : 0.0;
+            C[L] = (double)st.events_f / nn;
+        }
+    }
+    return MLKD_OK;
+}
+
 mlkd_status mlkd_debug_transforms(const uint32_t *words, uint64_t n, float *log_u, float *sin_2pi_u,
                                   float *cos_2pi_u, void *stream)
 {

@@ -212,3 +212,20 @@ def test_level_set_pairs_and_estimate(orc, mk, ctx):
     assert [lv["n"] for lv in rg.levels] == d["n_fixed"]
     assert rg.estimate == pytest.approx(ro.estimate, rel=1e-12)
     np.testing.assert_allclose(rg.density, ro.density, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("d", [
+    dict(eps=0.5, T=0.5, dt0=0.1, M=2, L=4, qoi=0, init=0, nbins=0, seed=3),
+    dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=7, qoi=1, init=1, nbins=0, seed=12),
+])
+def test_level_pilot_matches_oracle(orc, mk, ctx, d):
+    """Sec. 4.2 pilot on the GPU (FP64) against the oracle's on the same
+    streams: V, rho and C per level within 1e-9, hence the same optimal level
+    set."""
+    po = oracle_problem(orc, d)
+    Vo, ro, Co = orc.level_pilot(po, 3000, threads=8)
+    Vg, rg, Cg = ctx.level_pilot(gpu_problem(mk, d, precision=mk.PREC_FP64), 3000)
+    np.testing.assert_allclose(Vg, Vo, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(rg, ro, rtol=1e-9, atol=1e-9)
+    assert Cg == Co
+    assert mk.level_select_opt(Vg, rg, Cg) == orc.level_select_opt(Vo, ro, Co)

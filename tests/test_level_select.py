@@ -60,3 +60,71 @@ def test_level_set_estimate_telescopes(orc):
     exact = 2.0 * (0.5 - 0.09 * (1.0 - math.exp(-0.5 / 0.09)))
     assert [s.n for s in r.levels] == [60_000, 30_000, 20_000]
     assert abs(r.estimate - exact) < 4.5 * math.sqrt(r.variance)
+
+
+# ---------------------------------------------------------------------------
+# Level selection by optimisation (Sec. 4.2, eqs. level_selection, integerLP,
+# V_approx).
+# ---------------------------------------------------------------------------
+def _lib():
+    from paper_2004_04071_gb300 import _build
+    _build.build()
+    import paper_2004_04071_gb300 as mk
+    return mk
+
+
+def test_v_pair_approx_special_cases(orc):
+    """eq. V_approx reduces to (sqrt V_i - sqrt V_j)^2 for perfectly
+    correlated levels, to V_i + V_j where the bounds admit rho_{i,j} = 0, and
+    to the exact Var(Q_L - Q_j) = V_L + V_j - 2 rho sqrt(V_L V_j) when one of
+    the levels is L (rho_{L,L} = 1)."""
+    assert orc.v_pair_approx(4.0, 1.0, 1.0, 1.0) == pytest.approx((2.0 - 1.0) ** 2)
+    assert orc.v_pair_approx(4.0, 1.0, 0.6, 0.8) == pytest.approx(5.0)
+    assert orc.v_pair_approx(4.0, 1.0, 0.3, 0.2) == pytest.approx(5.0)      # root argument < 0
+    assert orc.v_pair_approx(4.0, 9.0, 1.0, 0.5) == pytest.approx(4.0 + 9.0 - 2 * 0.5 * 6.0)
+
+
+def test_optimal_level_set_hand_example(orc):
+    """L = 2, V = (1, 1, 1), C = (1, 4, 16), level 1 perfectly correlated
+    with level 2, level 0 uncorrelated.  Costs worked by hand:
+      {2}: sqrt(16) = 4;  {0,2}: 1 + sqrt(2 * 17);  {0,1,2}: 1 + sqrt(2 * 5) + 0;
+      {1,2}: sqrt(4) + sqrt(0 * 20) = 2  (the optimum)."""
+    V, rho, C = [1.0, 1.0, 1.0], [0.0, 1.0], [1.0, 4.0, 16.0]
+    assert orc.level_set_cost([2], V, rho, C) == pytest.approx(4.0)
+    assert orc.level_set_cost([0, 2], V, rho, C) == pytest.approx(1 + math.sqrt(34))
+    assert orc.level_set_cost([0, 1, 2], V, rho, C) == pytest.approx(1 + math.sqrt(10))
+    assert orc.level_set_cost([1, 2], V, rho, C) == pytest.approx(2.0)
+    assert orc.level_select_opt(V, rho, C) == [1, 2]
+    assert _lib().level_select_opt(V, rho, C) == [1, 2]
+
+
+def test_library_optimal_selection_equals_brute_force(orc):
+    """The library's shortest-path solution equals the oracle's enumeration
+    of every subset on 300 random problems with L = 1..9, shaped like the
+    homogeneous curves (variances and costs spanning decades)."""
+    mk = _lib()
+    rng = np.random.default_rng(11)
+    for t in range(300):
+        L = int(rng.integers(1, 10))
+        V = list(10.0 ** rng.uniform(-3, 1, L + 1))
+        C = sorted(10.0 ** rng.uniform(0, 4, L + 1))
+        rho = list(rng.uniform(0.0, 1.0, L))
+        assert mk.level_select_opt(V, rho, C) == orc.level_select_opt(V, rho, C), t
+
+
+def test_level_pilot_statistics(orc):
+    """Pilot of Sec. 4.2 on a small free-space problem: the level variances
+    match those of plain single-level runs at each step size (same law),
+    correlations lie in [-1, 1] and grow toward the finest level, and the
+    cost per path does not fall as the step shrinks."""
+    p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=4, qoi=0, init=0, seed=3)
+    V, rho, C = orc.level_pilot(p, 20000, threads=8)
+    assert len(V) == 5 and len(rho) == 4 and len(C) == 5
+    assert all(-1.0 <= r <= 1.0 for r in rho)
+    assert rho[-1] > rho[0] and rho[-1] > 0.9
+    assert all(b >= a - 1e-9 for a, b in zip(C[:-1], C[1:]))
+    for i in (0, 2, 4):
+        xs, es = orc.single_paths(orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=4, seed=77), i, 0, 20000)
+        vs = float(np.var(xs * xs, ddof=1))
+        # x^2 has kurtosis near 26 here: each sample variance carries about 3.5 %
+        assert abs(V[i] - vs) < 0.2 * vs
