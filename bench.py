@@ -225,7 +225,8 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         step()
-    ttt = sorted(ttt_once(adaptive)[0] for _ in range(3))[1]
+    ttt_runs = sorted((ttt_once(adaptive) for _ in range(3)), key=lambda x: x[0])
+    ttt, ttt_res = ttt_runs[1]
 
     # the same adaptive estimates in plain FP64, one per-level call per
     # estimate (the comparison the metric names), after one warm-up call
@@ -305,6 +306,10 @@ def run_gpu(args):
                    "autotune": tune,  # seconds over ppt {1,2,4,8} x substeps {16,64,256,unbounded}
                    "events_per_step": ev / args.steps / world,
                    "time_to_tolerance_s": ttt, "time_to_tolerance_first_call_s": ttt_first,
+                   "time_to_tolerance_rounds": [r.rounds for r in ttt_res],
+                   "time_to_tolerance_estimates": [r.estimate for r in ttt_res],
+                   "time_to_tolerance_variances": [r.variance for r in ttt_res],
+                   "time_to_tolerance_met": [r.variance <= TOL * TOL / 2 * (1 + 1e-9) for r in ttt_res],
                    "time_to_tolerance_plain_fp64_s": ttt_fp64,
                    "time_to_tolerance_speedup_vs_plain_fp64": ttt_fp64 / ttt,
                    "estimates_plain_fp64": [r.estimate for r in r64],
