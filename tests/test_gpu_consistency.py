@@ -9,6 +9,12 @@
 * Sec. 5.2, homogeneous case: the variance of the level difference peaks near
   dt = 1/R and decays like dt^3 below it; the cost per pair grows like 1/dt
   above it and is flat below it.  Checked on the FP32 path.
+* Exact values of the periodic problem from the KD scheme's characteristic
+  function (`kd_charfn`): the level sums of every precision, at 2^24 pairs per
+  level, against E[F(x_l)] = 1/3 + phi_l(2 pi)/(2 pi^2), the coupled
+  E[Y_l] = (phi_l - phi_{l-1})(2 pi)/(2 pi^2) and the histogram's bin masses;
+  and the batched estimates of the periodic benchmark problem against
+  int x^2 f.
 """
 import math
 
@@ -16,7 +22,9 @@ import numpy as np
 import pytest
 from scipy import stats
 
+import workloads as W
 from helpers import check_level_curve, gpu_problem, level_curve
+from kd_charfn import kd_charfn
 
 pytestmark = pytest.mark.gpu
 
@@ -73,3 +81,63 @@ def test_level_variance_and_cost_curve_fp32(mk, ctx):
         return st["sy"], st["sy2"], st["n"], st["events_f"] + st["events_c"]
 
     check_level_curve(level_curve(sums, 12, 100_000), 1.0 / eps ** 2)
+
+
+def _periodic_exact(eps, dt, n):
+    return 1.0 / 3.0 + kd_charfn(2 * math.pi, eps, dt, n) / (2 * math.pi ** 2)
+
+
+@pytest.mark.parametrize("precision", ["PREC_FP64", "PREC_FP32_DY64", "PREC_FP32_COMP"])
+def test_periodic_level_sums_match_charfn(mk, ctx, precision):
+    # Near-diffusive regime (R dt = 5 at level 0), where the coupled level
+    # difference is large against its noise.
+    eps, T, dt0, nb = 0.1, 0.05, 0.05, 16
+    p = gpu_problem(mk, dict(eps=eps, T=T, dt0=dt0, M=2, L=3, qoi=1, init=1, nbins=nb, lo=0.0,
+                             hi=1.0, seed=3), precision=getattr(mk, precision))
+    n = 1 << 24
+    edges = np.arange(nb + 1) / nb
+    for level in range(4):
+        dt = dt0 / 2 ** level
+        steps = 2 ** level
+        st = ctx.run_level(p, level, 0, n)
+        assert st["n"] == n
+        ef = _periodic_exact(eps, dt, steps)
+        mf = st["sqf"] / n
+        se = math.sqrt((st["sqf2"] / n - mf * mf) / n)
+        assert abs(mf - ef) <= 4.5 * se, (level, mf, ef, se)
+        if level > 0:
+            ec = _periodic_exact(eps, 2 * dt, steps // 2)
+            mc = st["sqc"] / n
+            se_c = math.sqrt((st["sqc2"] / n - mc * mc) / n)
+            assert abs(mc - ec) <= 4.5 * se_c, (level, mc, ec, se_c)
+            my = st["sy"] / n
+            se_y = math.sqrt((st["sy2"] / n - my * my) / n)
+            assert abs(my - (ef - ec)) <= 4.5 * se_y, (level, my, ef - ec, se_y)
+            assert abs(ef - ec) > 4.5 * se_y or level == 3
+        phi = kd_charfn(2 * math.pi, eps, dt, steps)
+        expected = n * (1.0 / nb + phi * np.diff(np.sin(2 * math.pi * edges)) / (2 * math.pi))
+        hf = st["hist_f"].astype(np.float64)
+        assert hf.sum() == n
+        chi2 = float(np.sum((hf - expected) ** 2 / expected))
+        assert stats.chi2.sf(chi2, nb - 1) > 1e-4, (level, chi2)
+
+
+def test_periodic_benchmark_estimates_match_exact_value(mk, ctx):
+    """The batched estimates of the periodic benchmark problem (tol = 1e-3)
+    against int x^2 f of the finest level's scheme.  At eps = 1 (L = 1) that
+    is 1/3 + phi_1(2 pi)/(2 pi^2), phi_1 = 2.2e-4; at eps = 0.1 and 1e-3 the
+    cosine mode is below 1e-12 by T = 1 and the value is 1/3.  The estimator
+    variance is at most tol^2/2."""
+    ds = [dict(W.periodic_problem(eps), request=i) for i, eps in enumerate(W.PERIODIC_EPS)]
+    probs = [gpu_problem(mk, d, precision=mk.PREC_FP32_COMP) for d in ds]
+    res = ctx.estimate_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))
+    for d, r in zip(ds, res):
+        if d["eps"] == 1.0:
+            exact = _periodic_exact(1.0, d["dt0"] / 2 ** d["L"], 2 ** (d["L"] + 1))
+        else:
+            exact = 1.0 / 3.0
+        assert r.variance <= d["tol"] ** 2 / 2 * (1 + 1e-9)
+        assert abs(r.estimate - exact) <= 4.5 * math.sqrt(r.variance), (d["eps"], r.estimate, exact)
+        # Every periodic sample lands in [0, 1): the level-0 histogram carries
+        # mass 1 and each correction level carries mass 0.
+        assert float(np.sum(r.density)) / d["nbins"] == pytest.approx(1.0, abs=1e-12)
