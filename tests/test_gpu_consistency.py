@@ -113,7 +113,8 @@ def test_periodic_level_sums_match_charfn(mk, ctx, precision):
             my = st["sy"] / n
             se_y = math.sqrt((st["sy2"] / n - my * my) / n)
             assert abs(my - (ef - ec)) <= 4.5 * se_y, (level, my, ef - ec, se_y)
-            assert abs(ef - ec) > 4.5 * se_y or level == 3
+            if level == 1:
+                assert abs(ef - ec) > 15 * se_y       # the check above has teeth
         phi = kd_charfn(2 * math.pi, eps, dt, steps)
         expected = n * (1.0 / nb + phi * np.diff(np.sin(2 * math.pi * edges)) / (2 * math.pi))
         hf = st["hist_f"].astype(np.float64)
@@ -122,7 +123,7 @@ def test_periodic_level_sums_match_charfn(mk, ctx, precision):
         assert stats.chi2.sf(chi2, nb - 1) > 1e-4, (level, chi2)
 
 
-def test_periodic_benchmark_estimates_match_exact_value(mk, ctx):
+def test_periodic_benchmark_estimates_match_exact_value(mk):
     """The batched estimates of the periodic benchmark problem (tol = 1e-3)
     against int x^2 f of the finest level's scheme.  At eps = 1 (L = 1) that
     is 1/3 + phi_1(2 pi)/(2 pi^2), phi_1 = 2.2e-4; at eps = 0.1 and 1e-3 the
@@ -130,7 +131,12 @@ def test_periodic_benchmark_estimates_match_exact_value(mk, ctx):
     variance is at most tol^2/2."""
     ds = [dict(W.periodic_problem(eps), request=i) for i, eps in enumerate(W.PERIODIC_EPS)]
     probs = [gpu_problem(mk, d, precision=mk.PREC_FP32_COMP) for d in ds]
-    res = ctx.estimate_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))
+    cfg = mk.batch_config(max_requests=64, max_nbins=128)
+    bctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
+    try:
+        res = bctx.estimate_batch(probs, cfg)
+    finally:
+        bctx.close()
     for d, r in zip(ds, res):
         if d["eps"] == 1.0:
             exact = _periodic_exact(1.0, d["dt0"] / 2 ** d["L"], 2 ** (d["L"] + 1))
