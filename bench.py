@@ -97,6 +97,15 @@ def problems_for_rank(rank: int):
             for i, eps in enumerate(EPS_SET)]
 
 
+def exact_values():
+    """The int x^2 f that each periodic estimate targets (finest level's scheme),
+    one per eps of EPS_SET.  tests/golden/make_periodic_exact.py writes them
+    from the KD scheme's exact characteristic function."""
+    with open(os.path.join(ROOT, "tests", "golden", "periodic_benchmark_exact.json")) as f:
+        vals = {v["eps"]: v["exact"] for v in json.load(f)["values"]}
+    return [vals[eps] for eps in EPS_SET]
+
+
 def reduce_over_ranks(maxima, sums):
     """Max over ranks of `maxima` and sum of `sums` (the timed region and the
     work); unchanged on one rank.  Uses the process group's own device."""
@@ -227,6 +236,7 @@ def run_gpu(args):
         step()
     ttt_runs = sorted((ttt_once(adaptive) for _ in range(3)), key=lambda x: x[0])
     ttt, ttt_res = ttt_runs[1]
+    exact = exact_values()
 
     # the same adaptive estimates in plain FP64, one per-level call per
     # estimate (the comparison the metric names), after one warm-up call
@@ -310,6 +320,9 @@ def run_gpu(args):
                    "time_to_tolerance_estimates": [r.estimate for r in ttt_res],
                    "time_to_tolerance_variances": [r.variance for r in ttt_res],
                    "time_to_tolerance_met": [r.variance <= TOL * TOL / 2 * (1 + 1e-9) for r in ttt_res],
+                   "exact_values": exact,
+                   "time_to_tolerance_error_in_sd": [(r.estimate - x) / math.sqrt(r.variance)
+                                                     for r, x in zip(ttt_res, exact)],
                    "time_to_tolerance_plain_fp64_s": ttt_fp64,
                    "time_to_tolerance_speedup_vs_plain_fp64": ttt_fp64 / ttt,
                    "estimates_plain_fp64": [r.estimate for r in r64],

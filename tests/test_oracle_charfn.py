@@ -150,3 +150,16 @@ def test_oracle_periodic_benchmark_value(orc, eps, levels):
         s = orc.run_level(p, level, 0, n, threads=8)
         se = math.sqrt((s.sqf2 / n - (s.sqf / n) ** 2) / n)
         assert abs(s.sqf / n - exact) <= Z * se
+
+
+def test_benchmark_exact_values_file():
+    """tests/golden/periodic_benchmark_exact.json (read by the benchmark) holds
+    what make_periodic_exact.py computes."""
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden",
+                           "periodic_benchmark_exact.json")) as f:
+        vals = {v["eps"]: v for v in json.load(f)["values"]}
+    assert vals[1.0]["exact"] == pytest.approx(periodic_exact(1.0, 0.25, 4), rel=1e-15)
+    for eps in (0.1, 1e-3):
+        assert abs(vals[eps]["exact"] - 1.0 / 3.0) < 1e-12
