@@ -1,20 +1,26 @@
 // mlkd_batch.cu -- batched form: many independent MLMC estimates advanced by
-// one persistent pair kernel pulling chunks from a device work queue.
+// one persistent pair kernel whose warps claim chunks from device queues.
 //
 // Device state (in the context arena, after the base workspace):
 //   ReqDesc[max_requests]   problem of each request slot (host-written)
 //   ReqState[max_requests]  level sums, pairs scheduled, round bookkeeping
-//   Chunk[cap]              work queue: (request, level, first pair, count)
-//   rows[cap][8]            one row of sums per chunk (fixed-order input of
+//   Chunk[slots][kSlotChunks]  (request, level, first pair, count); each
+//                           request slot owns its range of chunk ids
+//   rows[...][8]            one row of sums per chunk (fixed-order input of
 //                           the finalize)
+//   q/l/p id rings          queues of chunk ids: main, long chunks, small rounds
 //   hist[max_requests][16][3][max_nbins]  fine/coarse/both bin counts
-//   BatchCtl                queue head/tail and the live-request count
+//   BatchCtl                queue counters, live and running requests, events,
+//                           the error flag
+//   slice state             stored chunk positions and lane states of sliced
+//                           launches
 //
-// One iteration of the loop: the scheduler kernel (one block per request)
-// finalizes every request whose round has completed, runs the FP64
-// controller of Sec. 4.1 for it and appends its next round's chunks (finest
-// level first); the pair kernel runs one slice; the bookkeeping kernel trims
-// the queue head and, in the graph form, sets the while-node condition.
+// One iteration of the loop: the scheduler kernel (one warp per request
+// slot) admits new requests and frees cancelled ones; the pair kernel runs
+// one slice, and the warp that finishes a round's last chunk finalizes it,
+// runs the FP64 controller of Sec. 4.1 and publishes the next round (finest
+// level first) on the spot; the bookkeeping kernel sets the live count and,
+// in the graph form, the while-node condition.
 #include <condition_variable>
 #include <cstdio>
 #include <deque>
