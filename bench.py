@@ -356,14 +356,14 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def oracle_sample(cpu_seconds: float, fixed=None):
+def oracle_sample(cpu_seconds: float, fixed=None, threads=None):
     """Times the oracle on a bounded sample of the workload.  Each round runs,
     for every eps and level, a slice of pairs proportional to that level's
     N_l (at least 32), continuing the pair index where the last round
-    stopped; rounds repeat until about `cpu_seconds` have passed, on all host
-    cores."""
+    stopped; rounds repeat until about `cpu_seconds` have passed, on
+    `threads` host threads (default: all cores)."""
     import oracle as O
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     if fixed is None:
         fixed = [[max(100, 2 ** (12 - l)) for l in range(W.periodic_levels(e) + 1)] for e in EPS_SET]
     total = float(sum(sum(n) for n in fixed))
@@ -395,7 +395,11 @@ def oracle_sample(cpu_seconds: float, fixed=None):
 
 def cpu_baseline(cpu_seconds, fixed):
     try:
-        return oracle_sample(cpu_seconds, fixed)
+        out = oracle_sample(cpu_seconds, fixed)
+        one = oracle_sample(max(1.0, cpu_seconds / 5), fixed, threads=1)
+        out["value_1_thread"] = one["value"]
+        out["sample_1_thread"] = one["sample"]
+        return out
     except Exception as exc:  # the baseline must not sink the GPU line
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                 "sample": "failed: %s" % exc}
