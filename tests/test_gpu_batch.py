@@ -260,3 +260,49 @@ def test_full_size_periodic_step_matches_per_level_form(mk):
             np.testing.assert_allclose(b.density, r.density, rtol=0, atol=1e-3)
     finally:
         ctx.close()
+
+
+def _exact_periodic(eps, dt, n):
+    from kd_charfn import kd_charfn
+    return 1.0 / 3.0 + kd_charfn(2 * math.pi, eps, dt, n) / (2 * math.pi ** 2)
+
+
+@pytest.mark.parametrize("case", ["free_x2", "periodic"])
+def test_mse_of_200_adaptive_estimates(mk, ctx, case):
+    """Eq. mse (Sec. 4.1) over 200 independent adaptive estimates on the GPU.
+
+    free_x2: E[x(T)^2] in free space, whose closed form
+    2(T - eps^2 (1 - e^{-T/eps^2})) holds at every level, so the estimator is
+    unbiased.  periodic: int x^2 f of the finest level's scheme, exact from the
+    KD scheme's characteristic function.  With the standardised errors
+    z_i = (estimate_i - exact)/sqrt(variance_i), the mean of z must be 0 within
+    4.5 standard errors, and the mean of z^2 must lie between the 0.1 % and 99.9 %
+    points of chi^2(200)/200.  Together these check the bias and the variance
+    that the controller reports.  The MSE must also stay below the
+    chi-square bound of tol^2/2."""
+    from scipy import stats
+    if case == "free_x2":
+        base = dict(eps=0.5, T=0.5, dt0=0.1, M=2, L=3, qoi=0, init=0, nbins=0, tol=2e-3,
+                    n_warmup=100)
+        exact = W.msd_closed_form(0.5, 0.5)
+    else:
+        base = dict(eps=0.1, T=0.05, dt0=0.05, M=2, L=3, qoi=1, init=1, nbins=0, tol=2e-3,
+                    n_warmup=100)
+        exact = _exact_periodic(0.1, 0.05 / 8, 8)
+    n_est = 200
+    # One seed for a batch; the request ids separate the 200 streams.
+    ds = [dict(base, seed=11, request=i) for i in range(n_est)]
+    cfg = mk.batch_config(max_requests=64, max_nbins=128)
+    res = []
+    for k in range(0, n_est, 64):
+        probs = [gpu_problem(mk, d, precision=mk.PREC_FP32_COMP) for d in ds[k:k + 64]]
+        res += ctx.estimate_batch(probs, cfg)
+    tol = base["tol"]
+    est = np.array([r.estimate for r in res])
+    var = np.array([r.variance for r in res])
+    assert np.all(var <= tol * tol / 2 * (1 + 1e-9))
+    z = (est - exact) / np.sqrt(var)
+    assert abs(z.mean()) < 4.5 / math.sqrt(n_est), z.mean()
+    lo, hi = stats.chi2.ppf([0.001, 0.999], n_est) / n_est
+    assert lo < np.mean(z * z) < hi, np.mean(z * z)
+    assert np.mean((est - exact) ** 2) < tol * tol / 2 * hi
