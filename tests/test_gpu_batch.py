@@ -43,6 +43,8 @@ def mixed_problems(precision, seed=5):
         dict(eps=1e-3, T=1.0, dt0=0.5, M=2, L=6, qoi=1, init=1, nbins=0, tol=0.003, n_warmup=100,
              seed=seed, request=4),
         dict(W.TWO_LEVEL, seed=seed, request=5),
+        dict(eps=0.2, T=0.6, dt0=0.2, M=3, L=2, qoi=0, init=0, nbins=0, tol=0.01, n_warmup=100,
+             seed=seed, request=6),
     ]
 
 

@@ -5,7 +5,8 @@
   coarse path of a level-l pair (built by the Sec. 3 mapping and aggregation
   from the fine path's random numbers) has the law of an independent
   single-level run at dt_{l-1}, in position and in the mean number of
-  collisions.  M runs from 2 to 64 (Sec. 5.1 uses M up to 64 as well).
+  collisions.  M runs from 2 to 64 (Sec. 5.1 uses M up to 64 as well),
+  including 3 and 6, which are not powers of two.
 * Sec. 5.2, homogeneous case: the variance of the level difference peaks near
   dt = 1/R and decays like dt^3 below it; the cost per pair grows like 1/dt
   above it and is flat below it.  Checked on the FP32 path.
@@ -49,9 +50,9 @@ def ctx(mk):
 # (eps, M, level): kinetic, mixed and diffusive regimes at every coarsening.
 SWEEP = [(0.2, 2, 1), (0.2, 2, 3), (0.2, 4, 1), (0.2, 4, 2), (0.2, 8, 1), (0.2, 8, 2),
          (0.2, 16, 1), (0.2, 16, 2), (0.2, 32, 1), (0.2, 64, 1), (0.2, 64, 2),
-         (0.05, 4, 2), (0.05, 16, 1)]
+         (0.05, 4, 2), (0.05, 16, 1), (0.2, 3, 1), (0.2, 3, 2), (0.2, 6, 1)]
 # The 0.1 % critical value of each two-sample test keeps the family-wise
-# false-rejection rate of the sweep near 1.3 % (13 cases).
+# false-rejection rate of the sweep near 1.6 % (16 cases).
 ALPHA = 1e-3
 
 

@@ -45,6 +45,7 @@ CASES = {
     "periodic_eps0.1": W.periodic_problem(0.1),
     "diffusive_eps1e-3": dict(W.periodic_problem(1e-3), L=6),
     "kinetic": dict(eps=2.0, T=1.0, dt0=0.25, M=2, L=3, qoi=0, init=0, nbins=0, seed=5),
+    "M3": dict(eps=0.2, T=0.6, dt0=0.2, M=3, L=2, qoi=0, init=0, nbins=0, seed=17),
 }
 
 

@@ -44,6 +44,10 @@ REGIMES = {
                      seed=21),
     "deep_diffusive": dict(eps=1e-3, T=1.0, dt0=0.5, M=2, L=6, qoi=1, init=1, nbins=64, lo=0.0,
                            hi=1.0, seed=2),
+    # refinement factors that are not powers of two: the coarse step end is
+    # found by division instead of a shift
+    "M3": dict(eps=0.2, T=0.6, dt0=0.2, M=3, L=2, qoi=0, init=0, nbins=12, lo=-3.0, hi=3.0, seed=17),
+    "M6_diffusive": dict(eps=0.05, T=1.0, dt0=0.5, M=6, L=2, qoi=1, init=1, nbins=0, seed=19),
 }
 
 

@@ -163,3 +163,20 @@ def test_benchmark_exact_values_file():
     assert vals[1.0]["exact"] == pytest.approx(periodic_exact(1.0, 0.25, 4), rel=1e-15)
     for eps in (0.1, 1e-3):
         assert abs(vals[eps]["exact"] - 1.0 / 3.0) < 1e-12
+
+
+def test_oracle_pairs_match_charfn_refinement_three(orc):
+    """M = 3 (not a power of two): the coarse path of a level-l pair has the
+    law of a single-level run at 3 dt_l."""
+    eps, T, dt0 = 0.1, 0.045, 0.045          # R dt = 4.5, 1.5, 0.5
+    p = orc.Problem(eps=eps, T=T, dt0=dt0, M=3, L=2, seed=8)
+    n = 400_000
+    for level in (1, 2):
+        xf, xc, _, _ = orc.pairs(p, level, 0, n, threads=8)
+        for k in KS:
+            pf = kd_charfn(k, eps, p.dt(level), p.nsteps(level))
+            pc = kd_charfn(k, eps, p.dt(level - 1), p.nsteps(level - 1))
+            cf, cc = np.cos(k * xf), np.cos(k * xc)
+            _check(cf, pf, ("fine", level, k))
+            _check(cc, pc, ("coarse", level, k))
+            _check(cf - cc, pf - pc, ("difference", level, k))
