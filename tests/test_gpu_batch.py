@@ -60,7 +60,7 @@ def test_batch_matches_per_level_fp64(mk, ctx):
             assert lb["events_f"] == lr["events_f"] and lb["events_c"] == lr["events_c"]
             assert lb["sy"] == pytest.approx(lr["sy"], rel=1e-12, abs=1e-12)
         assert b.estimate == pytest.approx(r.estimate, rel=1e-12, abs=1e-14)
-        assert b.variance == pytest.approx(r.variance, rel=1e-10)
+        assert b.variance == pytest.approx(r.variance, rel=1e-10, abs=0)
         if p.nbins:
             np.testing.assert_allclose(b.density, r.density, rtol=1e-12, atol=1e-12)
 

@@ -107,8 +107,8 @@ def test_series_branch_meets_closed_form(orc, name):
     the switch, where both are accurate to ~1e-15."""
     fn = getattr(orc.lib(), "orc_%ss" % name)
     for s in (1.0 - 1e-13, 0.999, 0.9, 0.75):
-        assert fn(s) == pytest.approx(_closed(name, s), rel=2e-14)
-    assert fn(1.0 - 1e-15) == pytest.approx(fn(1.0), rel=1e-13)
+        assert fn(s) == pytest.approx(_closed(name, s), rel=2e-14, abs=0)
+    assert fn(1.0 - 1e-15) == pytest.approx(fn(1.0), rel=1e-13, abs=0)
 
 
 @pytest.mark.parametrize("name", ["f", "g", "h"])
@@ -120,7 +120,7 @@ def test_series_branch_small_arguments(orc, name):
         S = mp.mpf(s)
         e = mp.e ** (-S)
         ref = {"f": 2 * (e - 1) + S * (e + 1), "g": 1 - 2 * S * e - e * e, "h": e + S - 1}[name]
-        assert fn(s) == pytest.approx(float(ref), rel=1e-14)
+        assert fn(s) == pytest.approx(float(ref), rel=1e-14, abs=0)
 
 
 def test_unconditioned_variance_identity(orc):
@@ -135,7 +135,7 @@ def test_unconditioned_variance_identity(orc):
         d0 = L.orc_diffusion(R, mu, sigma, theta, mu) ** 2
         d1 = L.orc_diffusion(R, mu, sigma, theta, mu + 1.0) ** 2 - d0
         total = d0 + d1 * sigma ** 2 + a1 ** 2 * sigma ** 2
-        assert total == pytest.approx(2 * sigma ** 2 / R ** 2 * (s - 1 + math.exp(-s)), rel=1e-12)
+        assert total == pytest.approx(2 * sigma ** 2 / R ** 2 * (s - 1 + math.exp(-s)), rel=1e-12, abs=0)
 
 
 def test_cosine_inverse_cdf(orc):

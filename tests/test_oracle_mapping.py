@@ -71,7 +71,7 @@ def test_collision_on_grid_point_takes_full_diffusive_step(orc):
     v0, v1 = nu[0], nu[1]
     a = L.orc_advection(R, 0.0, 0.5, v1)
     x_expect = v0 * 0.5 + a + v1 * (n * dt - 1.0)
-    assert out["xf"] == pytest.approx(x_expect, rel=1e-14)
+    assert out["xf"] == pytest.approx(x_expect, rel=1e-14, abs=0)
 
 
 def _hand_trace(flights, nu, chi, R, mu, sigma, dt, n, M):
