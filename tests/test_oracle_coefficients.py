@@ -152,3 +152,23 @@ def test_cosine_inverse_cdf(orc):
     xs = np.array([L.orc_cosine_inverse(u) for u in rng.random(20000)])
     cdf = lambda x: x + np.sin(2 * np.pi * x) / (2 * np.pi)
     assert stats.kstest(xs, cdf).pvalue > 1e-3
+
+
+def test_cosine_inverse_near_the_centre(orc):
+    """Near u = 1/2 the CDF is flat (F'(1/2) = 0), so F(x) = u cannot show an
+    error in x there.  Compare x with the root of G(y) = y - sin(2 pi y)/(2 pi)
+    = u - 1/2 solved in 60-digit arithmetic, and G itself with its closed form
+    at small y, where the oracle sums its Taylor series."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    L = orc.lib()
+    G = lambda y: y - mp.sin(2 * mp.pi * y) / (2 * mp.pi)
+    for y in (1e-7, 1e-5, 1e-4, 1e-3, 0.01, 0.1, -1e-4, -0.05):
+        assert L.orc_cosine_G(y) == pytest.approx(float(G(mp.mpf(y))), rel=1e-14, abs=0)
+    for g in (1e-15, 1e-12, 1e-9, 1e-6, 1e-3, 0.1, 0.3, 0.49):
+        for sgn in (1.0, -1.0):
+            u = 0.5 + sgn * g
+            g_eff = mp.mpf(u) - mp.mpf("0.5")            # exact: u - 1/2 in binary
+            y0 = mp.sign(g_eff) * mp.cbrt(6 * abs(g_eff) / (2 * mp.pi) ** 2)
+            y = mp.findroot(lambda t: G(t) - g_eff, y0)
+            assert abs(L.orc_cosine_inverse(u) - float(mp.mpf("0.5") + y)) <= 3e-16, (u, y)
