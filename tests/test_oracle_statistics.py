@@ -184,6 +184,49 @@ def test_density_counts_consistent(orc):
     assert np.all(s.hist_f + s.hist_c - 2 * s.hist_both >= np.abs(s.hist_f - s.hist_c))
 
 
+@pytest.mark.parametrize("periodic", [False, True])
+def test_density_variance_and_estimate_from_positions(orc, periodic):
+    """The density QoI's V_l (largest bin variance of Y_b/h, the sup norm of
+    R16) and the MLMC density estimate, recomputed by brute force from the
+    pair positions: per-pair bin indicators and np.histogram, with no use of
+    the oracle's counts or its bin function."""
+    nb = 16
+    if periodic:
+        p = orc.Problem(eps=0.3, T=0.2, dt0=0.1, M=2, L=2, qoi=orc.QOI_DENSITY,
+                        init=orc.INIT_COSINE, nbins=nb, lo=0.0, hi=1.0, seed=4,
+                        n_fixed=[3000, 2000, 1000])
+        lo, hi = 0.0, 1.0
+        wrap = lambda x: x - np.floor(x)
+    else:
+        p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=2, qoi=orc.QOI_DENSITY, nbins=nb,
+                        lo=-1.5, hi=1.5, seed=4, n_fixed=[3000, 2000, 1000])
+        lo, hi = -1.5, 1.5
+        wrap = lambda x: x
+    h = (hi - lo) / nb
+    edges = lo + h * np.arange(nb + 1)
+
+    def onehot(x):
+        x = wrap(x)
+        k = np.floor((x - lo) / h)
+        inside = (x >= lo) & (x < hi)
+        return (k[:, None] == np.arange(nb)[None, :]) & inside[:, None]
+
+    dens = np.zeros(nb)
+    for level, n in enumerate(p.n_fixed):
+        xf, xc, ef, ec = orc.pairs(p, level, 0, n)
+        s = orc.level_sums(p, level, xf, xc, ef, ec)
+        yb = onehot(xf).astype(float) - (onehot(xc).astype(float) if level else 0.0)
+        v_brute = np.var(yb, axis=0, ddof=1).max() / (h * h)
+        assert orc.level_variance(p, s) == pytest.approx(v_brute, rel=1e-12, abs=0)
+        hf = np.histogram(wrap(xf), bins=edges)[0]
+        hc = np.histogram(wrap(xc), bins=edges)[0] if level else np.zeros(nb)
+        dens += (hf - hc) / n / h
+    r = orc.estimate(p)
+    assert np.allclose(r.density, dens, rtol=1e-12, atol=1e-12)
+    if periodic:
+        assert np.sum(r.density) * h == pytest.approx(1.0, abs=1e-12)
+
+
 def test_level_variance_and_cost_curve(orc):
     eps = 0.1
     p = orc.Problem(eps=eps, T=1.0, dt0=0.5, M=2, L=12, qoi=0, init=0, nbins=0, seed=5)
