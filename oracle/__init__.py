@@ -468,7 +468,6 @@ def level_set_cost(levels, V, rho, C):
     ending at L): sqrt(V_{l1} C_{l1}) + sum_j sqrt(V_{lj,lj-1} C_{lj,lj-1}),
     with V_{i,j} from eq. V_approx (rho_{L,L} = 1) and C_{i,j} = C_i + C_j
     (cost measured in KD events of both paths of a pair)."""
-    L = len(V) - 1
     r = list(rho) + [1.0]
     total = math.sqrt(V[levels[0]] * C[levels[0]])
     for a, b in zip(levels[:-1], levels[1:]):

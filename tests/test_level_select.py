@@ -17,6 +17,8 @@ CASES = [
     ([1.0] * 6, [0, 0.5, 0.4, 0.3, 0.26, 0.26], [0, 1, 5]),
     # no level with Vd < V: a single-level estimate on L
     ([1.0] * 4, [0, 2.0, 2.0, 2.0], [3]),
+    # the first level with Vd < V is L itself: the pair (L-1, L)
+    ([1.0] * 4, [0, 2.0, 2.0, 0.5], [2, 3]),
 ]
 
 

@@ -236,3 +236,68 @@ def test_level_variance_and_cost_curve(orc):
         return s.sy, s.sy2, s.n, s.events_f + s.events_c
 
     check_level_curve(level_curve(sums, 12, 6000), 1.0 / eps ** 2)
+
+
+def test_qoi_values_by_hand(orc):
+    """F(x) = (x mod 1)^2 on the periodic interval and x^2 in free space, at
+    points worked out by hand (negative x and whole periods included)."""
+    per = orc.Problem(eps=1.0, T=1.0, dt0=0.5, qoi=orc.QOI_X2_PERIODIC, init=orc.INIT_COSINE)
+    free = orc.Problem(eps=1.0, T=1.0, dt0=0.5)
+    x = np.array([0.25, -0.25, 1.75, 3.0, -2.5, 0.0])
+    assert np.array_equal(orc.qoi_values(per, x), [0.0625, 0.5625, 0.5625, 0.0, 0.25, 0.0])
+    assert np.array_equal(orc.qoi_values(free, x), x * x)
+
+
+@pytest.mark.parametrize("periodic,level", [(True, 0), (True, 2), (False, 1)])
+def test_level_sums_from_positions(orc, periodic, level):
+    """Every field of the oracle's level sums, its mean, sample variance and
+    cost, recomputed with numpy from the pair positions and event counts; and
+    sums of two pair ranges merged with add() equal the sums of their union."""
+    if periodic:
+        p = orc.Problem(eps=0.3, T=0.5, dt0=0.25, M=2, L=2, qoi=orc.QOI_X2_PERIODIC,
+                        init=orc.INIT_COSINE, nbins=8, lo=0.0, hi=1.0, seed=6)
+        F = lambda x: np.mod(x, 1.0) ** 2
+    else:
+        p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=1, nbins=8, lo=-2.0, hi=2.0, seed=6)
+        F = lambda x: x ** 2
+    n, k = 6000, 2500
+    xf, xc, ef, ec = orc.pairs(p, level, 0, n)
+    s = orc.level_sums(p, level, xf, xc, ef, ec)
+    qf = F(xf)
+    qc = F(xc) if level else np.zeros(n)
+    y = qf - qc
+    close = lambda a, b: a == pytest.approx(b, rel=1e-12, abs=1e-300)
+    assert s.n == n
+    assert close(s.sy, y.sum()) and close(s.sy2, (y * y).sum())
+    assert close(s.sqf, qf.sum()) and close(s.sqf2, (qf * qf).sum())
+    assert close(s.sqc, qc.sum()) and close(s.sqc2, (qc * qc).sum())
+    assert s.events_f == ef.sum() and s.events_c == ec.sum()
+    assert close(s.mean(), y.mean()) and close(s.var(), np.var(y, ddof=1))
+    assert close(s.cost(), (ef + ec).mean())
+    a = orc.run_level(p, level, 0, k)
+    a.add(orc.run_level(p, level, k, n - k))
+    assert a.n == n and a.events_f == s.events_f and a.events_c == s.events_c
+    for f in ("sy", "sy2", "sqf", "sqf2", "sqc", "sqc2"):
+        assert close(getattr(a, f), getattr(s, f)), f
+    for f in ("hist_f", "hist_c", "hist_both"):
+        assert np.array_equal(getattr(a, f), getattr(s, f)), f
+
+
+def test_controller_loop_reaches_its_targets(orc, monkeypatch):
+    """The adaptive loop of Sec. 4.1 as a function of the level statistics.
+    Levels are stubbed so that every pair range has sample variance V_l and
+    cost C_l exactly.  After the warm-up the loop must raise each level to
+    the count of eqs. Nopt1/Noptj, no further, and then stop."""
+    V = [4.0, 1.0, 0.05, 0.002]
+    C = [3.0, 10.0, 40.0, 160.0]
+    tol = 0.01
+
+    def fake_run_level(problem, level, first, count, threads=1):
+        return orc.LevelSums(n=count, sy=0.0, sy2=V[level] * (count - 1),
+                             events_f=int(C[level] * count), events_c=0)
+
+    monkeypatch.setattr(orc, "run_level", fake_run_level)
+    p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=3, tol=tol, n_warmup=100)
+    r = orc.estimate(p)
+    want = [max(p.n_warmup, t) for t in orc.optimal_counts(V, C, tol)]
+    assert [s.n for s in r.levels] == want
