@@ -301,3 +301,25 @@ def test_controller_loop_reaches_its_targets(orc, monkeypatch):
     r = orc.estimate(p)
     want = [max(p.n_warmup, t) for t in orc.optimal_counts(V, C, tol)]
     assert [s.n for s in r.levels] == want
+
+
+def test_bin_index_by_hand(orc):
+    """Bins of [lo, hi): the lower edge belongs to bin 0, the upper edge is
+    outside in free space, and a position just below hi whose (x - lo)/h rounds
+    up to nb still lands in the last bin; periodic positions wrap first."""
+    free = orc.Problem(eps=1.0, T=1.0, dt0=0.5, nbins=20, lo=-3.0, hi=3.0)
+    below_hi = np.nextafter(3.0, 0.0)                  # (x - lo)/h rounds to 20.0
+    x = np.array([-3.0, 3.0, below_hi, np.nextafter(-3.0, -4.0), 0.0, 2.95])
+    assert list(orc.bin_index(free, x)) == [0, -1, 19, -1, 10, 19]
+    per = orc.Problem(eps=1.0, T=1.0, dt0=0.5, nbins=8, qoi=orc.QOI_X2_PERIODIC,
+                      init=orc.INIT_COSINE)
+    x = np.array([1.0, -0.01, 0.5, 2.125, -3.9])
+    assert list(orc.bin_index(per, x)) == [0, 7, 4, 1, 0]
+
+
+def test_sample_variance_small_counts(orc):
+    """Unbiased sample variance with the N - 1 divisor (R10) at N = 2 and 3,
+    and 0 below two samples."""
+    assert orc.LevelSums(n=2, sy=1.0, sy2=1.0).var() == 0.5          # samples {0, 1}
+    assert orc.LevelSums(n=3, sy=3.0, sy2=5.0).var() == 1.0          # samples {0, 1, 2}
+    assert orc.LevelSums(n=1, sy=2.0, sy2=4.0).var() == 0.0
