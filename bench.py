@@ -289,6 +289,22 @@ def run_gpu(args):
         fine += sum(lv["events_f"] for r in rs for lv in r.levels)
         coarse += sum(lv["events_c"] for r in rs for lv in r.levels)
     rt = ctx.get_timing(reset=True)
+
+    # per-level breakdown (untimed for the headline): each level of each
+    # estimate alone in the per-level form, at the step's N_l
+    per_level = []
+    for d, nl in zip(dicts, fixed):
+        p = mk.make_problem(precision=prec, **d)
+        for level, n in enumerate(nl):
+            ctx.get_timing(reset=True)
+            st = ctx.run_level(p, level, 0, int(n), stream)
+            lt = ctx.get_timing(reset=True)
+            evl = int(st["events_f"] + st["events_c"])
+            per_level.append({"eps": d["eps"], "level": level, "pairs": int(n),
+                              "events_f": int(st["events_f"]), "events_c": int(st["events_c"]),
+                              "ms": lt["pair_kernel_ms"],
+                              "events_per_s": evl / (lt["pair_kernel_ms"] / 1e3)
+                              if lt["pair_kernel_ms"] > 0 else None})
     ctx.set_timing(False)
 
     (t_dev, t_host), (ev,) = reduce_over_ranks([dev_ms / 1e3, host_s], [float(events_total)])
@@ -328,7 +344,8 @@ def run_gpu(args):
                    "estimates_plain_fp64": [r.estimate for r in r64],
                    "estimates": [r.estimate for r in last],
                    "variances": [r.variance for r in last],
-                   "l2": "flushed (256 MB write) between timed steps; no input arrays"},
+                   "l2": "flushed (256 MB write) between timed steps; no input arrays",
+                   "per_level": per_level},
         "e2e": {"value": ev / t_host, "unit": UNIT,
                 "h2d_bytes_per_step": len(step_problems) * (88 + 8 * 13),
                 "d2h_bytes_per_step": len(step_problems) * (1400 + 8 * 128)},
