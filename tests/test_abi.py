@@ -74,6 +74,13 @@ def test_validation_without_gpu(built):
         assert mk.workspace_bytes(mk.make_problem(**kw)) == 0, b
     # 5 * 3^15 fine steps: exact step indices in FP64 state, not in FP32 state
     assert mk.workspace_bytes(mk.make_problem(eps=0.5, T=0.5, dt0=0.1, M=3, L=15)) > 0
+    # the caps are inclusive: 2^30 fine steps with FP64 state, 2^24 with FP32 state
+    for prec, L, ok_at_cap in [(0, 15, True), (3, 15, True), (1, 12, True), (2, 12, True)]:
+        at_cap = mk.make_problem(eps=0.5, T=1.0, dt0=1.0, M=4, L=L, precision=prec)
+        over = mk.make_problem(eps=0.5, T=2.0, dt0=1.0, M=4, L=L, precision=prec)
+        assert mk.workspace_bytes(at_cap) > 0, (prec, L)
+        assert mk.workspace_bytes(over) == 0, (prec, L)
+    assert mk.workspace_bytes(mk.make_problem(eps=0.5, T=1.0, dt0=1.0, M=4, L=13, precision=2)) == 0
 
 
 def test_status_strings(built):

@@ -46,6 +46,9 @@ CASES = {
     "diffusive_eps1e-3": dict(W.periodic_problem(1e-3), L=6),
     "kinetic": dict(eps=2.0, T=1.0, dt0=0.25, M=2, L=3, qoi=0, init=0, nbins=0, seed=5),
     "M3": dict(eps=0.2, T=0.6, dt0=0.2, M=3, L=2, qoi=0, init=0, nbins=0, seed=17),
+    # 2^24 fine steps at level 12, the FP32 cap: step indices at the top of
+    # the range where FP32 holds them exactly
+    "largest_level": dict(eps=0.5, T=1.0, dt0=1.0, M=4, L=12, qoi=0, init=0, nbins=0, seed=23),
 }
 
 

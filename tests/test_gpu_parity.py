@@ -89,6 +89,15 @@ def test_single_pair_and_empty(orc, mk, ctx):
     assert np.all(st["hist_f"] == 0)
 
 
+def test_fp64_parity_at_the_largest_level(orc, mk, ctx):
+    """2^30 fine steps (the FP64 cap), M = 4: kinetic pairs whose flights
+    span hundreds of millions of steps, so step indices and flights in step
+    units reach the top of their range."""
+    d = dict(eps=0.5, T=1.0, dt0=1.0, M=4, L=15, qoi=0, init=0, nbins=0, seed=23)
+    _compare_pairs(orc, mk, ctx, d, 15, 0, 300)
+    _compare_pairs(orc, mk, ctx, d, 14, 1 << 20, 300)
+
+
 def test_ballistic_pairs(orc, mk, ctx):
     d = dict(eps=1e4, T=1.0, dt0=0.5, M=2, L=2, qoi=0, init=0, nbins=0, seed=3)
     for level in (0, 1, 2):
