@@ -184,6 +184,19 @@ MLKD_API mlkd_status mlkd_estimate_resumable(mlkd_context *ctx, const mlkd_probl
                                              int max_rounds, void *stream, mlkd_result *out,
                                              uint64_t *hist_out);
 
+/* On-line phase of Sec. 5.3: one adaptive estimate continued through the
+ * tolerances tols[0..n_tol-1] (the paper uses tol_r = 2^(-r/2), r = 0..R).
+ * Stage r resumes stage r-1's level sums and histogram counts under tols[r],
+ * so earlier samples are kept and each stage adds only what its tolerance
+ * needs; stage 0 starts with the warm-up.  results[r] (caller-owned, n_tol
+ * entries; results[r].density NULL or nbins doubles) is the estimate after
+ * stage r, its seconds that stage's wall time.  The problem must be
+ * tolerance-driven (no n_fixed) and every tols[r] > 0 (else MLKD_EINVAL).
+ * Synchronous. */
+MLKD_API mlkd_status mlkd_estimate_sequence(mlkd_context *ctx, const mlkd_problem *problem,
+                                            int n_tol, const double *tols, void *stream,
+                                            mlkd_result *results);
+
 /* Per-pair results of pairs [first_pair, first_pair + n_pairs) of `level`:
  * device arrays of n_pairs entries for the final fine and coarse positions
  * (xc = 0 on level 0) and the fine and coarse KD event counts.  Any of the
@@ -223,6 +236,19 @@ MLKD_API mlkd_status mlkd_level_select_opt(const double *V, const double *rho, c
  * n >= 2.  Runs L launches of the pair kernel.  Synchronous. */
 MLKD_API mlkd_status mlkd_level_pilot(mlkd_context *ctx, const mlkd_problem *problem, uint64_t n,
                                       void *stream, double *V, double *rho, double *C);
+
+/* Off-line phase of the level selection (Sec. 5.3): n_warmup pairs on each
+ * level l = 0..tau, where tau is the first level with R dt_l <= 1 (the step
+ * at most the mean time between collisions, near the peak of V_{l,l-1}; L if
+ * no level is that fine).  Writes V[l] = Var(F(x_l)) and Vd[l] = Var(Y_l)
+ * (Vd[0] = 0) from those samples for l <= tau, and for l > tau V[l] = V[tau]
+ * and Vd[l] = Vd[tau] M^(-3(l - tau)), the dt^3 decay of the level
+ * differences.  V and Vd hold L+1 doubles; *tau_out receives tau.  The result
+ * is the input of mlkd_level_select (Alg. 3).  Scalar QoI, L >= 1, no level
+ * set, n_warmup >= 2 (else MLKD_EINVAL).  Synchronous. */
+MLKD_API mlkd_status mlkd_level_warmup(mlkd_context *ctx, const mlkd_problem *problem,
+                                       uint64_t n_warmup, void *stream, double *V, double *Vd,
+                                       int32_t *tau_out);
 
 /* Validation aid: the FP32 variate transforms of the pair kernel applied to
  * n 32-bit Philox output words (device array `words`).  With the 24-bit

@@ -512,6 +512,37 @@ def level_pilot(problem: Problem, n: int, threads: int = 1):
     return V, rho, C
 
 
+def warmup_tau(problem: Problem) -> int:
+    """Sec. 5.3: the level tau with dt_tau near 1/R, read as the first level
+    l >= 1 whose step is at most 1/R; the finest level L when none is."""
+    for l in range(1, problem.L + 1):
+        if problem.R * problem.dt(l) <= 1.0:
+            return l
+    return problem.L
+
+
+def level_warmup(problem: Problem, n_warmup: int = 100, threads: int = 1):
+    """Off-line phase of Sec. 5.3 for a scalar QoI: n_warmup samples on levels
+    0..tau give V_l (variance of F(x_l)) and V_{l,l-1} (variance of Y_l); past
+    tau, V_{l,l-1} follows the asymptotic O(dt_l^3) decay from its value on
+    tau, and V_l keeps its value on tau.  Returns (V, Vd, tau), Vd[0] = 0,
+    the input of level_select (Alg. 3)."""
+    L = problem.L
+    tau = warmup_tau(problem)
+    V, Vd = [0.0] * (L + 1), [0.0] * (L + 1)
+    for l in range(tau + 1):
+        xf, xc, ef, ec = pairs(problem, l, 0, n_warmup, threads)
+        qf = qoi_values(problem, xf)
+        V[l] = float(np.var(qf, ddof=1))
+        if l > 0:
+            y = qf - qoi_values(problem, xc)
+            Vd[l] = float(np.var(y, ddof=1))
+    for l in range(tau + 1, L + 1):
+        V[l] = V[tau]
+        Vd[l] = Vd[tau] * float(problem.M) ** (-3 * (l - tau))
+    return V, Vd, tau
+
+
 def optimal_counts(V, C, tol):
     """N_j = ceil(2/tol^2 sqrt(V_j/C_j) sum_i sqrt(V_i C_i))  (eqs. Nopt1/Noptj)."""
     total = sum(math.sqrt(v * c) for v, c in zip(V, C))
@@ -530,6 +561,45 @@ class MLMCResult:
     variance: float
     levels: list
     density: np.ndarray = None
+
+
+def _result(problem: Problem, sums) -> MLMCResult:
+    est = sum(s.mean() for s in sums)
+    var = sum(level_variance(problem, s) / s.n for s in sums if s.n > 0)
+    dens = None
+    if problem.nbins > 0:
+        lo, hi = problem.bin_range()
+        h = (hi - lo) / problem.nbins
+        dens = sum((s.hist_f - s.hist_c) / s.n for s in sums) / h
+    return MLMCResult(est, var, sums, dens)
+
+
+def estimate_sequence(problem: Problem, tols, threads: int = 1, max_rounds: int = 64):
+    """On-line phase of Sec. 5.3: one MLMC estimator run for a decreasing
+    sequence of RMSE tolerances, keeping its samples from one tolerance to the
+    next.  Each stage raises N_l to the optimal counts for its tolerance
+    (eqs. Nopt1/Noptj) until no level needs more.  Returns one result per
+    tolerance (each with a snapshot of the level sums)."""
+    import copy
+    J = len(problem.estimator_levels())
+    sums = [LevelSums() for _ in range(J)]
+    for l in range(J):
+        sums[l].add(run_level(problem, l, 0, problem.n_warmup, threads))
+    out = []
+    for tol in tols:
+        for _ in range(max_rounds):
+            V = [level_variance(problem, s) for s in sums]
+            C = [s.cost() for s in sums]
+            target = optimal_counts(V, C, tol)
+            grew = False
+            for l in range(J):
+                if target[l] > sums[l].n:
+                    sums[l].add(run_level(problem, l, sums[l].n, target[l] - sums[l].n, threads))
+                    grew = True
+            if not grew:
+                break
+        out.append(_result(problem, copy.deepcopy(sums)))
+    return out
 
 
 def estimate(problem: Problem, threads: int = 1, max_rounds: int = 64) -> MLMCResult:

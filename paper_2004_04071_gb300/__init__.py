@@ -37,7 +37,8 @@ EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_estimate_batch", "mlkd_autotune_batch", "mlkd_server_start", "mlkd_submit",
             "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop",
             "mlkd_debug_transforms", "mlkd_level_select", "mlkd_estimate_resumable",
-            "mlkd_level_select_opt", "mlkd_level_pilot"]
+            "mlkd_level_select_opt", "mlkd_level_pilot", "mlkd_level_warmup",
+            "mlkd_estimate_sequence"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -190,6 +191,12 @@ def lib():
         L.mlkd_estimate_resumable.argtypes = [vp, P(Problem), P(Result), P(ctypes.c_uint64), ctypes.c_int,
                                               vp, P(Result), P(ctypes.c_uint64)]
         L.mlkd_estimate_resumable.restype = ctypes.c_int
+        L.mlkd_level_warmup.argtypes = [vp, P(Problem), u64, vp, P(ctypes.c_double),
+                                        P(ctypes.c_double), P(ctypes.c_int32)]
+        L.mlkd_level_warmup.restype = ctypes.c_int
+        L.mlkd_estimate_sequence.argtypes = [vp, P(Problem), ctypes.c_int, P(ctypes.c_double), vp,
+                                             P(Result)]
+        L.mlkd_estimate_sequence.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -336,6 +343,41 @@ class Context:
         _check(lib().mlkd_level_pilot(self.handle, ctypes.byref(problem), n, _stream_handle(stream),
                                       v, r, c), "mlkd_level_pilot")
         return list(v), list(r)[:L], list(c)
+
+    def level_warmup(self, problem: Problem, n_warmup: int = 100, stream=None):
+        """mlkd_level_warmup (Sec. 5.3, off-line phase): (V[0..L], Vd[0..L], tau)
+        for mlkd_level_select."""
+        L = problem.L
+        v = (ctypes.c_double * (L + 1))()
+        vd = (ctypes.c_double * (L + 1))()
+        tau = ctypes.c_int32()
+        _check(lib().mlkd_level_warmup(self.handle, ctypes.byref(problem), n_warmup,
+                                       _stream_handle(stream), v, vd, ctypes.byref(tau)),
+               "mlkd_level_warmup")
+        return list(v), list(vd), int(tau.value)
+
+    def estimate_sequence(self, problem: Problem, tols, stream=None):
+        """mlkd_estimate_sequence (Sec. 5.3, on-line phase): one estimate
+        continued through the tolerances; one EstimateResult per stage."""
+        n = len(tols)
+        t = (ctypes.c_double * n)(*[float(x) for x in tols])
+        res = (Result * n)()
+        dens = []
+        for r in res:
+            d = np.zeros(problem.nbins, np.float64) if problem.nbins > 0 else None
+            if d is not None:
+                r.density = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            dens.append(d)
+        _check(lib().mlkd_estimate_sequence(self.handle, ctypes.byref(problem), n, t,
+                                            _stream_handle(stream), res), "mlkd_estimate_sequence")
+        out = []
+        for r, d in zip(res, dens):
+            nl = r.n_levels
+            out.append(EstimateResult(r.estimate, r.variance, r.rounds,
+                                      [r.lv[l].as_dict() for l in range(nl)],
+                                      [r.var_level[l] for l in range(nl)],
+                                      [r.cost_level[l] for l in range(nl)], d, r.seconds))
+        return out
 
     def run_level(self, problem: Problem, level: int, first_pair: int, n_pairs: int, stream=None):
         st = LevelStats()

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 
 #include "mlkd_host.h"
 
@@ -433,6 +434,47 @@ mlkd_status mlkd_level_pilot(mlkd_context *ctx, const mlkd_problem *problem, uin
     return MLKD_OK;
 }
 
+mlkd_status mlkd_level_warmup(mlkd_context *ctx, const mlkd_problem *problem, uint64_t n_warmup,
+                              void *stream, double *V, double *Vd, int32_t *tau_out)
+{
+    Derived d;
+    if (!ctx || !problem || !V || !Vd || !tau_out || n_warmup < 2 || !validate(problem, &d))
+        return MLKD_EINVAL;
+    if (problem->qoi == MLKD_QOI_DENSITY || problem->L < 1 || problem->n_set > 0) return MLKD_EINVAL;
+    const int L = problem->L;
+    const double R = 1.0 / (problem->eps * problem->eps);
+    // tau: the first level whose step is at most 1/R, the mean time between
+    // collisions (where V_{l,l-1} peaks); the finest level if none is
+    int tau = L;
+    for (int l = 1; l <= L; ++l) {
+        const double dtl = problem->dt0 / std::pow((double)problem->M, (double)l);
+        if (R * dtl <= 1.0) {
+            tau = l;
+            break;
+        }
+    }
+    mlkd_problem q = *problem;
+    q.n_fixed = nullptr;
+    for (int l = 0; l <= tau; ++l) {
+        mlkd_level_stats st;
+        const mlkd_status s = mlkd_run_level(ctx, &q, l, 0, n_warmup, stream, &st, nullptr);
+        if (s != MLKD_OK) return s;
+        const double nn = (double)st.n;
+        const double vf = (st.sqf2 - st.sqf * st.sqf / nn) / (nn - 1.0);
+        const double vy = (st.sy2 - st.sy * st.sy / nn) / (nn - 1.0);
+        V[l] = vf > 0.0 ? vf : 0.0;
+        Vd[l] = l > 0 && vy > 0.0 ? vy : 0.0;
+    }
+    // beyond tau: V_l as on tau, V_{l,l-1} decaying like dt_l^3
+    const double M3 = (double)problem->M * problem->M * problem->M;
+    for (int l = tau + 1; l <= L; ++l) {
+        V[l] = V[tau];
+        Vd[l] = Vd[tau] / std::pow(M3, (double)(l - tau));
+    }
+    *tau_out = tau;
+    return MLKD_OK;
+}
+
 mlkd_status mlkd_debug_transforms(const uint32_t *words, uint64_t n, float *log_u, float *sin_2pi_u,
                                   float *cos_2pi_u, void *stream)
 {
@@ -666,6 +708,34 @@ mlkd_status mlkd_estimate_resumable(mlkd_context *ctx, const mlkd_problem *probl
                                     uint64_t *hist_out)
 {
     return estimate_impl(ctx, problem, resume, hist_in, max_rounds, stream, out, hist_out);
+}
+
+mlkd_status mlkd_estimate_sequence(mlkd_context *ctx, const mlkd_problem *problem, int n_tol,
+                                   const double *tols, void *stream, mlkd_result *results)
+{
+    Derived d;
+    if (!ctx || !problem || !tols || !results || n_tol < 1 || !validate(problem, &d))
+        return MLKD_EINVAL;
+    if (problem->n_fixed) return MLKD_EINVAL;
+    for (int r = 0; r < n_tol; ++r)
+        if (!(tols[r] > 0.0)) return MLKD_EINVAL;
+    // one estimator continued through the sequence: each stage resumes the
+    // previous one's sums and histogram counts under the next tolerance
+    const int nb = problem->nbins;
+    std::vector<uint64_t> hist[2];
+    if (nb > 0)
+        for (auto &h : hist) h.assign((size_t)d.J * 3 * nb, 0);
+    mlkd_problem q = *problem;
+    for (int r = 0; r < n_tol; ++r) {
+        q.tol = tols[r];
+        const mlkd_result *prev = r > 0 ? &results[r - 1] : nullptr;
+        const int max_rounds = (prev ? prev->rounds : 0) + 64;
+        const uint64_t *hin = nb > 0 && r > 0 ? hist[(r - 1) & 1].data() : nullptr;
+        uint64_t *hout = nb > 0 ? hist[r & 1].data() : nullptr;
+        const mlkd_status st = estimate_impl(ctx, &q, prev, hin, max_rounds, stream, &results[r], hout);
+        if (st != MLKD_OK) return st;
+    }
+    return MLKD_OK;
 }
 
 }  // extern "C"

@@ -242,3 +242,32 @@ def test_level_pilot_matches_oracle(orc, mk, ctx, d):
     np.testing.assert_allclose(rg, ro, rtol=1e-9, atol=1e-9)
     assert Cg == Co
     assert mk.level_select_opt(Vg, rg, Cg) == orc.level_select_opt(Vo, ro, Co)
+
+
+def test_level_warmup_matches_oracle(orc, mk, ctx):
+    """Sec. 5.3 off-line phase on the device: tau, the sampled variances up
+    to tau, the extrapolated ones past it, and the level set Alg. 3 picks."""
+    for d in (dict(eps=0.2, T=1.0, dt0=0.5, M=2, L=7, qoi=0, init=0, nbins=0, seed=9),
+              dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=8, qoi=1, init=1, nbins=0, seed=3)):
+        V, Vd, tau = ctx.level_warmup(gpu_problem(mk, d), 100)
+        Vo, Vdo, tau_o = orc.level_warmup(oracle_problem(orc, d), 100, threads=8)
+        assert tau == tau_o
+        assert np.allclose(V, Vo, rtol=1e-9, atol=0) and np.allclose(Vd, Vdo, rtol=1e-9, atol=0)
+        assert mk.level_select(V, Vd) == orc.level_select(Vo, Vdo)
+
+
+@pytest.mark.parametrize("name", ["two_level", "periodic"])
+def test_estimate_sequence_matches_oracle(orc, mk, ctx, name):
+    """Sec. 5.3 on-line phase: one estimate continued through a decreasing
+    tolerance sequence picks the oracle's N_l at every stage."""
+    d = dict(REGIMES[name], L=3)
+    tols = [0.02, 0.01, 0.005] if name == "two_level" else [0.004, 0.002]
+    rg = ctx.estimate_sequence(gpu_problem(mk, d), tols)
+    ro = orc.estimate_sequence(oracle_problem(orc, d), tols, threads=8)
+    for tol, g, o in zip(tols, rg, ro):
+        assert [lv["n"] for lv in g.levels] == [s.n for s in o.levels]
+        assert g.estimate == pytest.approx(o.estimate, rel=1e-11, abs=1e-14)
+        assert g.variance == pytest.approx(o.variance, rel=1e-9, abs=0)
+        assert g.variance <= tol * tol / 2 * (1 + 1e-9)
+        if d.get("nbins", 0) > 0:
+            assert np.allclose(g.density, o.density, rtol=1e-11, atol=1e-12)

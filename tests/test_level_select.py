@@ -130,3 +130,66 @@ def test_level_pilot_statistics(orc):
         vs = float(np.var(xs * xs, ddof=1))
         # x^2 has kurtosis near 26 here: each sample variance carries about 3.5 %
         assert abs(V[i] - vs) < 0.2 * vs
+
+
+def test_warmup_tau_by_hand(orc):
+    """Sec. 5.3: tau is the first level with dt_tau <= 1/R, else L."""
+    P = lambda eps, L, dt0=0.5, M=2: orc.Problem(eps=eps, T=1.0, dt0=dt0, M=M, L=L)
+    assert orc.warmup_tau(P(0.1, 8)) == 6          # R dt_l = 50 / 2^l: 0.78 at l = 6
+    assert orc.warmup_tau(P(1.0, 1)) == 1          # R dt_1 = 0.25
+    assert orc.warmup_tau(P(1e-3, 12)) == 12       # 5e5 / 2^12 > 1: none, so L
+    assert orc.warmup_tau(P(0.5, 4, dt0=0.25, M=4)) == 1   # 4 * 0.25 / 4 = 1 exactly
+
+
+def test_warmup_extrapolation_and_samples(orc):
+    """Levels up to tau: sample variances of F(x_l) and Y_l over the first
+    n_warmup pairs, recomputed here from the positions.  Past tau: V_l = V_tau,
+    V_{l,l-1} = V_{tau,tau-1} M^(-3 (l - tau))."""
+    p = orc.Problem(eps=0.2, T=1.0, dt0=0.5, M=2, L=7, seed=9)     # R dt_l = 12.5 / 2^l: tau = 4
+    V, Vd, tau = orc.level_warmup(p, 300, threads=8)
+    assert tau == 4 and Vd[0] == 0.0
+    for l in range(tau + 1):
+        xf, xc, _, _ = orc.pairs(p, l, 0, 300)
+        assert V[l] == pytest.approx(np.var(xf ** 2, ddof=1), rel=1e-12, abs=0)
+        if l:
+            assert Vd[l] == pytest.approx(np.var(xf ** 2 - xc ** 2, ddof=1), rel=1e-12, abs=0)
+    for l in range(tau + 1, 8):
+        assert V[l] == V[tau]
+        assert Vd[l] == pytest.approx(Vd[tau] / 8.0 ** (l - tau), rel=1e-15, abs=0)
+
+
+def test_estimate_sequence_continues_one_estimator(orc, monkeypatch):
+    """The on-line phase of Sec. 5.3 with stubbed levels (sample variance V_l
+    and cost C_l exactly, for every pair range): stage r raises each level to
+    the larger of its current count and the optimal count for tol_r, and no
+    further."""
+    V = [4.0, 1.0, 0.05, 0.002]
+    C = [3.0, 10.0, 40.0, 160.0]
+    tols = [0.05, 0.02, 0.01]
+
+    def fake_run_level(problem, level, first, count, threads=1):
+        # sum Y^2 over pairs [0, N) is V (N - 1) for every N: the sample
+        # variance stays exactly V however the ranges are merged
+        return orc.LevelSums(n=count, sy=0.0, sy2=V[level] * (count - (first == 0)),
+                             events_f=int(C[level] * count), events_c=0)
+
+    monkeypatch.setattr(orc, "run_level", fake_run_level)
+    p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=3, n_warmup=100)
+    res = orc.estimate_sequence(p, tols)
+    have = [100] * 4
+    for tol, r in zip(tols, res):
+        have = [max(h, t) for h, t in zip(have, orc.optimal_counts(V, C, tol))]
+        assert [s.n for s in r.levels] == have
+
+
+def test_estimate_sequence_single_tolerance_is_the_estimate(orc):
+    p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=2, tol=0.01, seed=12)
+    (r,) = orc.estimate_sequence(p, [0.01], threads=8)
+    e = orc.estimate(p, threads=8)
+    assert [s.n for s in r.levels] == [s.n for s in e.levels]
+    assert r.estimate == e.estimate and r.variance == e.variance
+    rs = orc.estimate_sequence(p, [0.03, 0.015, 0.01], threads=8)
+    for tol, s in zip([0.03, 0.015, 0.01], rs):
+        assert s.variance <= tol * tol / 2 * (1 + 1e-12)
+    for a, b in zip(rs[:-1], rs[1:]):
+        assert all(x.n <= y.n for x, y in zip(a.levels, b.levels))
