@@ -624,11 +624,4 @@ def estimate(problem: Problem, threads: int = 1, max_rounds: int = 64) -> MLMCRe
                     grew = True
             if not grew:
                 break
-    est = sum(s.mean() for s in sums)
-    var = sum(level_variance(problem, s) / s.n for s in sums if s.n > 0)
-    dens = None
-    if problem.nbins > 0:
-        lo, hi = problem.bin_range()
-        h = (hi - lo) / problem.nbins
-        dens = sum((s.hist_f - s.hist_c) / s.n for s in sums) / h
-    return MLMCResult(est, var, sums, dens)
+    return _result(problem, sums)

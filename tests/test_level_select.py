@@ -138,7 +138,9 @@ def test_warmup_tau_by_hand(orc):
     assert orc.warmup_tau(P(0.1, 8)) == 6          # R dt_l = 50 / 2^l: 0.78 at l = 6
     assert orc.warmup_tau(P(1.0, 1)) == 1          # R dt_1 = 0.25
     assert orc.warmup_tau(P(1e-3, 12)) == 12       # 5e5 / 2^12 > 1: none, so L
-    assert orc.warmup_tau(P(0.5, 4, dt0=0.25, M=4)) == 1   # 4 * 0.25 / 4 = 1 exactly
+    assert orc.warmup_tau(P(0.1, 7)) == 6           # the level below L
+    assert orc.warmup_tau(P(0.1, 5)) == 5           # 50 / 32 > 1; level 6 would qualify
+    assert orc.warmup_tau(P(0.5, 4, dt0=1.0, M=4)) == 1    # R dt_1 = 4 * 1/4 = 1 exactly
 
 
 def test_warmup_extrapolation_and_samples(orc):
@@ -147,7 +149,7 @@ def test_warmup_extrapolation_and_samples(orc):
     V_{l,l-1} = V_{tau,tau-1} M^(-3 (l - tau))."""
     p = orc.Problem(eps=0.2, T=1.0, dt0=0.5, M=2, L=7, seed=9)     # R dt_l = 12.5 / 2^l: tau = 4
     V, Vd, tau = orc.level_warmup(p, 300, threads=8)
-    assert tau == 4 and Vd[0] == 0.0
+    assert tau == 4 and Vd[0] == 0.0 and len(V) == len(Vd) == 8
     for l in range(tau + 1):
         xf, xc, _, _ = orc.pairs(p, l, 0, 300)
         assert V[l] == pytest.approx(np.var(xf ** 2, ddof=1), rel=1e-12, abs=0)
@@ -183,11 +185,13 @@ def test_estimate_sequence_continues_one_estimator(orc, monkeypatch):
 
 
 def test_estimate_sequence_single_tolerance_is_the_estimate(orc):
-    p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=2, tol=0.01, seed=12)
+    p = orc.Problem(eps=0.5, T=0.5, dt0=0.1, M=2, L=2, tol=0.01, seed=12, nbins=12, lo=-2.0,
+                    hi=2.0)
     (r,) = orc.estimate_sequence(p, [0.01], threads=8)
     e = orc.estimate(p, threads=8)
     assert [s.n for s in r.levels] == [s.n for s in e.levels]
     assert r.estimate == e.estimate and r.variance == e.variance
+    assert np.array_equal(r.density, e.density)
     rs = orc.estimate_sequence(p, [0.03, 0.015, 0.01], threads=8)
     for tol, s in zip([0.03, 0.015, 0.01], rs):
         assert s.variance <= tol * tol / 2 * (1 + 1e-12)
