@@ -69,9 +69,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--workload", default="periodic",
-                    choices=["periodic", "twolevel", "precision", "batched64", "serving"],
+                    choices=["periodic", "twolevel", "precision", "batched64", "serving",
+                             "complexity"],
                     help="periodic: the headline (full periodic MLMC); the others measure the "
-                         "two-level, precision, batched and serving configurations")
+                         "two-level, precision, batched and serving configurations, and the "
+                         "cost-tolerance slope of the Sec. 5.3 protocol")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--time-limit", type=float, default=60.0,
@@ -655,6 +657,43 @@ def run_serving(args):
     ctx.close()
 
 
+def run_complexity(args):
+    """Sec. 5.3 protocol on the periodic problems: the off-line warm-up (100
+    pairs per level up to tau, V_{l,l-1} extrapolated past it), Alg. 3 level
+    selection, then one estimate continued through tol_r = 10^-2 2^(-r/2),
+    r = 0..6.  Per stage: the KD events of all samples so far and the stage's
+    time; and the slope of log(events) against log(tol) over the last four
+    stages (an O(tol^-2) cost gives -2)."""
+    import numpy as np
+    torch, mk, ctx, cfg = _gpu_setup(args)
+    prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
+    tols = [1e-2 * 2.0 ** (-r / 2.0) for r in range(7)]
+    runs = []
+    for eps in EPS_SET:
+        d = dict(W.periodic_problem(eps), nbins=0)
+        V, Vd, tau = ctx.level_warmup(mk.make_problem(precision=prec, **d), 100)
+        levels = mk.level_select(V, Vd)
+        q = mk.make_problem(precision=prec, level_set=levels, **d)
+        stages = ctx.estimate_sequence(q, tols)
+        ev = [float(sum(lv["events_f"] + lv["events_c"] for lv in r.levels)) for r in stages]
+        lt, le = np.log(tols[-4:]), np.log(ev[-4:])
+        slope = float(np.polyfit(lt, le, 1)[0])
+        runs.append({"eps": eps, "tau": tau, "level_set": levels,
+                     "stages": [{"tol": t, "events": e, "seconds": r.seconds, "estimate": r.estimate,
+                                 "variance": r.variance, "n": [lv["n"] for lv in r.levels]}
+                                for t, e, r in zip(tols, ev, stages)],
+                     "slope": slope})
+    out = {"metric": "Sec. 5.3 tolerance sequence: slope of log(KD events) against log(tol)",
+           "value": float(np.mean([r["slope"] for r in runs])), "unit": "d log events / d log tol",
+           "higher_is_better": False, "dtype": {"fp32": "f32", "fp32comp": "f32", "fp64": "f64"}[args.precision],
+           "data": "synthetic (Philox streams; analytic homogeneous background)",
+           "config": {"workload": "periodic, eps in {1,0.1,1e-3}, T=1, dt0=0.5, M=2, scalar QoI; "
+                                  "warm-up + Alg. 3 level set; tol 1e-2 * 2^(-r/2), r=0..6"},
+           "runs": runs}
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -663,7 +702,7 @@ def main():
         run_gpu(args)
     else:
         {"twolevel": run_twolevel, "precision": run_precision, "batched64": run_batched64,
-         "serving": run_serving}[args.workload](args)
+         "serving": run_serving, "complexity": run_complexity}[args.workload](args)
 
 
 if __name__ == "__main__":

@@ -148,3 +148,24 @@ def test_periodic_benchmark_estimates_match_exact_value(mk):
         # Every periodic sample lands in [0, 1): the level-0 histogram carries
         # mass 1 and each correction level carries mass 0.
         assert float(np.sum(r.density)) / d["nbins"] == pytest.approx(1.0, abs=1e-12)
+
+
+@pytest.mark.parametrize("eps", [1.0, 0.1])
+def test_tolerance_sequence_cost_grows_like_tol_minus_two(mk, ctx, eps):
+    """Sec. 5.3 protocol end to end on the device: the off-line warm-up,
+    Alg. 3 level selection, then one estimate through tol_r = 10^-2 2^(-r/2).
+    Once the sample counts are well above the warm-up, the KD events of all
+    samples grow like tol^-2 (the O(eps^-2) complexity of Sec. 5.3), and every
+    stage meets its statistical budget."""
+    d = dict(W.periodic_problem(eps), nbins=0)
+    V, Vd, tau = ctx.level_warmup(mk.make_problem(precision=mk.PREC_FP32_COMP, **d), 100)
+    levels = mk.level_select(V, Vd)
+    assert levels[-1] == d["L"]
+    q = mk.make_problem(precision=mk.PREC_FP32_COMP, level_set=levels, **d)
+    tols = [1e-2 * 2.0 ** (-r / 2.0) for r in range(7)]
+    stages = ctx.estimate_sequence(q, tols)
+    ev = [sum(lv["events_f"] + lv["events_c"] for lv in r.levels) for r in stages]
+    for tol, r in zip(tols, stages):
+        assert r.variance <= tol * tol / 2 * (1 + 1e-9)
+    slope = np.polyfit(np.log(tols[-4:]), np.log(ev[-4:]), 1)[0]
+    assert -2.2 < slope < -1.8, slope
