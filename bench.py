@@ -240,6 +240,21 @@ def run_gpu(args):
     ttt, ttt_res = ttt_runs[1]
     exact = exact_values()
 
+    # the same estimates on the level sets of the Sec. 5.3 protocol (off-line
+    # warm-up, Alg. 3), the warm-up's time included
+    def ttt_selected():
+        t = time.perf_counter()
+        sets = []
+        for d in dicts:
+            V, Vd, _ = ctx.level_warmup(mk.make_problem(precision=prec, **d), 100, stream)
+            sets.append(mk.level_select(V, Vd))
+        probs = [mk.make_problem(precision=prec, level_set=ls, **d) for d, ls in zip(dicts, sets)]
+        rs = ttt_once(probs)[1]
+        return time.perf_counter() - t, rs, sets
+
+    ttt_selected()
+    ttt_sel, sel_res, sel_sets = sorted((ttt_selected() for _ in range(3)), key=lambda x: x[0])[1]
+
     # the same adaptive estimates in plain FP64, one per-level call per
     # estimate (the comparison the metric names), after one warm-up call
     fp64 = [mk.make_problem(precision=mk.PREC_FP64, **d) for d in dicts]
@@ -341,6 +356,12 @@ def run_gpu(args):
                    "exact_values": exact,
                    "time_to_tolerance_error_in_sd": [(r.estimate - x) / math.sqrt(r.variance)
                                                      for r, x in zip(ttt_res, exact)],
+                   "time_to_tolerance_level_selected_s": ttt_sel,
+                   "level_selected_sets": sel_sets,
+                   "level_selected_events": [sum(lv["events_f"] + lv["events_c"] for lv in r.levels)
+                                             for r in sel_res],
+                   "level_selected_error_in_sd": [(r.estimate - x) / math.sqrt(r.variance)
+                                                  for r, x in zip(sel_res, exact)],
                    "time_to_tolerance_plain_fp64_s": ttt_fp64,
                    "time_to_tolerance_speedup_vs_plain_fp64": ttt_fp64 / ttt,
                    "estimates_plain_fp64": [r.estimate for r in r64],
