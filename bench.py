@@ -40,21 +40,53 @@ TOL = 1e-3
 
 # Algorithmic instruction budget per KD event of the FP32 pair kernel (lane
 # instructions): Philox4x32-10 block, three uniforms, Box-Muller and -log u,
-# the KD coefficients and position update, the aggregation weights.  Stated
-# with its derivation in the design notes; the ncu summary
-# profiles/pair_kernel_fp32_periodic.md gives the measured count.
-# DRAM bytes (read + written) of one full-size launch of the batched pair
-# kernel on this workload, from ncu (dram__bytes_read.sum +
-# dram__bytes_write.sum; profiles/batch_pair_kernel_periodic.md).  A counter
-# taken for one build of the kernel: re-take it whenever the kernel changes.
-DRAM_BYTES_PER_LAUNCH = 1157120 + 4096
-# From the same capture: warp instructions issued over (4 per SM per cycle x
-# elapsed cycles), i.e. the measured use of the FP32/INT issue slots.
-ISSUE_FRACTION_NCU = 0.757
+# the KD coefficients and position update, the aggregation weights; stated
+# with its derivation in the design notes.
 INST_PER_FINE_EVENT = 190.0
 INST_PER_COARSE_EVENT = 50.0
+# ncu counters of one full-size launch of the batched pair kernel (DRAM bytes
+# read + written, issue-slot use) are kept in the profile summary of that
+# kernel, with a hash of the kernel sources they were taken on; the bench
+# line reports them only while the sources still have that hash.
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "batch_pair_kernel_periodic.md")
+KERNEL_SOURCES = ("mlkd_batch.cu", "mlkd_pair.cuh", "mlkd_device.cuh", "mlkd_internal.h")
+TTT_RUNS = 11
+# N_l of the benchmark's adaptive pilot at tol 1e-3 (eps = 1, 0.1, 1e-3; as
+# measured on GB300 with the FP32_COMP batched form), for the fixed ncu case.
+PILOT_N_FIXED = [[352000, 181600],
+                 [9000000, 3040000, 2560000, 3144000, 2544000, 2000000, 1584000, 1352000, 800000],
+                 [6280000, 800, 800, 800, 800, 800, 800, 800, 800, 800, 18320, 19440, 20800]]
 SMSP_PER_SM = 4
 LANES = 32
+
+
+def kernel_sources_hash() -> str:
+    """First 16 hex digits of the SHA-256 of the batched kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2004_04071_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def profile_counters():
+    """(traffic bytes per launch, issue fraction, note) from the profile
+    summary's 'counters:' line, or (None, None, why) when that line is
+    missing or was taken on other kernel sources."""
+    import re
+    try:
+        with open(PROFILE_SUMMARY) as f:
+            text = f.read()
+    except OSError:
+        return None, None, "no profile summary"
+    m = re.search(r"counters: sources=([0-9a-f]{16}) traffic_bytes_per_launch=(\d+) "
+                  r"issue_fraction=([0-9.]+)", text)
+    if not m:
+        return None, None, "no counters line in the profile summary"
+    if m.group(1) != kernel_sources_hash():
+        return None, None, "counters were taken on other kernel sources (%s)" % m.group(1)
+    return int(m.group(2)), float(m.group(3)), "ncu, sources %s" % m.group(1)
 
 
 def parse():
@@ -68,12 +100,17 @@ def parse():
                     help="batched persistent form (default) or the per-level form")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--oracle-ttt-seconds", type=float, default=90.0,
+                    help="budget of the oracle's time to tolerance (0: skip it)")
     ap.add_argument("--workload", default="periodic",
                     choices=["periodic", "twolevel", "precision", "batched64", "serving",
-                             "complexity"],
+                             "complexity", "kernelcase"],
                     help="periodic: the headline (full periodic MLMC); the others measure the "
                          "two-level, precision, batched and serving configurations, and the "
-                         "cost-tolerance slope of the Sec. 5.3 protocol")
+                         "cost-tolerance slope of the Sec. 5.3 protocol; kernelcase: fixed "
+                         "launches for ncu captures")
+    ap.add_argument("--scale", type=int, default=0,
+                    help="kernelcase: log2 scale of the pair counts (batch: 3 is the full step)")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="serving: arrivals per second")
     ap.add_argument("--time-limit", type=float, default=60.0,
@@ -236,8 +273,11 @@ def run_gpu(args):
 
     for _ in range(args.warmup):
         step()
-    ttt_runs = sorted((ttt_once(adaptive) for _ in range(3)), key=lambda x: x[0])
-    ttt, ttt_res = ttt_runs[1]
+    # time to tolerance over TTT_RUNS runs (the same estimates each time):
+    # the median, and every run in order, so that the spread is visible
+    ttt_runs = [ttt_once(adaptive) for _ in range(TTT_RUNS)]
+    ttt_all = [t for t, _ in ttt_runs]
+    ttt, ttt_res = sorted(ttt_runs, key=lambda x: x[0])[len(ttt_runs) // 2]
     exact = exact_values()
 
     # the same estimates on the level sets of the Sec. 5.3 protocol (off-line
@@ -326,6 +366,8 @@ def run_gpu(args):
 
     (t_dev, t_host), (ev,) = reduce_over_ranks([dev_ms / 1e3, host_s], [float(events_total)])
 
+    traffic, issue_ncu, counters_note = (profile_counters() if args.form == "batch" and args.precision == "fp32comp"
+                                         else (None, None, "counters are taken for the FP32_COMP batched kernel"))
     kernel_s = rt["pair_kernel_ms"] / 1e3
     algo_inst = fine * INST_PER_FINE_EVENT + coarse * INST_PER_COARSE_EVENT
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
@@ -349,6 +391,8 @@ def run_gpu(args):
                    "autotune": tune,  # seconds over ppt {1,2,4,8} x substeps {16,64,256,unbounded}
                    "events_per_step": ev / args.steps / world,
                    "time_to_tolerance_s": ttt, "time_to_tolerance_first_call_s": ttt_first,
+                   "time_to_tolerance_runs_s": ttt_all,
+                   "time_to_tolerance_spread_s": [min(ttt_all), max(ttt_all)],
                    "time_to_tolerance_rounds": [r.rounds for r in ttt_res],
                    "time_to_tolerance_estimates": [r.estimate for r in ttt_res],
                    "time_to_tolerance_variances": [r.variance for r in ttt_res],
@@ -376,9 +420,10 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak / 1e9,
                      "unit": "Ginst/s (lane instructions)",
                      "frac": achieved / peak if peak else None,
-                     "traffic": DRAM_BYTES_PER_LAUNCH if args.form == "batch" and args.precision == "fp32comp" else None,
+                     "traffic": traffic,
                      "traffic_unit": "bytes per launch that carries the step's pairs (ncu)",
-                     "issue_fraction_ncu": ISSUE_FRACTION_NCU if args.form == "batch" and args.precision == "fp32comp" else None,
+                     "issue_fraction_ncu": issue_ncu,
+                     "counters": counters_note,
                      "kernel": kname,
                      "launches_timed": rt["launches"],
                      "avg_launch_ms": rt["pair_kernel_ms"] / max(1, rt["launches"]),
@@ -389,7 +434,10 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, fixed)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, fixed, ev / args.steps / world,
+                                           args.oracle_ttt_seconds)
+        out["config"]["time_to_tolerance_oracle_s"] = \
+            out["cpu_baseline"].get("time_to_tolerance", {}).get("time_to_tolerance_s")
         print(json.dumps(out), flush=True)
     ctx.close()
     if world > 1:
@@ -433,16 +481,54 @@ def oracle_sample(cpu_seconds: float, fixed=None, threads=None):
                       % (rounds, pairs, ev, dt)}
 
 
-def cpu_baseline(cpu_seconds, fixed):
+def oracle_time_to_tolerance(threads, events_per_step, rate, budget_s):
+    """The oracle's adaptive estimates of the workload (warm-up, then rounds
+    of eqs. Nopt1/Noptj until the statistical constraint holds), one after
+    the other on `threads` host threads.  Its work is about the step's
+    events (the step runs the same final N_l); if that would take longer
+    than budget_s at the measured oracle rate, each estimate runs at the
+    looser tolerance tol' = tol sqrt(projected/budget) and its time is scaled
+    by (tol'/tol)^2, the O(tol^-2) cost of the estimator, and the line says
+    so."""
+    import oracle as O
+    projected = events_per_step / rate if rate else float("inf")
+    scale = max(1.0, projected / budget_s)
+    tol = TOL * math.sqrt(scale)
+    runs, total = [], 0.0
+    for i, eps in enumerate(EPS_SET):
+        d = W.periodic_problem(eps, seed=0, tol=tol)
+        p = O.Problem(**{k: d[k] for k in ("eps", "T", "dt0", "M", "L", "qoi", "init", "nbins",
+                                           "lo", "hi", "tol", "n_warmup", "seed")}, request=i)
+        t = time.perf_counter()
+        r = O.estimate(p, threads=threads)
+        dt = time.perf_counter() - t
+        total += dt
+        runs.append({"eps": eps, "seconds": dt, "estimate": r.estimate, "variance": r.variance,
+                     "met": r.variance <= tol * tol / 2 * (1 + 1e-9),
+                     "n": [s.n for s in r.levels]})
+    return {"time_to_tolerance_s": total * scale, "tol_run": tol, "scaled_by": scale,
+            "projected_s_at_tol": projected, "cores": threads, "runs": runs,
+            "how": ("oracle.estimate at tol %.3g on %d threads, time x %.3g to tol %.3g"
+                    % (tol, threads, scale, TOL)) if scale > 1.0 else
+                   ("oracle.estimate at tol %.3g on %d threads, measured whole" % (TOL, threads))}
+
+
+def cpu_baseline(cpu_seconds, fixed, events_per_step=None, ttt_budget_s=90.0):
     try:
         out = oracle_sample(cpu_seconds, fixed)
         one = oracle_sample(max(1.0, cpu_seconds / 5), fixed, threads=1)
         out["value_1_thread"] = one["value"]
         out["sample_1_thread"] = one["sample"]
-        return out
     except Exception as exc:  # the baseline must not sink the GPU line
         return {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                 "sample": "failed: %s" % exc}
+    if events_per_step and ttt_budget_s > 0:
+        try:
+            out["time_to_tolerance"] = oracle_time_to_tolerance(out["cores"], events_per_step,
+                                                                out["value"], ttt_budget_s)
+        except Exception as exc:
+            out["time_to_tolerance"] = {"failed": str(exc)}
+    return out
 
 
 def run_reference(args):
@@ -641,7 +727,7 @@ def run_serving(args):
             d = dict(stream[i])
             d.pop("arrival")
             p = mk.make_problem(precision=prec, **d)
-            pending[ctx.submit(p)] = (d, p.nbins)
+            pending[ctx.submit(p)] = (d, p.nbins, time.perf_counter())
             i += 1
         for rid in list(pending):
             rc, r = ctx.poll(rid, 0, nbins=pending[rid][1])
@@ -654,11 +740,22 @@ def run_serving(args):
         if deadline is not None and time.perf_counter() > deadline:
             break
         time.sleep(0.0005)
-    wall = time.perf_counter() - t0
+    t_end = time.perf_counter()
+    wall = t_end - t0
     st = ctx.server_stats()
     ctx.server_stop()
     lat = sorted(r.seconds for _, r in done)
     q = lambda f: lat[min(len(lat) - 1, int(f * len(lat)))] if lat else None
+    # over ALL requests: an unfinished request's latency is censored at the
+    # time it had waited when the run stopped (a lower bound)
+    everyone = sorted([(r.seconds, False) for _, r in done] +
+                      [(t_end - ts, True) for (_, _, ts) in pending.values()])
+
+    def q_all(f):
+        if not everyone:
+            return None
+        v, cens = everyone[min(len(everyone) - 1, int(f * len(everyone)))]
+        return {"seconds": v, "censored": cens}
     ev = _events([r for _, r in done])
     ok = sum(1 for d, r in done if r.variance <= d["tol"] ** 2 / 2 * (1 + 1e-9))
     out = {"metric": "serving: p50/p99 latency and estimates/s (Poisson arrivals)",
@@ -667,7 +764,12 @@ def run_serving(args):
            "rate": args.rate, "slots": args.slots, "substeps_per_launch": args.substeps,
            "arena_bytes": mk.batch_workspace_bytes(cfg),
            "completed": len(done), "unfinished_at_limit": len(pending),
-           "latency_p50_s": q(0.5), "latency_p99_s": q(0.99), "wall_s": wall,
+           "latency_all_p50": q_all(0.5), "latency_all_p99": q_all(0.99),
+           "latency_all_note": "over every request of the stream; an unfinished request counts "
+                               "with the time it had waited at the stop (censored: a lower bound)",
+           "latency_finished_p50_s": q(0.5), "latency_finished_p99_s": q(0.99), "wall_s": wall,
+           "finished_per_s": len(done) / wall,
+           "admitted": st["admitted"], "queued_at_stop": st["submitted"] - st["admitted"],
            "events_per_s": st["events_processed"] / wall,
            "events_per_busy_s": st["events_processed"] / st["busy_seconds"] if st["busy_seconds"] else None,
            "merged_events_per_s": st["events"] / wall,
@@ -715,6 +817,45 @@ def run_complexity(args):
     ctx.close()
 
 
+def run_kernelcase(args):
+    """Fixed pair-kernel launches for ncu captures (no timing, one JSON line).
+
+    --form batch: the benchmark's three periodic estimates (eps = 1, 0.1,
+    1e-3) with the N_l of its pilot at tol 1e-3 scaled by 2^scale / 8, in one
+    batched call with unbounded slices and no graph, so that the pair work is
+    one batch_pair_kernel launch (scale 3 is the full step).  Device memory:
+    the batch arena, about 0.3 GB.
+    --form plain: three per-level launches on the periodic problem --
+    eps = 0.1 level 8 (mixed regime), eps = 1e-3 level 6 (deep diffusive),
+    eps = 0.1 level 0 (start-dominated) -- of 2^(20+scale) pairs (2^(22+scale)
+    for level 0).  Device memory: the 0.7 MB context arena."""
+    import torch
+    import paper_2004_04071_gb300 as mk
+    torch.cuda.set_device(0)
+    prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
+    out = {"workload": "kernelcase", "form": args.form, "precision": args.precision,
+           "scale": args.scale, "launches": []}
+    if args.form == "batch":
+        cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=0, use_graph=0,
+                              max_requests=16, max_nbins=128)
+        ctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
+        fixed = [[max(1, (x << args.scale) >> 3) for x in n] for n in PILOT_N_FIXED]
+        probs = [mk.make_problem(precision=prec, n_fixed=n, request=i, **dict(W.periodic_problem(e)))
+                 for i, (e, n) in enumerate(zip(EPS_SET, fixed))]
+        rs = ctx.estimate_batch(probs, cfg)
+        out["launches"] = [{"eps": e, "events": sum(lv["events_f"] + lv["events_c"] for lv in r.levels)}
+                           for e, r in zip(EPS_SET, rs)]
+    else:
+        ctx = mk.Context(0)
+        for eps, level, n in ((0.1, 8, 1 << 20), (1e-3, 6, 1 << 20), (0.1, 0, 1 << 22)):
+            p = mk.make_problem(precision=prec, **W.periodic_problem(eps))
+            st = ctx.run_level(p, level, 0, n << args.scale)
+            out["launches"].append({"eps": eps, "level": level, "pairs": n << args.scale,
+                                    "events_f": st["events_f"], "events_c": st["events_c"]})
+    ctx.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -723,7 +864,8 @@ def main():
         run_gpu(args)
     else:
         {"twolevel": run_twolevel, "precision": run_precision, "batched64": run_batched64,
-         "serving": run_serving, "complexity": run_complexity}[args.workload](args)
+         "serving": run_serving, "complexity": run_complexity,
+         "kernelcase": run_kernelcase}[args.workload](args)
 
 
 if __name__ == "__main__":

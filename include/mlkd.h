@@ -43,7 +43,7 @@ extern "C" {
 #define MLKD_API
 #endif
 
-#define MLKD_ABI_VERSION 1
+#define MLKD_ABI_VERSION 2
 #define MLKD_MAX_LEVELS 16      /* levels 0..15 */
 #define MLKD_MAX_BINS 1024
 
@@ -298,6 +298,13 @@ typedef struct {
     int32_t max_nbins;           /* histogram bins per request (<= 256)                      */
     int32_t refill_min;          /* a warp sums and restarts finished pairs once this many of
                                     its lanes are idle (1..32; 0: library default)           */
+    int32_t publish_wait_spins;  /* bound of the device wait for earlier reservations of a
+                                    work queue to be published (0: library default, 2^22);
+                                    a wait that runs out ends the call with MLKD_ETIMEDOUT   */
+    int32_t test_stall_queues;   /* test hook, 0 in normal use: n > 0 leaves n reserved
+                                    places at the head of every work queue that are never
+                                    published, so that the first publication wait runs out
+                                    (0 .. 2^20)                                               */
 } mlkd_batch_config;
 
 /* Arena bytes a context needs for the batched and serving forms with this
@@ -388,9 +395,11 @@ MLKD_API mlkd_status mlkd_server_stop(mlkd_context *ctx);
  * Scratch: the block partial sums, the level sums and the histogram counters
  * live in one file-scope device array inside the library of
  * MLKD_NOALLOC_SCRATCH_BYTES (137 472 bytes), which every GPU that loads the
- * library holds until the process exits.  The first call on a device (with
- * that device current) looks up the array's device address; make this first
- * call before any stream capture on that device.
+ * library holds until the process exits.  The first call in each CUDA
+ * context of a device (with that device current) looks up the array's device
+ * address; make this first call before any stream capture on that device.
+ * A device reset gives the device a new context, in which the next call
+ * looks the address up again.
  *
  * Limits: nbins <= MLKD_NOALLOC_MAX_BINS, else MLKD_ENOMEM; the grid is
  * capped at MLKD_NOALLOC_MAX_BLOCKS blocks (any n_pairs is accepted).
@@ -398,7 +407,11 @@ MLKD_API mlkd_status mlkd_server_stop(mlkd_context *ctx);
  * work overlaps (different streams or host threads) race on it and return
  * wrong sums, so serialise them.  Problem validation, pair streams, outputs
  * and synchronisation are as for mlkd_run_level; the call uses the current
- * CUDA device and calls no device allocator. */
+ * CUDA device and calls no device allocator.  Event counts and histogram
+ * counts equal mlkd_run_level's exactly.  The floating-point sums equal them
+ * bit for bit while the grid of mlkd_run_level (SMs x resident blocks, at
+ * most 4096) fits under MLKD_NOALLOC_MAX_BLOCKS; where the cap binds, the
+ * pairs are split over fewer blocks and the sums agree to rounding only. */
 #define MLKD_NOALLOC_MAX_BLOCKS 2048
 #define MLKD_NOALLOC_MAX_BINS 256
 #define MLKD_NOALLOC_SCRATCH_BYTES (MLKD_NOALLOC_MAX_BLOCKS * 64 + 256 + 3 * MLKD_NOALLOC_MAX_BINS * 8)

@@ -1,4 +1,6 @@
-"""Exact characteristic function of the KD scheme's displacement (test helper).
+"""Exact characteristic function of the KD scheme's displacement -- TEST
+INFRASTRUCTURE ONLY (part of the oracle: only tests/, the smoke check and the
+CPU-baseline leg of the benchmark use it).
 
 For the homogeneous background with mu = 0, a path of Alg. 1 on the grid
 dt_l = T/n is a sequence of KD events.  From a grid point (or t = 0) a flight

@@ -29,6 +29,7 @@ INIT_ORIGIN, INIT_COSINE = 0, 1
 PREC_FP64, PREC_FP32_DY64, PREC_FP32_COMP, PREC_FP64_U24 = 0, 1, 2, 3
 MAX_LEVELS = 16
 MAX_BINS = 1024
+ABI_VERSION = 2
 
 EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_context_create", "mlkd_context_destroy", "mlkd_run_level",
@@ -85,17 +86,19 @@ class Result(ctypes.Structure):
 class BatchConfig(ctypes.Structure):
     _fields_ = [("pairs_per_thread", ctypes.c_int32), ("substeps_per_launch", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("max_requests", ctypes.c_int32),
-                ("max_nbins", ctypes.c_int32), ("refill_min", ctypes.c_int32)]
+                ("max_nbins", ctypes.c_int32), ("refill_min", ctypes.c_int32),
+                ("publish_wait_spins", ctypes.c_int32), ("test_stall_queues", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def batch_config(pairs_per_thread=1, substeps_per_launch=256, use_graph=1, max_requests=64,
-                 max_nbins=128, refill_min=0) -> BatchConfig:
+                 max_nbins=128, refill_min=0, publish_wait_spins=0, test_stall_queues=0) -> BatchConfig:
     c = BatchConfig()
     c.pairs_per_thread, c.substeps_per_launch, c.use_graph = pairs_per_thread, substeps_per_launch, use_graph
     c.max_requests, c.max_nbins, c.refill_min = max_requests, max_nbins, refill_min
+    c.publish_wait_spins, c.test_stall_queues = publish_wait_spins, test_stall_queues
     return c
 
 
@@ -137,6 +140,9 @@ def lib():
         L.mlkd_status_string.argtypes = [ctypes.c_int]
         L.mlkd_status_string.restype = ctypes.c_char_p
         L.mlkd_abi_version.restype = ctypes.c_int
+        if L.mlkd_abi_version() != ABI_VERSION:
+            raise RuntimeError("libmlkd.so has ABI version %d, the binding expects %d; rebuild it"
+                               % (L.mlkd_abi_version(), ABI_VERSION))
         L.mlkd_workspace_bytes.argtypes = [P(Problem)]
         L.mlkd_workspace_bytes.restype = ctypes.c_size_t
         L.mlkd_context_create.argtypes = [ctypes.c_int, vp, ctypes.c_size_t, P(vp)]
@@ -266,17 +272,6 @@ def level_select_opt(V, rho, C):
     n = ctypes.c_int32()
     _check(lib().mlkd_level_select_opt(v, r, c, L, out, ctypes.byref(n)), "mlkd_level_select_opt")
     return [int(out[i]) for i in range(n.value)]
-
-
-def level_variances(result):
-    """(V_l, Vd_l) of an all-levels estimate: variance of F on each level's
-    fine path and of the adjacent difference Y_l."""
-    V, Vd = [], []
-    for lv in result.levels:
-        n = lv["n"]
-        V.append((lv["sqf2"] - lv["sqf"] ** 2 / n) / (n - 1) if n > 1 else 0.0)
-        Vd.append((lv["sy2"] - lv["sy"] ** 2 / n) / (n - 1) if n > 1 else 0.0)
-    return V, Vd
 
 
 def workspace_bytes(problem: Problem) -> int:

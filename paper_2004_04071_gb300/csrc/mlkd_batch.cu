@@ -135,6 +135,8 @@ struct BatchLaunch {
     int32_t slice_iters;
     int32_t n_slots;
     int32_t refill_min;          // idle lanes a warp gathers before it restarts them together
+    int32_t publish_spins;       // bound of the publication wait
+    int32_t pad_;
     PhiloxKeys keys;
 };
 
@@ -217,7 +219,9 @@ __device__ long long chunk_target(double events_per_pair)
 
 // Appends chunk ids [id0, id0 + n) to a queue (whole warp): reserve, write,
 // publish in reservation order.  The wait for earlier reservations is
-// bounded; running out sets BatchCtl::error, which ends the loop.
+// bounded; running out sets BatchCtl::error, which ends the loop, and leaves
+// the ids unpublished (consumers never see places that an earlier, stalled
+// reservation may not have written).
 __device__ void push_ids(const BatchLaunch &B, unsigned long long *ring, unsigned long long *resv,
                          unsigned long long *tail, int32_t *avail, unsigned long long id0, int n, int lane)
 {
@@ -230,14 +234,16 @@ __device__ void push_ids(const BatchLaunch &B, unsigned long long *ring, unsigne
     __syncwarp();
     if (lane == 0) {
         int k = 0;
+        bool published = true;
         while (atomicCAS(tail, base, base + (unsigned long long)n) != base) {
-            if (++k >= kPublishSpins) {
+            if (++k >= B.publish_spins) {
                 atomicExch(&B.ctl->error, 1);
+                published = false;
                 break;
             }
             __nanosleep(32);
         }
-        atomicAdd(avail, n);
+        if (published) atomicAdd(avail, n);
     }
     __syncwarp();
 }
@@ -848,6 +854,8 @@ static bool batch_cfg_ok(const mlkd_batch_config *c)
         c->pairs_per_thread != 8) return false;
     if (c->substeps_per_launch < 0) return false;
     if (c->refill_min < 0 || c->refill_min > 32) return false;
+    if (c->publish_wait_spins < 0) return false;
+    if (c->test_stall_queues < 0 || c->test_stall_queues > (1 << 20)) return false;
     if (c->max_requests < 1 || c->max_requests > 4096) return false;
     if (c->max_nbins < 0 || c->max_nbins > 256) return false;
     return true;
@@ -980,8 +988,24 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->max_nbins = cfg->max_nbins > 0 ? cfg->max_nbins : 1;
     B->slice_iters = cfg->substeps_per_launch;
     B->refill_min = cfg->refill_min > 0 ? cfg->refill_min : kRefillMin;
+    B->publish_spins = cfg->publish_wait_spins > 0 ? cfg->publish_wait_spins : kPublishSpins;
     B->n_slots = n_slots;
     fill_keys(seed, &B->keys);
+}
+
+// Test hook (mlkd_batch_config::test_stall_queues): n places reserved at the
+// head of every queue that nobody ever publishes, so that the first
+// producer's bounded publication wait runs out.  Written after BatchCtl is
+// cleared.
+static mlkd_status stall_queues(char *ctl, int n, cudaStream_t s)
+{
+    if (n <= 0) return MLKD_OK;
+    const unsigned long long v = (unsigned long long)n;
+    MLKD_CUDA(cudaMemcpyAsync(ctl + offsetof(BatchCtl, q_resv), &v, sizeof(v), cudaMemcpyHostToDevice, s));
+    MLKD_CUDA(cudaMemcpyAsync(ctl + offsetof(BatchCtl, l_resv), &v, sizeof(v), cudaMemcpyHostToDevice, s));
+    MLKD_CUDA(cudaMemcpyAsync(ctl + offsetof(BatchCtl, p_resv), &v, sizeof(v), cudaMemcpyHostToDevice, s));
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    return MLKD_OK;
 }
 
 // Enqueues the loop body once: scheduler, pair slice, bookkeeping.
@@ -1055,6 +1079,10 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
     MLKD_CUDA(cudaMemsetAsync(ctx->arena + BL.hist, 0, hist_bytes, s));
     MLKD_CUDA(cudaMemsetAsync(ctx->arena + BL.ctl, 0, sizeof(BatchCtl), s));
     MLKD_CUDA(cudaMemsetAsync(ctx->arena + BL.hdr, 0, (kMaxLanes / 32) * sizeof(WarpHdr), s));
+    {
+        const mlkd_status hs = stall_queues(ctx->arena + BL.ctl, cfg->test_stall_queues, s);
+        if (hs != MLKD_OK) return hs;
+    }
 
     BatchLaunch B;
     make_launch(ctx, BL, cfg, n, seed, &B);
@@ -1459,6 +1487,8 @@ static mlkd_status server_start(mlkd_context *ctx, const mlkd_server_config *cfg
         cudaMemsetAsync(ctx->arena + BL.ctl, 0, sizeof(BatchCtl), S->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->arena + BL.hdr, 0, (kMaxLanes / 32) * sizeof(WarpHdr), S->stream) != cudaSuccess ||
         cudaMemsetAsync(ctx->arena + BL.status, 0, (size_t)n * sizeof(int32_t), S->stream) != cudaSuccess)
+        return fail(MLKD_ECUDA);
+    if (stall_queues(ctx->arena + BL.ctl, cfg->batch.test_stall_queues, S->stream) != MLKD_OK)
         return fail(MLKD_ECUDA);
     make_launch(ctx, BL, &cfg->batch, n, cfg->seed, &S->B);
     if (batch_grid(ctx, S->mode, S->ppt, cfg->batch.max_nbins, &S->grid) != MLKD_OK) return fail(MLKD_ECUDA);

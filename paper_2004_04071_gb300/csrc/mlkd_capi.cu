@@ -9,6 +9,8 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>
+
 #include "mlkd_host.h"
 
 using namespace mlkd;
@@ -760,21 +762,60 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 namespace {
 
 constexpr int kNoAllocMaxDevices = 64;
-std::mutex g_noalloc_mutex;
-void *g_noalloc_device_ptr[kNoAllocMaxDevices] = {};
 
-// Device address of the scratch array on `device` (the current device),
-// looked up once per device.
+// The array's device address belongs to the CUDA context that loaded the
+// module: after a device reset (or a primary-context teardown) the module is
+// loaded again at another address.  The cached address is therefore keyed on
+// the unique id of the current context (cuCtxGetId, reached through the
+// runtime's driver entry points, so the library does not link libcuda), and
+// looked up again whenever that id changes.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+struct NoAllocSlot {
+    unsigned long long ctx_id;
+    void *ptr;
+};
+
+std::mutex g_noalloc_mutex;
+NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices] = {};
+CtxGetCurrentFn g_ctx_get_current = nullptr;
+CtxGetIdFn g_ctx_get_id = nullptr;
+
+// Unique id of the current context (0 if it cannot be read).
+bool current_context_id(unsigned long long *id)
+{
+    if (!g_ctx_get_current || !g_ctx_get_id) {
+        void *f1 = nullptr, *f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) != cudaSuccess ||
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) != cudaSuccess ||
+            q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !f1 || !f2)
+            return false;
+        g_ctx_get_current = (CtxGetCurrentFn)f1;
+        g_ctx_get_id = (CtxGetIdFn)f2;
+    }
+    CUcontext ctx = nullptr;
+    if (g_ctx_get_current(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_ctx_get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array in the current context of `device`
+// (the current device): looked up on the first call in each context.
 mlkd_status noalloc_scratch(int device, unsigned char **out)
 {
     if (device < 0 || device >= kNoAllocMaxDevices) return MLKD_EINVAL;
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-    if (!g_noalloc_device_ptr[device]) {
+    unsigned long long id = 0;
+    if (!current_context_id(&id)) return MLKD_ECUDA;
+    NoAllocSlot &slot = g_noalloc_slot[device];
+    if (!slot.ptr || slot.ctx_id != id) {
         void *ptr = nullptr;
         if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return MLKD_ECUDA;
-        g_noalloc_device_ptr[device] = ptr;
+        slot.ptr = ptr;
+        slot.ctx_id = id;
     }
-    *out = (unsigned char *)g_noalloc_device_ptr[device];
+    *out = (unsigned char *)slot.ptr;
     return MLKD_OK;
 }
 

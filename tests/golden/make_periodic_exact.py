@@ -18,11 +18,10 @@ import os
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-sys.path.insert(0, os.path.dirname(HERE))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
 import workloads as W  # noqa: E402
-from kd_charfn import kd_charfn  # noqa: E402
+from oracle.kd_charfn import kd_charfn  # noqa: E402
 
 
 def main():

@@ -265,7 +265,7 @@ def test_full_size_periodic_step_matches_per_level_form(mk):
 
 
 def _exact_periodic(eps, dt, n):
-    from kd_charfn import kd_charfn
+    from oracle.kd_charfn import kd_charfn
     return 1.0 / 3.0 + kd_charfn(2 * math.pi, eps, dt, n) / (2 * math.pi ** 2)
 
 
@@ -308,3 +308,28 @@ def test_mse_of_200_adaptive_estimates(mk, ctx, case):
     lo, hi = stats.chi2.ppf([0.001, 0.999], n_est) / n_est
     assert lo < np.mean(z * z) < hi, np.mean(z * z)
     assert np.mean((est - exact) ** 2) < tol * tol / 2 * hi
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_publication_wait_runs_out_and_the_context_recovers(mk, ctx, use_graph):
+    """The device's bounded wait for earlier queue reservations: with the test
+    hook, every queue starts with places that are reserved and never
+    published, so the first producer's wait (bounded at 1000 spins here) runs
+    out.  The call must end with MLKD_ETIMEDOUT -- no fault, no hang, no
+    unpublished place read -- and the context must serve the next call
+    normally."""
+    ds = mixed_problems(1, seed=13)[:3]
+    probs = [gpu_problem(mk, d, precision=1) for d in ds]
+    stall = mk.batch_config(pairs_per_thread=1, substeps_per_launch=256, use_graph=use_graph,
+                            max_requests=64, max_nbins=128, publish_wait_spins=1000,
+                            test_stall_queues=64)
+    with pytest.raises(mk.MlkdError) as e:
+        ctx.estimate_batch(probs, stall)
+    assert e.value.status == mk.MLKD_ETIMEDOUT
+    good = mk.batch_config(pairs_per_thread=1, substeps_per_launch=256, use_graph=use_graph,
+                           max_requests=64, max_nbins=128)
+    after = ctx.estimate_batch(probs, good)
+    fresh = ctx.estimate_batch(probs, good)
+    for a, b, d in zip(after, fresh, ds):
+        assert a.estimate == b.estimate and a.variance == b.variance
+        assert a.variance <= d["tol"] ** 2 / 2 * (1 + 1e-6)

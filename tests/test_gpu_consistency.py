@@ -25,7 +25,7 @@ from scipy import stats
 
 import workloads as W
 from helpers import check_level_curve, gpu_problem, level_curve
-from kd_charfn import kd_charfn
+from oracle.kd_charfn import kd_charfn
 
 pytestmark = pytest.mark.gpu
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import gpu_problem
+from helpers import gpu_problem, oracle_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -170,6 +170,34 @@ def test_submit_validation(mk):
             assert rc == mk.MLKD_EINVAL
         rc, _ = ctx.try_submit(gpu_problem(mk, dict(d, seed=7), precision=mk.PREC_FP64))
         assert rc == mk.MLKD_EINVAL
+    finally:
+        ctx.server_stop()
+        ctx.close()
+
+
+def test_fp64_server_results_match_oracle(orc, mk):
+    """FP64 requests through the server against the oracle's adaptive
+    estimate (eqs. Nopt1/Noptj) on the same request streams: the same N_l on
+    every level, and estimates, variances and densities equal to FP64
+    rounding of the sums."""
+    ds = [d for d in _requests(16, seed=3) if d["L"] <= 8][:4]
+    for d in ds:
+        d["tol"] = max(d["tol"], 0.1 if d["qoi"] == 2 else 5e-3)
+    ctx, cfg = _ctx(mk)
+    try:
+        ctx.server_start(mk.server_config(cfg, precision=mk.PREC_FP64, seed=0))
+        probs = [gpu_problem(mk, d, precision=mk.PREC_FP64) for d in ds]
+        ids = [ctx.submit(q) for q in probs]
+        for d, i, q in zip(ds, ids, probs):
+            rc, got = ctx.poll(i, -1, nbins=q.nbins)
+            assert rc == mk.MLKD_OK
+            ro = orc.estimate(oracle_problem(orc, d), threads=16)
+            assert [lv["n"] for lv in got.levels] == [s.n for s in ro.levels], d
+            assert [lv["events_f"] for lv in got.levels] == [s.events_f for s in ro.levels]
+            assert got.estimate == pytest.approx(ro.estimate, rel=1e-11, abs=1e-13)
+            assert got.variance == pytest.approx(ro.variance, rel=1e-9, abs=0)
+            if q.nbins:
+                np.testing.assert_allclose(got.density, ro.density, rtol=1e-11, atol=1e-11)
     finally:
         ctx.server_stop()
         ctx.close()

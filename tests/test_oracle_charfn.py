@@ -28,7 +28,7 @@ import numpy as np
 import pytest
 from scipy import stats
 
-from kd_charfn import kd_charfn
+from oracle.kd_charfn import kd_charfn
 
 Z = 4.5          # standard errors allowed per comparison
 KS = (math.pi, 2 * math.pi, 4 * math.pi)
