@@ -109,6 +109,8 @@ def parse():
                          "two-level, precision, batched and serving configurations, and the "
                          "cost-tolerance slope of the Sec. 5.3 protocol; kernelcase: fixed "
                          "launches for ncu captures")
+    ap.add_argument("--eps", type=float, default=None,
+                    help="kernelcase batch: only the estimate of this eps (default: all three)")
     ap.add_argument("--scale", type=int, default=0,
                     help="kernelcase: log2 scale of the pair counts (batch: 3 is the full step)")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
@@ -821,7 +823,8 @@ def run_kernelcase(args):
     """Fixed pair-kernel launches for ncu captures (no timing, one JSON line).
 
     --form batch: the benchmark's three periodic estimates (eps = 1, 0.1,
-    1e-3) with the N_l of its pilot at tol 1e-3 scaled by 2^scale / 8, in one
+    1e-3; --eps selects one) with the N_l of its pilot at tol 1e-3 scaled by
+    2^scale / 8, in one
     batched call with unbounded slices and no graph, so that the pair work is
     one batch_pair_kernel launch (scale 3 is the full step).  Device memory:
     the batch arena, about 0.3 GB.
@@ -840,11 +843,12 @@ def run_kernelcase(args):
                               max_requests=16, max_nbins=128)
         ctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
         fixed = [[max(1, (x << args.scale) >> 3) for x in n] for n in PILOT_N_FIXED]
-        probs = [mk.make_problem(precision=prec, n_fixed=n, request=i, **dict(W.periodic_problem(e)))
-                 for i, (e, n) in enumerate(zip(EPS_SET, fixed))]
+        sel = [i for i, e in enumerate(EPS_SET) if args.eps is None or e == args.eps]
+        probs = [mk.make_problem(precision=prec, n_fixed=fixed[i], request=i,
+                                 **dict(W.periodic_problem(EPS_SET[i]))) for i in sel]
         rs = ctx.estimate_batch(probs, cfg)
-        out["launches"] = [{"eps": e, "events": sum(lv["events_f"] + lv["events_c"] for lv in r.levels)}
-                           for e, r in zip(EPS_SET, rs)]
+        out["launches"] = [{"eps": EPS_SET[i], "events": sum(lv["events_f"] + lv["events_c"] for lv in r.levels)}
+                           for i, r in zip(sel, rs)]
     else:
         ctx = mk.Context(0)
         for eps, level, n in ((0.1, 8, 1 << 20), (1e-3, 6, 1 << 20), (0.1, 0, 1 << 22)):

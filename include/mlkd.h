@@ -197,6 +197,20 @@ MLKD_API mlkd_status mlkd_estimate_sequence(mlkd_context *ctx, const mlkd_proble
                                             int n_tol, const double *tols, void *stream,
                                             mlkd_result *results);
 
+/* Coarse random numbers of Sec. 5.1 (validation): for each pair j of
+ * [first_pair, first_pair + n_pairs) of coupled estimator level `level`
+ * (>= 1), the (nu~, E~, chi~) of its first per_pair coarse KD steps -- nu~ of
+ * eq. nu-update, E~ = R tau~ of eq. epsilon-update, chi~ of eq. chi-update --
+ * in device arrays nu_t, E_t, chi_t of n_pairs * per_pair doubles (pair j at
+ * [j * per_pair, (j + 1) * per_pair)), and count[j] (int32, device) = the
+ * pair's coarse steps (entries past per_pair are not written).  Same pair
+ * streams and arithmetic as mlkd_run_level, one thread per pair.  FP32_DY64
+ * runs as FP32_COMP (the draws do not depend on the sums).  Synchronous. */
+MLKD_API mlkd_status mlkd_debug_coarse_draws(mlkd_context *ctx, const mlkd_problem *problem, int level,
+                                             uint64_t first_pair, uint64_t n_pairs, int per_pair,
+                                             void *stream, double *nu_t, double *E_t, double *chi_t,
+                                             int32_t *count);
+
 /* Per-pair results of pairs [first_pair, first_pair + n_pairs) of `level`:
  * device arrays of n_pairs entries for the final fine and coarse positions
  * (xc = 0 on level 0) and the fine and coarse KD event counts.  Any of the
@@ -320,6 +334,20 @@ MLKD_API size_t mlkd_batch_workspace_bytes(const mlkd_batch_config *cfg);
 MLKD_API mlkd_status mlkd_estimate_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
                                          const mlkd_batch_config *cfg, void *stream,
                                          mlkd_result *results);
+
+/* Validation readout of the batched form: runs mlkd_estimate_batch on one
+ * problem with fixed sample counts (n_fixed required) and writes, for
+ * estimator level `level`, every pair's final fine and coarse positions and
+ * fine and coarse KD event counts as the batched pair kernel computed them:
+ * xf, xc (double) and kf, kc (int32) are device arrays of n_fixed[level]
+ * entries indexed by pair (xc = 0 and kc = 0 on level 0).  The kernel and its
+ * arithmetic are those of mlkd_estimate_batch with the same configuration;
+ * the readout adds one store per pair of that level.  A CUDA graph built for
+ * the readout is not kept.  Synchronous. */
+MLKD_API mlkd_status mlkd_debug_batch_pairs(mlkd_context *ctx, const mlkd_problem *problem,
+                                            const mlkd_batch_config *cfg, int level, void *stream,
+                                            mlkd_result *result, double *xf, double *xc,
+                                            int32_t *kf, int32_t *kc);
 
 /* Autotuner: times mlkd_estimate_batch on these problems for every
  * pairs_per_thread in {1, 2, 4, 8} and substeps_per_launch in

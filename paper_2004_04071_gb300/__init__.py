@@ -39,7 +39,7 @@ EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop",
             "mlkd_debug_transforms", "mlkd_level_select", "mlkd_estimate_resumable",
             "mlkd_level_select_opt", "mlkd_level_pilot", "mlkd_level_warmup",
-            "mlkd_estimate_sequence"]
+            "mlkd_estimate_sequence", "mlkd_debug_batch_pairs", "mlkd_debug_coarse_draws"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -167,6 +167,12 @@ def lib():
         L.mlkd_batch_workspace_bytes.restype = ctypes.c_size_t
         L.mlkd_estimate_batch.argtypes = [vp, P(Problem), ctypes.c_int, P(BatchConfig), vp, P(Result)]
         L.mlkd_estimate_batch.restype = ctypes.c_int
+        L.mlkd_debug_coarse_draws.argtypes = [vp, P(Problem), ctypes.c_int, u64, u64, ctypes.c_int,
+                                              vp, vp, vp, vp, vp]
+        L.mlkd_debug_coarse_draws.restype = ctypes.c_int
+        L.mlkd_debug_batch_pairs.argtypes = [vp, P(Problem), P(BatchConfig), ctypes.c_int, vp,
+                                             P(Result), vp, vp, vp, vp]
+        L.mlkd_debug_batch_pairs.restype = ctypes.c_int
         L.mlkd_autotune_batch.argtypes = [vp, P(Problem), ctypes.c_int, P(BatchConfig), vp,
                                           P(BatchConfig), P(ctypes.c_double)]
         L.mlkd_autotune_batch.restype = ctypes.c_int
@@ -407,6 +413,30 @@ class Context:
         return (xf[:n].cpu().numpy(), xc[:n].cpu().numpy(), kf[:n].cpu().numpy().astype(np.int64),
                 kc[:n].cpu().numpy().astype(np.int64))
 
+    def debug_coarse_draws(self, problem: Problem, level: int, first_pair: int, n_pairs: int,
+                           per_pair: int = 64, stream=None):
+        """mlkd_debug_coarse_draws: (nu~, E~, chi~, pair_of) of every recorded
+        coarse step, concatenated in pair order, and each pair's coarse-step
+        count (steps past per_pair are counted but not recorded)."""
+        import torch
+        dev = "cuda:%d" % self.device
+        m = max(n_pairs * per_pair, 1)
+        nu = torch.empty(m, dtype=torch.float64, device=dev)
+        E = torch.empty(m, dtype=torch.float64, device=dev)
+        chi = torch.empty(m, dtype=torch.float64, device=dev)
+        cnt = torch.empty(max(n_pairs, 1), dtype=torch.int32, device=dev)
+        vp = ctypes.c_void_p
+        _check(lib().mlkd_debug_coarse_draws(self.handle, ctypes.byref(problem), level, first_pair,
+                                             n_pairs, per_pair, _stream_handle(stream),
+                                             vp(nu.data_ptr()), vp(E.data_ptr()), vp(chi.data_ptr()),
+                                             vp(cnt.data_ptr())), "mlkd_debug_coarse_draws")
+        counts = cnt[:n_pairs].cpu().numpy().astype(np.int64)
+        rec = np.minimum(counts, per_pair)
+        idx = np.concatenate([j * per_pair + np.arange(r) for j, r in enumerate(rec)]) if n_pairs else \
+            np.zeros(0, np.int64)
+        pair_of = np.repeat(np.arange(n_pairs), rec)
+        return (nu.cpu().numpy()[idx], E.cpu().numpy()[idx], chi.cpu().numpy()[idx], pair_of, counts)
+
     # -- mlkd_estimate_batch / mlkd_autotune_batch ----------------------------
     def estimate_batch(self, problems, cfg: BatchConfig, stream=None):
         n = len(problems)
@@ -430,6 +460,34 @@ class Context:
                                       [r.var_level[l] for l in range(nl)],
                                       [r.cost_level[l] for l in range(nl)], dens[i], r.seconds))
         return out
+
+    def debug_batch_pairs(self, problem: Problem, cfg: BatchConfig, level: int, stream=None):
+        """mlkd_debug_batch_pairs: (EstimateResult, xf, xc, kf, kc) of a
+        fixed-count problem in the batched form, with the per-pair results of
+        estimator level `level`."""
+        import torch
+        dev = "cuda:%d" % self.device
+        n = int(problem.n_fixed[level])
+        xf = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+        xc = torch.empty(max(n, 1), dtype=torch.float64, device=dev)
+        kf = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        kc = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        r = Result()
+        d = None
+        if problem.nbins > 0:
+            d = np.zeros(problem.nbins, np.float64)
+            r.density = d.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        vp = ctypes.c_void_p
+        _check(lib().mlkd_debug_batch_pairs(self.handle, ctypes.byref(problem), ctypes.byref(cfg), level,
+                                            _stream_handle(stream), ctypes.byref(r), vp(xf.data_ptr()),
+                                            vp(xc.data_ptr()), vp(kf.data_ptr()), vp(kc.data_ptr())),
+               "mlkd_debug_batch_pairs")
+        nl = r.n_levels
+        er = EstimateResult(r.estimate, r.variance, r.rounds, [r.lv[l].as_dict() for l in range(nl)],
+                            [r.var_level[l] for l in range(nl)], [r.cost_level[l] for l in range(nl)],
+                            d, r.seconds)
+        return (er, xf[:n].cpu().numpy(), xc[:n].cpu().numpy(),
+                kf[:n].cpu().numpy().astype(np.int64), kc[:n].cpu().numpy().astype(np.int64))
 
     def autotune_batch(self, problems, base: BatchConfig, stream=None):
         n = len(problems)

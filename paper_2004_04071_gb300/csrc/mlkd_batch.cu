@@ -136,7 +136,12 @@ struct BatchLaunch {
     int32_t n_slots;
     int32_t refill_min;          // idle lanes a warp gathers before it restarts them together
     int32_t publish_spins;       // bound of the publication wait
+    int32_t dbg_req;             // per-pair readout of request slot dbg_req, estimator level
+    int32_t dbg_level;           // dbg_level (-1: none)
     int32_t pad_;
+    unsigned long long dbg_n;    // entries of the readout arrays
+    double *dbg_xf, *dbg_xc;
+    int32_t *dbg_kf, *dbg_kc;
     PhiloxKeys keys;
 };
 
@@ -597,6 +602,16 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                 if (bc >= 0 && bc == bf) atomicAdd(&wh[2 * nbins + bf], 1u);
             }
         }
+        if (B.dbg_xf && ch.req == B.dbg_req && ch.level == B.dbg_level) {
+            // validation readout: this pair's final state, by its pair index
+            const unsigned long long p = ((unsigned long long)(st[j].word2 ^ L.word2) << 32) | st[j].pair_lo;
+            if (p < B.dbg_n) {
+                B.dbg_xf[p] = (double)st[j].xf;
+                B.dbg_xc[p] = coupled ? (double)st[j].xc : 0.0;
+                B.dbg_kf[p] = (int32_t)st[j].k;
+                B.dbg_kc[p] = (int32_t)st[j].evc;
+            }
+        }
         done[j] = false;
     };
 
@@ -989,6 +1004,8 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->slice_iters = cfg->substeps_per_launch;
     B->refill_min = cfg->refill_min > 0 ? cfg->refill_min : kRefillMin;
     B->publish_spins = cfg->publish_wait_spins > 0 ? cfg->publish_wait_spins : kPublishSpins;
+    B->dbg_req = -1;
+    B->dbg_level = -1;
     B->n_slots = n_slots;
     fill_keys(seed, &B->keys);
 }
@@ -1040,8 +1057,17 @@ static mlkd_status batch_grid(mlkd_context *ctx, int mode, int ppt, int max_nbin
     return MLKD_OK;
 }
 
+// Per-pair readout of one (request, estimator level) of a batched run.
+struct BatchDebug {
+    int req, level;
+    unsigned long long n;
+    double *xf, *xc;
+    int32_t *kf, *kc;
+};
+
 static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
-                             const mlkd_batch_config *cfg, cudaStream_t s, mlkd_result *results)
+                             const mlkd_batch_config *cfg, cudaStream_t s, mlkd_result *results,
+                             const BatchDebug *dbg = nullptr)
 {
     if (!ctx || !problems || n < 1 || !results || !batch_cfg_ok(cfg)) return MLKD_EINVAL;
     if (ctx->server) return MLKD_EBUSY;
@@ -1086,6 +1112,16 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
 
     BatchLaunch B;
     make_launch(ctx, BL, cfg, n, seed, &B);
+    if (dbg) {
+        B.dbg_req = dbg->req;
+        B.dbg_level = dbg->level;
+        B.dbg_n = dbg->n;
+        B.dbg_xf = dbg->xf;
+        B.dbg_xc = dbg->xc;
+        B.dbg_kf = dbg->kf;
+        B.dbg_kc = dbg->kc;
+        batch_release(ctx);          // a graph with the readout is not kept for later calls
+    }
     int grid = 0;
     mlkd_status st = batch_grid(ctx, mode, ppt, cfg->max_nbins, &grid);
     if (st != MLKD_OK) return st;
@@ -1137,6 +1173,10 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
             bc->stream = s;
         }
         MLKD_CUDA(cudaGraphLaunch(bc->exec, s));
+        if (dbg) {
+            MLKD_CUDA(cudaStreamSynchronize(s));
+            batch_release(ctx);
+        }
     } else {
         for (int it = 0; it < 1000000; ++it) {
             st = enqueue_body(ctx, B, mode, ppt, grid, 0, 0, live_dev, s);
@@ -1524,6 +1564,20 @@ mlkd_status mlkd_estimate_batch(mlkd_context *ctx, const mlkd_problem *problems,
                                 const mlkd_batch_config *cfg, void *stream, mlkd_result *results)
 {
     return run_batch(ctx, problems, n, cfg, (cudaStream_t)stream, results);
+}
+
+mlkd_status mlkd_debug_batch_pairs(mlkd_context *ctx, const mlkd_problem *problem,
+                                   const mlkd_batch_config *cfg, int level, void *stream,
+                                   mlkd_result *result, double *xf, double *xc, int32_t *kf,
+                                   int32_t *kc)
+{
+    if (!problem || !problem->n_fixed || !xf || !xc || !kf || !kc || level < 0) return MLKD_EINVAL;
+    Derived d;
+    if (!validate(problem, &d) || level >= d.J) return MLKD_EINVAL;
+    const long long nl = problem->n_fixed[level];
+    if (nl < 0) return MLKD_EINVAL;
+    BatchDebug dbg{0, level, (unsigned long long)nl, xf, xc, kf, kc};
+    return run_batch(ctx, problem, 1, cfg, (cudaStream_t)stream, result, &dbg);
 }
 
 mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,

@@ -567,6 +567,27 @@ mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int
     return harvest_timing(ctx);
 }
 
+mlkd_status mlkd_debug_coarse_draws(mlkd_context *ctx, const mlkd_problem *problem, int level,
+                                    uint64_t first_pair, uint64_t n_pairs, int per_pair,
+                                    void *stream, double *nu_t, double *E_t, double *chi_t,
+                                    int32_t *count)
+{
+    Derived d;
+    if (!ctx || !validate(problem, &d)) return MLKD_EINVAL;
+    if (level < 1 || level >= d.J || per_pair < 1) return MLKD_EINVAL;
+    if (!nu_t || !E_t || !chi_t || !count) return MLKD_EINVAL;
+    if (n_pairs > (1ull << 31) / (unsigned long long)per_pair) return MLKD_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    MLKD_CUDA(cudaSetDevice(ctx->device));
+    if (n_pairs == 0) return MLKD_OK;
+    PairLaunch P;
+    fill_launch(problem, d, level, first_pair, n_pairs, &P);
+    MLKD_CUDA(launch_coarse_draws(d.mode, P, per_pair, nu_t, E_t, chi_t, count, s));
+    ctx->other_launches += 1;
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    return MLKD_OK;
+}
+
 }  // extern "C"
 
 // Adaptive MLMC (Sec. 4.1) with an optional starting state and a round limit.

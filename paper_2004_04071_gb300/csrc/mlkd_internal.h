@@ -90,6 +90,11 @@ cudaError_t launch_controller(const DevLevelStats *acc, const unsigned long long
                               int n_levels, int nbins, double h, int density_qoi, double tol,
                               DevControl *out, cudaStream_t stream);
 
+// Coarse random numbers (nu~, E~, chi~) of the first per_pair coarse steps of
+// each pair of a coupled level (validation); count[j] = coarse steps of pair j.
+cudaError_t launch_coarse_draws(int mode, const PairLaunch &p, int per_pair, double *nu, double *E,
+                                double *chi, int32_t *count, cudaStream_t stream);
+
 // FP32 variate transforms of n words (validation).
 cudaError_t launch_debug_transforms(const uint32_t *words, unsigned long long n, float *log_u,
                                     float *sn, float *cs, cudaStream_t stream);

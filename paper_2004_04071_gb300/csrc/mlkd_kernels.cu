@@ -219,6 +219,78 @@ finalize_kernel(const double *__restrict__ partials, int nblocks, long long n_pa
     }
 }
 
+// ---------------------------------------------------------------------------
+// Coarse random numbers of each pair (validation of Sec. 5.1): one thread
+// per pair runs the same pair_start/pair_event as the pair kernel and
+// records the first per_pair coarse steps' (nu~, E~, chi~).
+// ---------------------------------------------------------------------------
+struct CoarseTrace {
+    double *nu, *E, *chi;
+    int cap, n;
+    template <typename Real> __device__ void coarse(Real a, Real b, Real c)
+    {
+        if (n < cap) {
+            nu[n] = (double)a;
+            E[n] = (double)b;
+            chi[n] = (double)c;
+        }
+        ++n;
+    }
+};
+
+template <typename Real, int MODE>
+__global__ void __launch_bounds__(kThreads)
+coarse_draws_kernel(const __grid_constant__ PairLaunch P, int per_pair, double *nu, double *E,
+                    double *chi, int32_t *count)
+{
+    const unsigned long long j = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P.n_pairs) return;
+    const BgParams<Real> &bp = level_params<Real>(P);
+    LevelCtx<Real> L;
+    L.bg.R = bp.R;
+    L.bg.invR = bp.invR;
+    L.bg.mu = bp.mu;
+    L.bg.sigma = bp.sigma;
+    L.bg.two_c2 = bp.two_c2;
+    L.bg.dt = bp.dt;
+    L.bg.Rdt = bp.Rdt;
+    L.bg.inv_Rdt = bp.inv_Rdt;
+    L.n = P.n;
+    L.M = P.M;
+    L.m_shift = (P.M & (P.M - 1)) == 0 ? __ffs(P.M) - 1 : -1;
+    L.init = P.init;
+    L.word2 = P.word2;
+    L.request = P.request;
+    const size_t base = (size_t)j * (size_t)per_pair;
+    CoarseTrace tr{nu + base, E + base, chi + base, per_pair, 0};
+    PairState<Real> st;
+    st.fresh = true;
+    bool done = pair_start<Real, 1, ModeRecipe<MODE>::value>(st, P.first_pair + j, L, P.keys, true);
+    // a pair has at most n fine events
+    for (int it = 0; !done && it <= P.n; ++it)
+        done = pair_event<Real, 1, ModeRecipe<MODE>::value, CoarseTrace>(st, L, P.keys, true, &tr);
+    count[j] = tr.n;
+}
+
+cudaError_t launch_coarse_draws(int mode, const PairLaunch &p, int per_pair, double *nu, double *E,
+                                double *chi, int32_t *count, cudaStream_t stream)
+{
+    if (p.n_pairs == 0) return cudaSuccess;
+    const unsigned long long blocks = (p.n_pairs + kThreads - 1) / kThreads;
+    switch (mode) {
+    case kModeFP64:
+        coarse_draws_kernel<double, kModeFP64><<<(unsigned)blocks, kThreads, 0, stream>>>(p, per_pair, nu, E, chi, count);
+        break;
+    case kModeFP64U24:
+        coarse_draws_kernel<double, kModeFP64U24><<<(unsigned)blocks, kThreads, 0, stream>>>(p, per_pair, nu, E, chi, count);
+        break;
+    default:
+        coarse_draws_kernel<float, kModeFP32Comp><<<(unsigned)blocks, kThreads, 0, stream>>>(p, per_pair, nu, E, chi, count);
+        break;
+    }
+    return cudaGetLastError();
+}
+
 __global__ void debug_transforms_kernel(const uint32_t *words, unsigned long long n, float *log_u,
                                         float *sn, float *cs)
 {

@@ -13,9 +13,16 @@
 // so the coarse collision equals the fine collision kappa_k exactly.
 #pragma once
 
+#include <type_traits>
+
 #include "mlkd_internal.h"
 
 namespace mlkd {
+
+// Observer of the coarse steps (validation only): pair_event calls
+// tr->coarse(nu~, E~, chi~) at each coarse KD step when a tracer is given.
+// NoTrace compiles to nothing.
+struct NoTrace {};
 
 template <typename Real> struct PairState {
     Real xf, vf, qf;            // fine path: position, velocity, flight (fine units)
@@ -82,9 +89,10 @@ __device__ __forceinline__ bool pair_start(PairState<Real> &st, unsigned long lo
 }
 
 // One fine event; returns true when the pair has reached T.
-template <typename Real, int CPL, int RECIPE = 0>
+template <typename Real, int CPL, int RECIPE = 0, typename Trace = NoTrace>
 __device__ __forceinline__ bool pair_event(PairState<Real> &st, const LevelCtx<Real> &L,
-                                           const PhiloxKeys &keys, bool coupled_rt)
+                                           const PhiloxKeys &keys, bool coupled_rt,
+                                           Trace *tr = nullptr)
 {
     typedef Arith<Real> A;
     const bool coupled = pair_is_coupled<Real, CPL>(coupled_rt);
@@ -126,6 +134,8 @@ __device__ __forceinline__ bool pair_event(PairState<Real> &st, const LevelCtx<R
             const Real chit = st.den > Real(0) ? st.num * A::rsqrt_(st.den) : st.chi_first;
             st.xc = st.xc + st.vc * (st.qc * bg.dt) + (ac + dc * chit);
             st.qc = st.qf - (Real)(st.Ec - st.i_f);
+            if constexpr (!std::is_same<Trace, NoTrace>::value)
+                tr->coarse(d.nu, st.qc * bg.Rdt, chit);      // nu~, E~ = R tau~, chi~
             st.ic = st.Ec;
             st.vc = v1;
             ++st.evc;

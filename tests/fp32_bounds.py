@@ -140,6 +140,12 @@ def edge_allowance(x, d, lo, hi, nbins, periodic):
     return allow, int(np.count_nonzero(near))
 
 
+def fp32_mod1(x64):
+    """x - floor(x) of FP32 positions, rounded to FP32 as the kernel does."""
+    x = np.asarray(x64, np.float64).astype(np.float32)
+    return (x - np.floor(x)).astype(np.float32).astype(np.float64)
+
+
 def fp32_bins(x64, lo, hi, nbins, periodic):
     """The kernel's FP32 bin decision for FP32 positions (exact replica:
     wrap x - floor(x), the range test, floor((x - lo) * (1/h)) and the top
@@ -161,13 +167,18 @@ def host_level_sums(periodic, coupled, xf, xc, precision):
     FP32 formation of each term can lie from this FP64 formation."""
     xf = np.asarray(xf, np.float64)
     xc = np.asarray(xc, np.float64) if coupled else np.zeros_like(xf)
-    Ff = qoi(periodic, xf)
-    Fc = qoi(periodic, xc) if coupled else np.zeros_like(Ff)
-    if periodic or not coupled:
+    if periodic:
+        # x mod 1 exactly as the kernel forms it: x - floor(x) rounded to FP32
+        mf = fp32_mod1(xf)
+        mc = fp32_mod1(xc) if coupled else np.zeros_like(mf)
+        Ff, Fc = mf * mf, mc * mc
         Y = Ff - Fc
     else:
-        Y = (xf - xc) * (xf + xc)
-    rf = 4.0 * U32 * np.maximum(1.0, Ff)       # F in FP32, x mod 1 in FP32
+        Ff, Fc = xf * xf, xc * xc
+        Y = Ff - Fc if not coupled else (xf - xc) * (xf + xc)
+    if not coupled:
+        Fc = np.zeros_like(Ff)
+    rf = 4.0 * U32 * np.maximum(1.0, Ff)       # F formed in FP32
     rc = 4.0 * U32 * np.maximum(1.0, Fc) if coupled else np.zeros_like(Fc)
     ry = (rf + rc + 4.0 * U32 * np.abs(Y)) if precision == 2 else 4.0 * U64 * (Ff + Fc + np.abs(Y))
     sums = {"sy": Y, "sy2": Y * Y, "sqf": Ff, "sqf2": Ff * Ff, "sqc": Fc, "sqc2": Fc * Fc}

@@ -96,57 +96,42 @@ def _oracle_hist(orc, po, level, xf, xc):
     return hf, hc, np.bincount(bf[same], minlength=nb)
 
 
-@pytest.mark.parametrize("precision", [1, 2])
-@pytest.mark.parametrize("level", [0, 8])
-def test_fp32_level_sums_and_histograms_against_oracle(orc, mk, ctx, level, precision):
-    """The FP32 modes' level sums and histograms of the per-level form against
-    the oracle on the same 24-bit stream, on the benchmark's periodic problem
-    at eps = 0.1 (level 8: its busiest coupled level; level 0: single paths),
-    2^17 pairs.
-
-    1. Reduction: the kernel's sums against the FP64 sums of its own per-pair
-       QoIs (the same kernel's per-pair output), within the compensated-sum
-       bound; its histograms against the FP32 bin decisions of those
-       positions, exactly.
-    2. Oracle: each sum within the bound that the per-pair bound implies
-       (tests/fp32_bounds.py); each histogram bin within the count of pairs
-       whose oracle position lies within the per-pair bound of that bin's
-       edges.  Pairs whose event sequence differs (none expected) enter with
-       their actual difference."""
-    d = W.periodic_problem(0.1)
-    first, n = 12345, 1 << 17
+def _check_level(orc, po, level, n, sg, pairs_g, pairs_o, precision, what):
+    """Checks one level's FP32 sums (and histograms, if sg has them) against
+    (1) the FP64 sums of the same kernel's per-pair output, within the
+    compensated-sum bound, and exact FP32 bin decisions of those positions;
+    (2) the oracle on the same 24-bit stream, within the bounds the per-pair
+    bound implies (tests/fp32_bounds.py).  Returns the per-bin density
+    allowance of this level against the oracle, in counts."""
+    xf_g, xc_g, kf_g, kc_g = pairs_g
+    xf_o, xc_o, kf_o, kc_o = pairs_o
     coupled = level > 0
-    pg = gpu_problem(mk, d, precision=precision)
-    po = oracle_problem(orc, d, recipe=orc.RECIPE_24)
-    xf_o, xc_o, kf_o, kc_o = orc.pairs(po, level, first, n, threads=16)
     so = orc.level_sums(po, level, xf_o, xc_o, kf_o, kc_o)
-    sg = ctx.run_level(pg, level, first, n)
-    xf_g, xc_g, kf_g, kc_g = ctx.debug_pairs(pg, level, first, n)
-
-    # counts
     assert sg["n"] == n
     assert sg["events_f"] == int(kf_g.sum()) and sg["events_c"] == int(kc_g.sum())
     same = (kf_g == kf_o) & (kc_g == kc_o)
     flips = int(n - same.sum())
-    assert flips <= MAX_FLIP_FRACTION * n
+    assert flips <= MAX_FLIP_FRACTION * n, (what, level, flips)
     if flips == 0:
         assert sg["events_f"] == so.events_f and sg["events_c"] == so.events_c
 
-    # 1. reduction of the kernel's own pairs
+    # 1. the reduction of the kernel's own pairs
     host, form, terms = B.host_level_sums(True, coupled, xf_g, xc_g, precision)
     for k in SUM_KEYS:
         comp = precision == 2 or k not in ("sy", "sy2")
         tol = form[k] + B.sum_error(terms[k], comp, n)
-        assert abs(sg[k] - host[k]) <= tol, (k, sg[k], host[k], tol)
-    lo, hi, nb = 0.0, 1.0, pg.nbins
+        assert abs(sg[k] - host[k]) <= tol, (what, level, k, sg[k], host[k], tol)
+    lo, hi, nb = 0.0, 1.0, po.nbins
     bf = B.fp32_bins(xf_g, lo, hi, nb, True)
-    hf = np.bincount(bf[bf >= 0], minlength=nb)
-    assert np.array_equal(sg["hist_f"], hf)
+    hg = [np.bincount(bf[bf >= 0], minlength=nb), np.zeros(nb, np.int64), np.zeros(nb, np.int64)]
     if coupled:
         bc = B.fp32_bins(xc_g, lo, hi, nb, True)
-        assert np.array_equal(sg["hist_c"], np.bincount(bc[bc >= 0], minlength=nb))
         both = (bf == bc) & (bf >= 0)
-        assert np.array_equal(sg["hist_both"], np.bincount(bf[both], minlength=nb))
+        hg[1] = np.bincount(bc[bc >= 0], minlength=nb)
+        hg[2] = np.bincount(bf[both], minlength=nb)
+    if "hist_f" in sg:
+        for got, want in zip((sg["hist_f"], sg["hist_c"], sg["hist_both"]), hg):
+            assert np.array_equal(got, want), (what, level)
 
     # 2. against the oracle
     bound = B.level_sum_bounds(True, coupled, xf_o[same], xc_o[same], kf_o[same], kc_o[same],
@@ -158,72 +143,95 @@ def test_fp32_level_sums_and_histograms_against_oracle(orc, mk, ctx, level, prec
             bound[k] += float(np.sum(np.abs(tg[k] - to[k]))) * (1 + 1e-6) + 1e-9
     for k in SUM_KEYS:
         err = abs(sg[k] - getattr(so, k))
-        print("level %d prec %d %s: |gpu - oracle| = %.3e, derived bound %.3e"
-              % (level, precision, k, err, bound[k]))
-        assert err <= bound[k], (k, err, bound[k])
+        print("%s level %d prec %d %s: |gpu - oracle| = %.3e, derived bound %.3e"
+              % (what, level, precision, k, err, bound[k]))
+        assert err <= bound[k], (what, level, k, err, bound[k])
     ev = kf_o + kc_o
-    ho = _oracle_hist(orc, po, level, xf_o, xc_o)
-    af, nf = B.edge_allowance(xf_o, B.pair_delta(xf_o, ev), lo, hi, nb, True)
-    ac, nc = (B.edge_allowance(xc_o, B.pair_delta(xc_o, ev), lo, hi, nb, True) if coupled
-              else (np.zeros(nb, np.int64), 0))
-    print("level %d prec %d: positions near a bin edge %d (fine) %d (coarse) of %d pairs"
-          % (level, precision, nf, nc, n))
-    if flips:
-        extra = np.zeros(nb, np.int64)
-        for x in (xf_o[~same], xf_g[~same], xc_o[~same], xc_g[~same]):
-            b = B.fp32_bins(x, lo, hi, nb, True)
-            np.add.at(extra, b[b >= 0], 1)
-        af, ac = af + extra, ac + extra
-    assert np.all(np.abs(sg["hist_f"].astype(np.int64) - ho[0]) <= af)
-    assert np.all(np.abs(sg["hist_c"].astype(np.int64) - ho[1]) <= ac)
-    assert np.all(np.abs(sg["hist_both"].astype(np.int64) - ho[2]) <= af + ac)
+    af, nf = B.edge_allowance(xf_o[same], B.pair_delta(xf_o[same], ev[same]), lo, hi, nb, True)
+    ac, nc = (B.edge_allowance(xc_o[same], B.pair_delta(xc_o[same], ev[same]), lo, hi, nb, True)
+              if coupled else (np.zeros(nb, np.int64), 0))
+    print("%s level %d prec %d: %d flipped pairs; positions near a bin edge %d (fine) %d (coarse) "
+          "of %d pairs" % (what, level, precision, flips, nf, nc, n))
+    for x in (xf_o[~same], xf_g[~same], xc_o[~same], xc_g[~same]):
+        b = B.fp32_bins(x, lo, hi, nb, True)
+        np.add.at(af, b[b >= 0], 1)
+        np.add.at(ac, b[b >= 0], 1)
+    ho = (so.hist_f, so.hist_c, so.hist_both)
+    assert np.all(np.abs(hg[0] - ho[0]) <= af), (what, level)
+    assert np.all(np.abs(hg[1] - ho[1]) <= ac), (what, level)
+    assert np.all(np.abs(hg[2] - ho[2]) <= af + ac), (what, level)
+    return af + ac, hg
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("level", [0, 8])
+def test_fp32_level_sums_and_histograms_against_oracle(orc, mk, ctx, level, precision):
+    """The FP32 modes' level sums and histograms of the per-level form against
+    the oracle on the same 24-bit stream, on the benchmark's periodic problem
+    at eps = 0.1 (level 8: its busiest coupled level; level 0: single paths),
+    2^17 pairs.  The per-pair output of the same kernel (mlkd_debug_pairs)
+    gives the positions that feed the sums and histograms:
+
+    1. Reduction: the kernel's sums against the FP64 sums of its own per-pair
+       QoIs, within the compensated-sum bound; its histograms against the
+       FP32 bin decisions of those positions, exactly.
+    2. Oracle: each sum within the bound that the per-pair bound implies;
+       each histogram bin within the count of pairs whose oracle position
+       lies within the per-pair bound of that bin's edges.  Pairs whose event
+       sequence differs (at most 1e-3 of them) enter with their actual
+       difference."""
+    d = W.periodic_problem(0.1)
+    first, n = 12345, 1 << 17
+    pg = gpu_problem(mk, d, precision=precision)
+    po = oracle_problem(orc, d, recipe=orc.RECIPE_24)
+    pairs_o = orc.pairs(po, level, first, n, threads=16)
+    sg = ctx.run_level(pg, level, first, n)
+    pairs_g = ctx.debug_pairs(pg, level, first, n)
+    _check_level(orc, po, level, n, sg, pairs_g, pairs_o, precision, "per-level")
 
 
 @pytest.mark.parametrize("precision", [1, 2])
 def test_fp32_batched_step_against_oracle(orc, mk, precision):
-    """The benchmark's batched form and configuration (one pair per lane,
+    """The benchmark's batched kernel in its configuration (one pair per lane,
     unbounded slices, the CUDA graph, 128 bins) on the periodic problem at
-    eps = 0.1 with fixed N_l (2^17 pairs on level 8, one round, 2*10^4 on the
-    others): every level's pair and event counts exactly, its six sums within
-    the bound implied by the per-pair bound, and the density within the
-    edge-count allowance of every level, all against the oracle on the same
-    24-bit stream."""
+    eps = 0.1 with fixed N_l (2^17 pairs on level 8, one round; 2*10^4 on the
+    others).  For every level the batched kernel's own per-pair output
+    (mlkd_debug_batch_pairs) is checked as in the per-level test: its sums
+    against the FP64 sums of its pairs and, with its histograms, against the
+    oracle on the same 24-bit stream; the density against both."""
     d = dict(W.periodic_problem(0.1), tol=0.0)
     L = d["L"]
     n_fixed = [20000] * L + [1 << 17]
     cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=0, use_graph=1,
                           max_requests=16, max_nbins=128)
+    po = oracle_problem(orc, d, recipe=orc.RECIPE_24)
+    p = gpu_problem(mk, d, precision=precision, n_fixed=n_fixed)
+    nb, h = d["nbins"], 1.0 / d["nbins"]
     c = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
     try:
-        (rb,) = c.estimate_batch([gpu_problem(mk, d, precision=precision, n_fixed=n_fixed)], cfg)
+        ref = c.estimate_batch([p], cfg)[0]
+        dens_host = np.zeros(nb)
+        dens_o = np.zeros(nb)
+        allow = np.zeros(nb)
+        for level in range(L + 1):
+            n = n_fixed[level]
+            r, *pairs_g = c.debug_batch_pairs(p, cfg, level)
+            # the readout run is the benchmarked computation: same result
+            assert r.estimate == ref.estimate and np.array_equal(r.density, ref.density)
+            pairs_o = orc.pairs(po, level, 0, n, threads=16)
+            a, hg = _check_level(orc, po, level, n, r.levels[level], tuple(pairs_g), pairs_o,
+                                 precision, "batched")
+            so = orc.level_sums(po, level, *pairs_o)
+            dens_host += (hg[0] - hg[1]) / n / h
+            dens_o += (so.hist_f - so.hist_c) / n / h
+            allow += a / n / h
     finally:
         c.close()
-    po = oracle_problem(orc, d, recipe=orc.RECIPE_24)
-    nb, lo, hi = d["nbins"], 0.0, 1.0
-    h = (hi - lo) / nb
-    dens_o = np.zeros(nb)
-    dens_allow = np.zeros(nb)
-    for level in range(L + 1):
-        n = n_fixed[level]
-        xf, xc, kf, kc = orc.pairs(po, level, 0, n, threads=16)
-        so = orc.level_sums(po, level, xf, xc, kf, kc)
-        lg = rb.levels[level]
-        assert lg["n"] == n
-        assert lg["events_f"] == so.events_f and lg["events_c"] == so.events_c, level
-        bound = B.level_sum_bounds(True, level > 0, xf, xc, kf, kc, precision)
-        for k in SUM_KEYS:
-            err = abs(lg[k] - getattr(so, k))
-            assert err <= bound[k], (level, k, err, bound[k])
-        ev = kf + kc
-        af, _ = B.edge_allowance(xf, B.pair_delta(xf, ev), lo, hi, nb, True)
-        ac, _ = (B.edge_allowance(xc, B.pair_delta(xc, ev), lo, hi, nb, True) if level
-                 else (np.zeros(nb, np.int64), 0))
-        dens_o += (so.hist_f - so.hist_c) / n / h
-        dens_allow += (af + ac) / n / h
-    err = np.abs(rb.density - dens_o)
+    assert np.allclose(ref.density, dens_host, rtol=1e-12, atol=1e-12)
+    err = np.abs(ref.density - dens_o)
     print("prec %d: density |gpu - oracle| max %.3e, allowance min %.3e"
-          % (precision, err.max(), dens_allow.min()))
-    assert np.all(err <= dens_allow + 1e-12 * np.abs(dens_o) + 1e-15)
+          % (precision, err.max(), allow.min()))
+    assert np.all(err <= allow + 1e-12 * np.abs(dens_o) + 1e-15)
 
 
 def test_fp32_full_launch_sampled(orc, mk, ctx):

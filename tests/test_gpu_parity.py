@@ -48,6 +48,12 @@ REGIMES = {
     # found by division instead of a shift
     "M3": dict(eps=0.2, T=0.6, dt0=0.2, M=3, L=2, qoi=0, init=0, nbins=12, lo=-3.0, hi=3.0, seed=17),
     "M6_diffusive": dict(eps=0.05, T=1.0, dt0=0.5, M=6, L=2, qoi=1, init=1, nbins=0, seed=19),
+    # the large refinement factors of the Sec. 5.1 sweep: windows of up to 64
+    # fine steps per coarse step
+    "M16": dict(eps=0.05, T=1.0, dt0=0.5, M=16, L=2, qoi=0, init=0, nbins=0, seed=29),
+    "M32_periodic": dict(eps=0.1, T=1.0, dt0=1.0, M=32, L=2, qoi=1, init=1, nbins=32, lo=0.0,
+                         hi=1.0, seed=31),
+    "M64": dict(eps=0.02, T=0.5, dt0=0.5, M=64, L=2, qoi=0, init=0, nbins=0, seed=37),
 }
 
 

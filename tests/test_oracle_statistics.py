@@ -19,11 +19,13 @@
   until that point and is flat beyond it.
 """
 import math
+import os
 
 import numpy as np
 import pytest
 from scipy import stats
 
+from ad_test import ad_pvalue, ad_statistic
 from helpers import check_level_curve, level_curve
 
 
@@ -31,14 +33,24 @@ def msd(eps, T, mu=0.0):
     return mu * mu * T * T + 2.0 * (T - eps * eps * (1.0 - math.exp(-T / (eps * eps))))
 
 
-def ad_statistic(x, cdf):
-    """Anderson-Darling A^2 of a sample against a fully specified CDF
-    (eq. anderson, Sec. 5.1)."""
-    x = np.sort(np.asarray(x))
-    n = x.size
-    F = np.clip(cdf(x), 1e-300, 1 - 1e-16)
-    i = np.arange(1, n + 1)
-    return -n - np.sum((2 * i - 1) / n * (np.log(F) + np.log1p(-F[::-1])))
+def test_ad_pvalues_reproduce_the_papers_table():
+    """The AD p-value of tests/ad_test.py against (A^2, p) pairs printed in
+    Table hypothesis (Sec. 5.1), to the printed three decimals; and the
+    classic asymptotic percentage points 1.933 (10 %), 2.492 (5 %)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "ad_table_hypothesis.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) >= 8
+    for level, M, var, a2, p in rows:
+        assert abs(ad_pvalue(float(a2)) - float(p)) <= 1.5e-3, (level, M, var, a2, p)
+    assert abs(ad_pvalue(1.933) - 0.10) < 2e-4
+    assert abs(ad_pvalue(2.492) - 0.05) < 2e-4
+    # the statistic itself: a sample at the quantiles (i - 1/2)/N of its own
+    # law is nearly perfect (A^2 of order 1/N); the same sample shifted by
+    # 0.2 is rejected outright
+    N = 1000
+    x = stats.norm.ppf((np.arange(1, N + 1) - 0.5) / N)
+    assert 0.0 < ad_statistic(x, stats.norm.cdf) < 2.0 / N
+    assert ad_pvalue(ad_statistic(x + 0.2, stats.norm.cdf)) < 1e-4
 
 
 # Asymptotic critical values of A^2 for a fully specified law: 1 % -> 3.857,
