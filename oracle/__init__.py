@@ -101,8 +101,29 @@ def lib():
             L.orc_coarse_draws.restype = i64
             L.orc_stream_draws.argtypes = [P(LevelDesc), u64, i64, P(d), P(d), P(d), P(d)]
             L.orc_stream_draws.restype = None
+            L.orc_het_R.argtypes = [P(HetBg), d]
+            L.orc_het_R.restype = d
+            L.orc_het_depth.argtypes = [P(HetBg), d, d, d, d]
+            L.orc_het_depth.restype = d
+            L.orc_het_flight.argtypes = [P(HetBg), d, d, d, d]
+            L.orc_het_flight.restype = d
+            L.orc_het_pairs.argtypes = [P(HetDesc), u64, i64, P(d), P(d), P(i64), P(i64)]
+            L.orc_het_pairs.restype = ctypes.c_int
+            L.orc_het_coarse_draws.argtypes = [P(HetDesc), u64, i64, i64, P(d), P(d), P(d)]
+            L.orc_het_coarse_draws.restype = i64
             _lib = L
     return _lib
+
+
+class HetBg(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_double), ("a_left", ctypes.c_double), ("a_right", ctypes.c_double)]
+
+
+class HetDesc(ctypes.Structure):
+    _fields_ = [("bg", HetBg), ("dt", ctypes.c_double), ("n", ctypes.c_int64), ("M", ctypes.c_int32),
+                ("level", ctypes.c_int32), ("recipe", ctypes.c_int32), ("coupled", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("request", ctypes.c_uint32), ("pad_", ctypes.c_int32),
+                ("x0", ctypes.c_double)]
 
 
 def _ptr(a, ctype):
@@ -625,3 +646,101 @@ def estimate(problem: Problem, threads: int = 1, max_rounds: int = 64) -> MLMCRe
             if not grew:
                 break
     return _result(problem, sums)
+
+
+# --------------------------------------------------------------------------
+# Heterogeneous backgrounds B1/B2 (Sec. 5): mu = 0, sigma = 1, piecewise-linear
+# R(x) = b (1 + a_left max(1 - x, 0) + a_right max(x - 1, 0)); B1 has
+# a_left = a_right = a, B2 a_left = 0, a_right = a.  Levels dt_l = dt0 M^-l.
+# --------------------------------------------------------------------------
+BG_B1, BG_B2 = 1, 2
+
+
+def het_bg(kind: int, a: float, b: float) -> HetBg:
+    return HetBg(b, a if kind == BG_B1 else 0.0, a)
+
+
+def het_R(bg: HetBg, x: float) -> float:
+    return lib().orc_het_R(ctypes.byref(bg), x)
+
+
+def het_depth(bg: HetBg, x0: float, v: float, dt: float, u: float) -> float:
+    """int_0^u R(x0 + v dt w) dt dw (steps u; negative u: the segment behind)."""
+    return lib().orc_het_depth(ctypes.byref(bg), x0, v, dt, u)
+
+
+def het_flight(bg: HetBg, x0: float, v: float, dt: float, E: float) -> float:
+    """Flight in steps from x0 at velocity v that collects optical depth E (eq. intinv)."""
+    return lib().orc_het_flight(ctypes.byref(bg), x0, v, dt, E)
+
+
+def _het_desc(kind, a, b, T, dt0, M, level, coupled, x0, seed, request, recipe, coarsening):
+    r = T / dt0
+    n0 = int(round(r))
+    if n0 < 1 or abs(r - n0) > 1e-12 * max(1.0, r):
+        raise ValueError("T/dt0 must be a positive integer")
+    d = HetDesc()
+    d.bg = het_bg(kind, a, b)
+    d.dt = dt0 / float(M) ** level
+    d.n = n0 * M ** level
+    d.M = coarsening if coarsening else M
+    d.level, d.recipe, d.coupled = level, recipe, 1 if coupled else 0
+    d.seed, d.request, d.x0 = seed, request, x0
+    return d
+
+
+def het_coarse_draws(kind, a, b, T, dt0, M, level, first, count, cap, x0=1.0, seed=0, request=0,
+                     coarsening=None):
+    """(nu~, E~, chi~) of every coarse step of heterogeneous pairs, in order;
+    the coarse step is dt * coarsening (default M)."""
+    d = _het_desc(kind, a, b, T, dt0, M, level, True, x0, seed, request, RECIPE_53, coarsening)
+    nu, E, chi = np.zeros(cap), np.zeros(cap), np.zeros(cap)
+    dd = ctypes.c_double
+    w = lib().orc_het_coarse_draws(ctypes.byref(d), first, count, cap, _ptr(nu, dd), _ptr(E, dd),
+                                   _ptr(chi, dd))
+    if w < 0:
+        raise RuntimeError("oracle heterogeneous coarse draws failed")
+    return nu[:w], E[:w], chi[:w]
+
+
+def het_pairs(kind, a, b, T, dt0, M, level, coupled, first, count, x0=1.0, seed=0, request=0,
+              recipe=RECIPE_53, coarsening=None, threads=1):
+    """Final positions and event counts of pairs [first, first + count) of
+    fine level `level` (dt = dt0 M^-level) in background B1/B2; coupled pairs
+    couple with the step dt * coarsening (default M)."""
+    r = T / dt0
+    n0 = int(round(r))
+    if n0 < 1 or abs(r - n0) > 1e-12 * max(1.0, r):
+        raise ValueError("T/dt0 must be a positive integer")
+    d = HetDesc()
+    d.bg = het_bg(kind, a, b)
+    d.dt = dt0 / float(M) ** level
+    d.n = n0 * M ** level
+    d.M = coarsening if coarsening else M
+    d.level, d.recipe, d.coupled = level, recipe, 1 if coupled else 0
+    d.seed, d.request, d.x0 = seed, request, x0
+    xf, xc = np.zeros(count), np.zeros(count)
+    ef, ec = np.zeros(count, np.int64), np.zeros(count, np.int64)
+    L = lib()
+    threads = max(1, min(int(threads), count if count > 0 else 1))
+    bounds = np.linspace(0, count, threads + 1).astype(np.int64)
+
+    def work(t):
+        lo, hi = int(bounds[t]), int(bounds[t + 1])
+        if hi <= lo:
+            return 0
+        dd, i64 = ctypes.c_double, ctypes.c_int64
+        return L.orc_het_pairs(ctypes.byref(d), first + lo, hi - lo,
+                               ctypes.cast(xf.ctypes.data + 8 * lo, ctypes.POINTER(dd)),
+                               ctypes.cast(xc.ctypes.data + 8 * lo, ctypes.POINTER(dd)),
+                               ctypes.cast(ef.ctypes.data + 8 * lo, ctypes.POINTER(i64)),
+                               ctypes.cast(ec.ctypes.data + 8 * lo, ctypes.POINTER(i64)))
+
+    if threads == 1:
+        rcs = [work(0)]
+    else:
+        with ThreadPoolExecutor(threads) as ex:
+            rcs = list(ex.map(work, range(threads)))
+    if any(rc != 0 for rc in rcs):
+        raise RuntimeError("oracle heterogeneous pair simulation failed: %r" % rcs)
+    return xf, xc, ef, ec

@@ -9,6 +9,10 @@
  * it, and it shares no code with the CUDA sources.
  *
  * What it follows:
+ *   - Heterogeneous backgrounds B1/B2 of Sec. 5 (piecewise-linear R): eq.
+ *     intinv solved per linear piece, eq. epsilon-update as an integral of R
+ *     along the fine kinetic phase, Alg. 2 in its general form (readings H1,
+ *     H2 at that section).
  *   - Philox4x32-10: Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as
  *     easy as 1, 2, 3", SC'11 (published definition; the paper names no RNG).
  *   - KD step: Alg. 1 (KineticDiffusionStep), eqs. intinv, diffusive-time,
@@ -586,6 +590,292 @@ ORC_EXPORT int64_t orc_coarse_draws(const orc_level_desc *d, uint64_t first, int
             E_t[written] = tr.E_t[r];
             chi_t[written] = tr.chi_t[r];
             if (pair_of) pair_of[written] = (int64_t)j;
+            ++written;
+        }
+    }
+    free(kap); free(a);
+    return written;
+}
+
+/* ======================================================================== */
+/* Heterogeneous backgrounds B1/B2 (Sec. 5): mu = 0, sigma = 1 and the       */
+/* piecewise-linear collision rate                                          */
+/*   R(x) = b (1 + a_left max(1 - x, 0) + a_right max(x - 1, 0)),           */
+/* B1: a_left = a_right = a (symmetric), B2: a_left = 0, a_right = a.       */
+/* Time is kept in fine steps as in the homogeneous path; rho = R dt is the */
+/* collision rate per step.                                                 */
+/*                                                                          */
+/* Reading H1: the corrected coefficients a^hetero, d^hetero (Sec. 2) are   */
+/* not printed; the homogeneous eqs. advection/diffusion are used with R    */
+/* taken at the start of the diffusive phase (the collision point), and so  */
+/* are zeta_m and beta_m of Sec. 3.2 (their R_m).  This is a stand-in.      */
+/* Reading H2: Alg. 2 as printed, in its general form: the fine path moves  */
+/* (at least one KD step) until its collision's step ends after the coarse  */
+/* collision's step; then, if the coarse collision is before T, the coarse  */
+/* KD step uses nu~ = nu_kappa (eq. nu-update), E~ of eq. epsilon-update    */
+/* (an integral of R along the fine kinetic phase kappa, whose upper limit  */
+/* t_c - t_kappa may be negative, Fig. 2(d)) and chi~ of eq. chi-update;    */
+/* the coarse flight then solves eq. intinv from the coarse position.  The  */
+/* fine path may have to step past T to feed the coarse path; its output is */
+/* its state at the first collision at or after T (the "remove fine steps   */
+/* beyond T" line).  Once both collisions lie at or after T nothing is left */
+/* to compute and the pair ends.                                            */
+/* ======================================================================== */
+typedef struct {
+    double b, a_left, a_right;
+} orc_het_bg;
+
+ORC_EXPORT double orc_het_R(const orc_het_bg *B, double x)
+{
+    double l = 1.0 - x > 0.0 ? 1.0 - x : 0.0;
+    double r = x - 1.0 > 0.0 ? x - 1.0 : 0.0;
+    return B->b * (1.0 + B->a_left * l + B->a_right * r);
+}
+
+/* dR/dx on the side of x (the side a path through x = 1 enters when it moves
+ * with velocity v: v > 0 right, v < 0 left). */
+static double het_slope(const orc_het_bg *B, double x, double v)
+{
+    int right = x > 1.0 || (x == 1.0 && v > 0.0);
+    return right ? B->b * B->a_right : -B->b * B->a_left;
+}
+
+/* The path x0 + v dt u (u in steps) meets x = 1 at u_k > 0, or never. */
+static double het_kink(double x0, double v, double dt)
+{
+    if (v == 0.0 || x0 == 1.0) return INFINITY;
+    double u = (1.0 - x0) / (v * dt);
+    return u > 0.0 ? u : INFINITY;
+}
+
+/* Optical depth over u steps from x0 (eq. intinv's integral in step units):
+ * int_0^u rho(x0 + v dt w) dw, for u >= 0; a negative u is the depth of the
+ * path segment behind x0, counted negative. */
+ORC_EXPORT double orc_het_depth(const orc_het_bg *B, double x0, double v, double dt, double u)
+{
+    if (u < 0.0) return -orc_het_depth(B, x0 + v * dt * u, v, dt, -u);
+    double rho0 = orc_het_R(B, x0) * dt;
+    double s1 = het_slope(B, x0, v) * v * dt * dt;      /* d rho / du on the first piece */
+    double s2 = het_slope(B, 1.0, v) * v * dt * dt;     /* ... and past x = 1 */
+    double uk = s1 == s2 ? INFINITY : het_kink(x0, v, dt);   /* no kink where R is one line */
+    if (u <= uk) return rho0 * u + 0.5 * s1 * u * u;
+    double I1 = rho0 * uk + 0.5 * s1 * uk * uk;
+    double w = u - uk;
+    return I1 + B->b * dt * w + 0.5 * s2 * w * w;
+}
+
+/* root w >= 0 of rho w + s w^2/2 = E on one linear piece (stable form) */
+static double het_piece_root(double rho, double s, double E)
+{
+    if (s == 0.0) return E / rho;
+    double disc = rho * rho + 2.0 * s * E;
+    if (disc < 0.0) disc = 0.0;
+    return 2.0 * E / (rho + sqrt(disc));
+}
+
+/* eq. intinv in step units: the flight u with depth E from x0 at velocity v. */
+ORC_EXPORT double orc_het_flight(const orc_het_bg *B, double x0, double v, double dt, double E)
+{
+    double rho0 = orc_het_R(B, x0) * dt;
+    double s1 = het_slope(B, x0, v) * v * dt * dt;
+    double s2 = het_slope(B, 1.0, v) * v * dt * dt;
+    double uk = s1 == s2 ? INFINITY : het_kink(x0, v, dt);
+    if (uk < INFINITY) {
+        double I1 = rho0 * uk + 0.5 * s1 * uk * uk;
+        if (E > I1) return uk + het_piece_root(B->b * dt, s2, E - I1);
+    }
+    return het_piece_root(rho0, s1, E);
+}
+
+typedef struct {
+    double x, v, q, E;     /* position and velocity at the phase start, flight (steps), its E */
+    int64_t i, w;          /* phase start (fine steps), step width          */
+} orc_het_path;
+
+/* KD step of Alg. 1 with the stand-in coefficients (reading H1); returns
+ * theta_k and the local R of the diffusive phase. */
+static double orc_het_kd_step(const orc_het_bg *B, double dt, orc_het_path *p, double nu1,
+                              double E1, double chi, double *R_loc, int new_flight_from_E)
+{
+    double v1 = nu1;                                          /* mu = 0, sigma = 1 */
+    int64_t c = p->i + (int64_t)floor(p->q);
+    int64_t end = p->w * (c / p->w + 1);
+    double theta = dt * ((double)(end - p->i) - p->q);
+    double xcol = p->x + p->v * (p->q * dt);                  /* collision point */
+    double R = orc_het_R(B, xcol);
+    double a = orc_advection(R, 0.0, theta, v1);
+    double d = orc_diffusion(R, 0.0, 1.0, theta, v1);
+    p->x = xcol + (a + d * chi);
+    p->i = end;
+    p->v = v1;
+    p->E = E1;
+    if (new_flight_from_E) p->q = orc_het_flight(B, p->x, p->v, dt, E1);
+    *R_loc = R;
+    return theta;
+}
+
+static int orc_het_run_single(const orc_het_bg *B, double dt, int64_t n, const orc_stream *s,
+                              double x0, double *x_out, int64_t *events)
+{
+    double nu0, E0, ux0;
+    orc_draw_init(s, &nu0, &E0, &ux0);
+    orc_het_path p = {x0, nu0, 0.0, E0, 0, 1};
+    p.q = orc_het_flight(B, p.x, p.v, dt, E0);
+    int64_t k = 0;
+    while (p.q < (double)(n - p.i)) {
+        double nu1, E1, chi, R;
+        if (orc_draw_event(s, k + 1, &nu1, &E1, &chi)) return -1;
+        orc_het_kd_step(B, dt, &p, nu1, E1, chi, &R, 1);
+        ++k;
+    }
+    if (p.i < n) p.x = p.x + p.v * ((double)(n - p.i) * dt);
+    *x_out = p.x;
+    *events = k;
+    return 0;
+}
+
+static int orc_het_run_pair(const orc_het_bg *B, double dt, int64_t n, int M, const orc_stream *s,
+                            double x0, double *xf_out, double *xc_out, int64_t *ev_f, int64_t *ev_c,
+                            orc_trace *tr)
+{
+    double nu0, E0, ux0;
+    orc_draw_init(s, &nu0, &E0, &ux0);
+    orc_het_path f = {x0, nu0, 0.0, E0, 0, 1};
+    f.q = orc_het_flight(B, f.x, f.v, dt, E0);
+    orc_het_path c = f;                                        /* shared first flight */
+    c.w = M;
+    int64_t k1 = 0, k2 = 0;
+    int have_out = 0;
+    double xf_keep = 0.0, vf_keep = 0.0;
+    int64_t if_keep = 0;
+    static __thread double win_chi[ORC_MAX_WINDOW], win_theta[ORC_MAX_WINDOW], win_R[ORC_MAX_WINDOW];
+    static __thread double win_nu[ORC_MAX_WINDOW + 1], win_tau[ORC_MAX_WINDOW + 1];
+#define HET_FINE_DONE() (!(f.q < (double)(n - f.i)))
+#define HET_COARSE_DONE() (!(c.q < (double)(n - c.i)))
+    if (HET_FINE_DONE() && !have_out) { have_out = 1; xf_keep = f.x; vf_keep = f.v; if_keep = f.i; }
+    while (!HET_COARSE_DONE() || !HET_FINE_DONE()) {
+        int64_t cc = c.i + (int64_t)floor(c.q);
+        int64_t coarse_end = M * (cc / M + 1);                 /* step end of the coarse collision */
+        int64_t m = 0;
+        for (;;) {
+            double nu1, E1, chi, R;
+            if (m >= ORC_MAX_WINDOW) return -2;
+            if (orc_draw_event(s, k1 + 1, &nu1, &E1, &chi)) return -1;
+            double theta = orc_het_kd_step(B, dt, &f, nu1, E1, chi, &R, 1);
+            win_chi[m] = chi;
+            win_theta[m] = theta;
+            win_R[m] = R;
+            win_nu[m + 1] = nu1;
+            win_tau[m + 1] = f.q * dt;
+            ++m;
+            ++k1;
+            if (HET_FINE_DONE() && !have_out) { have_out = 1; xf_keep = f.x; vf_keep = f.v; if_keep = f.i; }
+            int64_t fc = f.i + (int64_t)floor(f.q < (double)(4 * n + 4) ? f.q : (double)(4 * n + 4));
+            if (fc + 1 > coarse_end) break;                    /* the until-test of Alg. 2 */
+            if (HET_COARSE_DONE() && HET_FINE_DONE()) break;   /* nothing left to feed */
+        }
+        if (!HET_COARSE_DONE()) {
+            double nu_t = win_nu[m];                           /* eq. nu-update */
+            /* eq. epsilon-update: E~ = E_kappa - int_0^{t_c - t_kappa} R(x_kappa + v_kappa t) dt */
+            double E_t = f.E - orc_het_depth(B, f.x, f.v, dt, (double)(coarse_end - f.i));
+            /* eq. chi-update with local R_m (reading H1) */
+            double beta0 = orc_beta(win_R[0], 1.0, orc_theta_prime(win_R[0], win_theta[0]));
+            double num = beta0 * win_chi[0], den = beta0 * beta0;
+            for (int64_t j = 1; j < m; ++j) {
+                double zeta_prev = orc_zeta(win_R[j - 1], win_theta[j - 1]);
+                double alpha = (win_tau[j] + zeta_prev) * 1.0;
+                double beta = orc_beta(win_R[j], 1.0, orc_theta_prime(win_R[j], win_theta[j]));
+                num += alpha * win_nu[j] + beta * win_chi[j];
+                den += alpha * alpha + beta * beta;
+            }
+            double chi_t = den > 0.0 ? num / sqrt(den) : win_chi[0];
+            if (tr && tr->n_coarse < tr->cap) {
+                int64_t r = tr->n_coarse++;
+                tr->kappa[r] = k1;
+                tr->nu_t[r] = nu_t;
+                tr->E_t[r] = E_t;
+                tr->chi_t[r] = chi_t;
+                tr->coarse_collision[r] = (double)c.i + c.q;
+            }
+            double R;
+            orc_het_kd_step(B, dt, &c, nu_t, E_t, chi_t, &R, 1);
+            ++k2;
+        }
+    }
+#undef HET_FINE_DONE
+#undef HET_COARSE_DONE
+    if (if_keep < n) xf_keep = xf_keep + vf_keep * ((double)(n - if_keep) * dt);
+    if (c.i < n) c.x = c.x + c.v * ((double)(n - c.i) * dt);
+    *xf_out = xf_keep;
+    *xc_out = c.x;
+    *ev_f = k1;
+    *ev_c = k2;
+    return 0;
+}
+
+typedef struct {
+    orc_het_bg bg;
+    double dt;       /* fine step of this level */
+    int64_t n;       /* fine steps to T         */
+    int32_t M;       /* coarsening of the pair's coarse path */
+    int32_t level;   /* fine level: Philox counter word 2    */
+    int32_t recipe;
+    int32_t coupled;
+    uint64_t seed;
+    uint32_t request;
+    int32_t pad_;
+    double x0;       /* initial position (the paper's test case: 1) */
+} orc_het_desc;
+
+/* Per-pair final positions and event counts of a heterogeneous level. */
+ORC_EXPORT int orc_het_pairs(const orc_het_desc *d, uint64_t first, int64_t count, double *xf,
+                             double *xc, int64_t *ev_f, int64_t *ev_c)
+{
+    orc_level_desc ld;
+    memset(&ld, 0, sizeof(ld));
+    ld.level = d->level; ld.recipe = d->recipe; ld.seed = d->seed; ld.request = d->request;
+    for (int64_t j = 0; j < count; ++j) {
+        orc_stream s;
+        orc_make_stream(&ld, first + (uint64_t)j, &s);
+        int rc;
+        if (!d->coupled) {
+            rc = orc_het_run_single(&d->bg, d->dt, d->n, &s, d->x0, &xf[j], &ev_f[j]);
+            xc[j] = 0.0;
+            ev_c[j] = 0;
+        } else {
+            rc = orc_het_run_pair(&d->bg, d->dt, d->n, d->M, &s, d->x0, &xf[j], &xc[j], &ev_f[j],
+                                  &ev_c[j], NULL);
+        }
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* The coarse draws (nu~, E~, chi~) of heterogeneous pairs [first, first +
+ * count), at most cap; returns the number written or a negative error. */
+ORC_EXPORT int64_t orc_het_coarse_draws(const orc_het_desc *d, uint64_t first, int64_t count,
+                                        int64_t cap, double *nu_t, double *E_t, double *chi_t)
+{
+    orc_level_desc ld;
+    memset(&ld, 0, sizeof(ld));
+    ld.level = d->level; ld.recipe = d->recipe; ld.seed = d->seed; ld.request = d->request;
+    int64_t written = 0, tcap = 1 << 16;
+    int64_t *kap = (int64_t *)malloc(sizeof(int64_t) * tcap);
+    double *a = (double *)malloc(sizeof(double) * tcap * 4);
+    if (!kap || !a) { free(kap); free(a); return -3; }
+    for (int64_t j = 0; j < count && written < cap; ++j) {
+        orc_stream s;
+        orc_make_stream(&ld, first + (uint64_t)j, &s);
+        orc_trace tr = {tcap, 0, kap, a, a + tcap, a + 2 * tcap, a + 3 * tcap};
+        double xf, xc; int64_t ef, ec;
+        if (orc_het_run_pair(&d->bg, d->dt, d->n, d->M, &s, d->x0, &xf, &xc, &ef, &ec, &tr)) {
+            written = -1;
+            break;
+        }
+        for (int64_t r = 0; r < tr.n_coarse && written < cap; ++r) {
+            nu_t[written] = tr.nu_t[r];
+            E_t[written] = tr.E_t[r];
+            chi_t[written] = tr.chi_t[r];
             ++written;
         }
     }
