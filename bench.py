@@ -111,6 +111,9 @@ def parse():
                          "launches for ncu captures")
     ap.add_argument("--eps", type=float, default=None,
                     help="kernelcase batch: only the estimate of this eps (default: all three)")
+    ap.add_argument("--warp-pair", type=int, default=0,
+                    help="kernelcase batch: warp_pair_min_events of the batch configuration "
+                         "(0: library default; -1: one pair per lane everywhere)")
     ap.add_argument("--scale", type=int, default=0,
                     help="kernelcase: log2 scale of the pair counts (batch: 3 is the full step)")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
@@ -251,11 +254,18 @@ def run_gpu(args):
     fixed = [[lv["n"] for lv in r.levels] for r in pilot]
     step_problems = [mk.make_problem(precision=prec, n_fixed=n, **d) for d, n in zip(dicts, fixed)]
 
-    cfg = base_cfg
-    tune = None
+    # The autotuner picks the configuration per workload: the fixed-N step
+    # (throughput: deep levels one pair per lane usually win, their chains
+    # hide behind the other levels) and the adaptive estimates of the time to
+    # tolerance (latency: deep levels one pair per warp usually win, rounds
+    # are as long as their longest chain).
+    cfg = cfg_ttt = base_cfg
+    tune = tune_ttt = None
     if args.form == "batch" and prec != mk.PREC_FP64:
         cfg, secs = ctx.autotune_batch(step_problems, base_cfg)
-        tune = {"best": cfg.as_dict(), "seconds_ppt_major": secs}
+        tune = {"best": cfg.as_dict(), "seconds_warp_ppt_substeps": secs}
+        cfg_ttt, secs_t = ctx.autotune_batch(adaptive, base_cfg)
+        tune_ttt = {"best": cfg_ttt.as_dict(), "seconds_warp_ppt_substeps": secs_t}
 
     def step():
         if args.form == "batch":
@@ -268,7 +278,7 @@ def run_gpu(args):
     def ttt_once(problems):
         t = time.perf_counter()
         if args.form == "batch":
-            rs = ctx.estimate_batch(problems, cfg, stream)
+            rs = ctx.estimate_batch(problems, cfg_ttt, stream)
         else:
             rs = [ctx.estimate(p, stream) for p in problems]
         return time.perf_counter() - t, rs
@@ -390,7 +400,9 @@ def run_gpu(args):
                                "L=min(12,ceil(log2(dt0/(eps^2/4)))), tol=1e-3, 128 bins",
                    "form": args.form, "precision": args.precision, "n_fixed": fixed,
                    "batch_config": cfg.as_dict() if args.form == "batch" else None,
-                   "autotune": tune,  # seconds over ppt {1,2,4,8} x substeps {16,64,256,unbounded}
+                   "autotune": tune,  # seconds over warp {default, never} x ppt {1,2,4,8} x substeps {16,64,256,unbounded}
+                   "batch_config_time_to_tolerance": cfg_ttt.as_dict() if args.form == "batch" else None,
+                   "autotune_time_to_tolerance": tune_ttt,
                    "events_per_step": ev / args.steps / world,
                    "time_to_tolerance_s": ttt, "time_to_tolerance_first_call_s": ttt_first,
                    "time_to_tolerance_runs_s": ttt_all,
@@ -837,10 +849,10 @@ def run_kernelcase(args):
     torch.cuda.set_device(0)
     prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
     out = {"workload": "kernelcase", "form": args.form, "precision": args.precision,
-           "scale": args.scale, "launches": []}
+           "scale": args.scale, "warp_pair": args.warp_pair, "launches": []}
     if args.form == "batch":
         cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=0, use_graph=0,
-                              max_requests=16, max_nbins=128)
+                              max_requests=16, max_nbins=128, warp_pair_min_events=args.warp_pair)
         ctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
         fixed = [[max(1, (x << args.scale) >> 3) for x in n] for n in PILOT_N_FIXED]
         sel = [i for i, e in enumerate(EPS_SET) if args.eps is None or e == args.eps]

@@ -43,7 +43,7 @@ extern "C" {
 #define MLKD_API
 #endif
 
-#define MLKD_ABI_VERSION 2
+#define MLKD_ABI_VERSION 3
 #define MLKD_MAX_LEVELS 16      /* levels 0..15 */
 #define MLKD_MAX_BINS 1024
 
@@ -54,18 +54,39 @@ typedef enum {
     MLKD_ECUDA = -3,       /* a CUDA runtime call or kernel launch failed      */
     MLKD_ETIMEDOUT = -4,   /* a bounded wait (device or poll) ran out          */
     MLKD_EBUSY = -5,       /* no free slot or arena room (serving)             */
-    MLKD_ENOTFOUND = -6    /* unknown request id                               */
+    MLKD_ENOTFOUND = -6,   /* unknown request id                               */
+    MLKD_EINTERNAL = -7    /* a device-side consistency check failed (the work
+                              was stopped; the context stays usable)           */
 } mlkd_status;
 
 /* Quantity of interest F(x(T)).  X2: x^2 in free space.  X2_PERIODIC:
  * (x mod 1)^2 on the periodic unit interval.  DENSITY: the histogram density
  * (nbins > 0) sets the sample counts through its largest bin variance; the
  * scalar F is still reduced (x^2, or (x mod 1)^2 for the cosine start). */
-typedef enum { MLKD_QOI_X2 = 0, MLKD_QOI_X2_PERIODIC = 1, MLKD_QOI_DENSITY = 2 } mlkd_qoi;
+typedef enum { MLKD_QOI_X2 = 0, MLKD_QOI_X2_PERIODIC = 1, MLKD_QOI_DENSITY = 2,
+               MLKD_QOI_X = 3 } mlkd_qoi;
+/* MLKD_QOI_X: F(x) = x, the position at T (the paper's test case, Sec. 5);
+ * free space only, per-level calls only (mlkd_run_level, mlkd_estimate,
+ * mlkd_debug_pairs). */
 
 /* Initial position: x = 0, or density proportional to 1 + cos(2 pi x) on the
  * periodic unit interval (inverse CDF of a uniform). */
-typedef enum { MLKD_INIT_ORIGIN = 0, MLKD_INIT_COSINE = 1 } mlkd_init;
+typedef enum { MLKD_INIT_ORIGIN = 0, MLKD_INIT_COSINE = 1, MLKD_INIT_POINT = 2 } mlkd_init;
+/* MLKD_INIT_POINT: every path starts at problem.x0 (per-level calls only). */
+
+/* Background of the collisions.  HOMOGENEOUS: the diffusive scaling of eps
+ * (R = 1/eps^2, sigma = 1/eps, mean velocity mu).  B1 / B2: the
+ * heterogeneous backgrounds of Sec. 5 with mu = 0, sigma = 1 and a
+ * piecewise-linear rate R_1(x) = b (1 + a |x - 1|) (symmetric), R_2(x) = b for
+ * x <= 1 and b (1 + a (x - 1)) for x > 1 (eps is not used; mu must be 0).
+ * The paper defers the corrected KD coefficients a^hetero, d^hetero of these
+ * backgrounds to another work; the library uses the homogeneous eqs.
+ * advection/diffusion (and the Sec. 3.2 weights) at the rate of the
+ * collision point, a stand-in for them.  Flights solve eq. intinv exactly per
+ * linear piece, and the coarse flight follows eq. epsilon-update.  Per-level
+ * calls only (mlkd_run_level, mlkd_estimate, mlkd_debug_pairs); the finest
+ * level has at most 2^24 fine steps. */
+typedef enum { MLKD_BG_HOMOGENEOUS = 0, MLKD_BG_B1 = 1, MLKD_BG_B2 = 2 } mlkd_background;
 
 /* Arithmetic of the pair state.  FP64: state and sums in FP64 (53-bit
  * uniforms, two Philox blocks per fine event).  FP32_DY64: FP32 state, 24-bit
@@ -108,6 +129,10 @@ typedef struct {
                                  Estimator level j couples level level_set[j] with
                                  level_set[j-1] (coarsening M^gap, Sec. 4.2); statistics,
                                  n_fixed and results are indexed by j. */
+    int32_t background;    /* mlkd_background                                  */
+    int32_t reserved2_;
+    double bg_a, bg_b;     /* B1 / B2 parameters a >= 0, b > 0                 */
+    double x0;             /* start of every path for MLKD_INIT_POINT          */
 } mlkd_problem;
 
 /* Sums over the pairs of one level (eq. mlmc-compact):
@@ -319,6 +344,10 @@ typedef struct {
                                     places at the head of every work queue that are never
                                     published, so that the first publication wait runs out
                                     (0 .. 2^20)                                               */
+    int32_t warp_pair_min_events;/* a level whose pairs average at least this many KD events
+                                    runs one pair per warp, 32 fine events per step, instead
+                                    of one pair per lane: its serial chains get 32 times
+                                    shorter (0: library default 1024; -1: never)             */
 } mlkd_batch_config;
 
 /* Arena bytes a context needs for the batched and serving forms with this
@@ -350,10 +379,12 @@ MLKD_API mlkd_status mlkd_debug_batch_pairs(mlkd_context *ctx, const mlkd_proble
                                             int32_t *kf, int32_t *kc);
 
 /* Autotuner: times mlkd_estimate_batch on these problems for every
- * pairs_per_thread in {1, 2, 4, 8} and substeps_per_launch in
+ * warp_pair_min_events in {0 (library default), -1 (one pair per lane
+ * everywhere)}, pairs_per_thread in {1, 2, 4, 8} and substeps_per_launch in
  * {16, 64, 256, 0 (unbounded)} (graph form), and writes the fastest
- * configuration to *best (its other fields copied from *base).  seconds[16],
- * if not NULL, receives the times in the order ppt-major. */
+ * configuration to *best (its other fields copied from *base).  seconds[32],
+ * if not NULL, receives the times in that nesting order (warp-pair setting
+ * outermost, substeps innermost). */
 MLKD_API mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
                                          const mlkd_batch_config *base, void *stream,
                                          mlkd_batch_config *best, double *seconds);

@@ -33,8 +33,10 @@ _LIB_PATH = os.path.join(_OUT_DIR, "liborc.so")
 QOI_X2 = 0            # F(x) = x^2 (free space)
 QOI_X2_PERIODIC = 1   # F(x) = (x mod 1)^2 on the periodic unit interval
 QOI_DENSITY = 2       # histogram density drives the sample counts
+QOI_X = 3             # F(x) = x, the paper's test-case QoI (Sec. 5)
 INIT_ORIGIN = 0
 INIT_COSINE = 1
+INIT_POINT = 2        # every path starts at Problem.x0
 RECIPE_24 = 0         # 24-bit uniforms (FP32 form of the stream)
 RECIPE_53 = 1         # 53-bit uniforms (FP64 form of the stream)
 
@@ -59,7 +61,8 @@ class LevelDesc(ctypes.Structure):
     _fields_ = [("R", ctypes.c_double), ("mu", ctypes.c_double), ("sigma", ctypes.c_double),
                 ("dt", ctypes.c_double), ("n", ctypes.c_int64), ("M", ctypes.c_int32),
                 ("level", ctypes.c_int32), ("init", ctypes.c_int32), ("recipe", ctypes.c_int32),
-                ("seed", ctypes.c_uint64), ("request", ctypes.c_uint32), ("coupled", ctypes.c_int32)]
+                ("seed", ctypes.c_uint64), ("request", ctypes.c_uint32), ("coupled", ctypes.c_int32),
+                ("x0", ctypes.c_double)]
 
 
 def lib():
@@ -163,14 +166,18 @@ class Problem:
     mu: float = 0.0
     n_fixed: list = field(default_factory=list)
     level_set: list = field(default_factory=list)   # estimator levels (Sec. 4.2); empty: 0..L
+    x0: float = 0.0                                 # start of every path for INIT_POINT
+    background: int = 0                             # 0 homogeneous; BG_B1 / BG_B2 (Sec. 5)
+    a: float = 0.0                                  # B1/B2: R(x) from a, b; mu = 0, sigma = 1
+    b: float = 0.0
 
     @property
     def R(self):
-        return 1.0 / (self.eps * self.eps)
+        return self.b if self.background else 1.0 / (self.eps * self.eps)
 
     @property
     def sigma(self):
-        return 1.0 / self.eps
+        return 1.0 if self.background else 1.0 / self.eps
 
     def steps0(self) -> int:
         r = self.T / self.dt0
@@ -205,10 +212,11 @@ class Problem:
         d.recipe = self.recipe
         d.seed = self.seed
         d.request = self.request
+        d.x0 = self.x0
         return d
 
     def bin_range(self):
-        if self.init == INIT_COSINE or self.qoi == QOI_X2_PERIODIC:
+        if self.periodic():
             return 0.0, 1.0
         return self.lo, self.hi
 
@@ -223,6 +231,13 @@ def pairs(problem: Problem, level: int, first: int, count: int, threads: int = 1
     """Final positions (x_l, x_{l-1}) and event counts of pairs
     [first, first+count) of estimator level `level`.  Estimator level 0 is
     Alg. 1 (x_c = 0)."""
+    if problem.background:
+        fine, coarsening = problem.estimator_levels()[level]
+        x0 = problem.x0 if problem.init == INIT_POINT else 0.0
+        return het_pairs(problem.background, problem.a, problem.b, problem.T, problem.dt0,
+                         problem.M, fine, level > 0, first, count, x0=x0, seed=problem.seed,
+                         request=problem.request, recipe=problem.recipe, coarsening=coarsening,
+                         threads=threads)
     d = problem.level_desc(level)
     xf = np.zeros(count, np.float64)
     xc = np.zeros(count, np.float64)
@@ -263,6 +278,7 @@ def _fine_desc(problem: Problem, level: int) -> LevelDesc:
     d.level = level
     d.init, d.recipe, d.seed, d.request, d.coupled = (problem.init, problem.recipe, problem.seed,
                                                       problem.request, 0)
+    d.x0 = problem.x0
     return d
 
 
@@ -338,6 +354,8 @@ def stream_draws(problem: Problem, level: int, pair: int, K: int):
 # Quantities of interest and level sums (Sec. 4.1).
 # --------------------------------------------------------------------------
 def qoi_values(problem: Problem, x: np.ndarray) -> np.ndarray:
+    if problem.qoi == QOI_X:
+        return np.array(x, np.float64, copy=True)
     if problem.periodic():
         xm = x - np.floor(x)
         return xm * xm
@@ -407,7 +425,7 @@ def level_sums(problem: Problem, level: int, xf, xc, ef, ec) -> LevelSums:
         y = qf
     else:
         qc = qoi_values(problem, xc)
-        if problem.periodic():
+        if problem.periodic() or problem.qoi == QOI_X:
             y = qf - qc
         else:
             y = (xf - xc) * (xf + xc)     # x_f^2 - x_c^2 without cancellation

@@ -310,7 +310,7 @@ static void orc_drift(const orc_params *P, orc_path *p)
 /* ------------------------------------------------------------------------ */
 /* Initial position.                                                         */
 /* ------------------------------------------------------------------------ */
-enum { ORC_INIT_ORIGIN = 0, ORC_INIT_COSINE = 1 };
+enum { ORC_INIT_ORIGIN = 0, ORC_INIT_COSINE = 1, ORC_INIT_POINT = 2 };
 
 /* G(y) = y - sin(2 pi y)/(2 pi) on [-1/2, 1/2]: the CDF of 1 + cos(2 pi x)
  * on [0,1) is F(x) = 1/2 + G(x - 1/2).  Small |y| from the series
@@ -483,6 +483,7 @@ typedef struct {
     uint64_t seed;
     uint32_t request;
     int32_t coupled; /* 0: single path (Alg. 1); 1: correlated pair (Alg. 2)    */
+    double x0;       /* start of every path when init == ORC_INIT_POINT          */
 } orc_level_desc;
 
 static void orc_make_stream(const orc_level_desc *d, uint64_t pair, orc_stream *s)
@@ -513,12 +514,13 @@ ORC_EXPORT int orc_pairs(const orc_level_desc *d, uint64_t first, int64_t count,
         orc_stream s;
         orc_make_stream(d, first + (uint64_t)j, &s);
         int rc;
+        const double *x0 = d->init == ORC_INIT_POINT ? &d->x0 : NULL;
         if (!d->coupled) {
-            rc = orc_run_single(&P, &s, d->init, NULL, &xf[j], &ev_f[j]);
+            rc = orc_run_single(&P, &s, d->init, x0, &xf[j], &ev_f[j]);
             xc[j] = 0.0;
             ev_c[j] = 0;
         } else {
-            rc = orc_run_pair(&P, &s, d->init, NULL, &xf[j], &xc[j], &ev_f[j], &ev_c[j], NULL);
+            rc = orc_run_pair(&P, &s, d->init, x0, &xf[j], &xc[j], &ev_f[j], &ev_c[j], NULL);
         }
         if (rc) return rc;
     }
@@ -694,11 +696,16 @@ typedef struct {
 
 /* KD step of Alg. 1 with the stand-in coefficients (reading H1); returns
  * theta_k and the local R of the diffusive phase. */
-static double orc_het_kd_step(const orc_het_bg *B, double dt, orc_het_path *p, double nu1,
-                              double E1, double chi, double *R_loc, int new_flight_from_E)
+/* Reading H3: a fine path that steps past T to feed the coarse path may meet
+ * flights far longer than the horizon; its step index is counted with the
+ * flight cut at 4n + 4 steps and the index capped at 4n + 4 (values that only
+ * enter the coarse path through eq. epsilon-update's upper limit). */
+static double orc_het_kd_step(const orc_het_bg *B, double dt, int64_t n, orc_het_path *p,
+                              double nu1, double E1, double chi, double *R_loc)
 {
     double v1 = nu1;                                          /* mu = 0, sigma = 1 */
-    int64_t c = p->i + (int64_t)floor(p->q);
+    const double cap = (double)(4 * n + 4);
+    int64_t c = p->i + (int64_t)floor(p->q < cap ? p->q : cap);
     int64_t end = p->w * (c / p->w + 1);
     double theta = dt * ((double)(end - p->i) - p->q);
     double xcol = p->x + p->v * (p->q * dt);                  /* collision point */
@@ -706,10 +713,10 @@ static double orc_het_kd_step(const orc_het_bg *B, double dt, orc_het_path *p, d
     double a = orc_advection(R, 0.0, theta, v1);
     double d = orc_diffusion(R, 0.0, 1.0, theta, v1);
     p->x = xcol + (a + d * chi);
-    p->i = end;
+    p->i = end < 4 * n + 4 ? end : 4 * n + 4;
     p->v = v1;
     p->E = E1;
-    if (new_flight_from_E) p->q = orc_het_flight(B, p->x, p->v, dt, E1);
+    p->q = orc_het_flight(B, p->x, p->v, dt, E1);
     *R_loc = R;
     return theta;
 }
@@ -725,7 +732,7 @@ static int orc_het_run_single(const orc_het_bg *B, double dt, int64_t n, const o
     while (p.q < (double)(n - p.i)) {
         double nu1, E1, chi, R;
         if (orc_draw_event(s, k + 1, &nu1, &E1, &chi)) return -1;
-        orc_het_kd_step(B, dt, &p, nu1, E1, chi, &R, 1);
+        orc_het_kd_step(B, dt, n, &p, nu1, E1, chi, &R);
         ++k;
     }
     if (p.i < n) p.x = p.x + p.v * ((double)(n - p.i) * dt);
@@ -754,14 +761,14 @@ static int orc_het_run_pair(const orc_het_bg *B, double dt, int64_t n, int M, co
 #define HET_COARSE_DONE() (!(c.q < (double)(n - c.i)))
     if (HET_FINE_DONE() && !have_out) { have_out = 1; xf_keep = f.x; vf_keep = f.v; if_keep = f.i; }
     while (!HET_COARSE_DONE() || !HET_FINE_DONE()) {
-        int64_t cc = c.i + (int64_t)floor(c.q);
+        int64_t cc = c.i + (int64_t)floor(c.q < (double)(4 * n + 4) ? c.q : (double)(4 * n + 4));
         int64_t coarse_end = M * (cc / M + 1);                 /* step end of the coarse collision */
         int64_t m = 0;
         for (;;) {
             double nu1, E1, chi, R;
             if (m >= ORC_MAX_WINDOW) return -2;
             if (orc_draw_event(s, k1 + 1, &nu1, &E1, &chi)) return -1;
-            double theta = orc_het_kd_step(B, dt, &f, nu1, E1, chi, &R, 1);
+            double theta = orc_het_kd_step(B, dt, n, &f, nu1, E1, chi, &R);
             win_chi[m] = chi;
             win_theta[m] = theta;
             win_R[m] = R;
@@ -798,7 +805,7 @@ static int orc_het_run_pair(const orc_het_bg *B, double dt, int64_t n, int M, co
                 tr->coarse_collision[r] = (double)c.i + c.q;
             }
             double R;
-            orc_het_kd_step(B, dt, &c, nu_t, E_t, chi_t, &R, 1);
+            orc_het_kd_step(B, dt, n, &c, nu_t, E_t, chi_t, &R);
             ++k2;
         }
     }

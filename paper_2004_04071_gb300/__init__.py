@@ -23,13 +23,15 @@ MLKD_ECUDA = -3
 MLKD_ETIMEDOUT = -4
 MLKD_EBUSY = -5
 MLKD_ENOTFOUND = -6
+MLKD_EINTERNAL = -7
 
-QOI_X2, QOI_X2_PERIODIC, QOI_DENSITY = 0, 1, 2
-INIT_ORIGIN, INIT_COSINE = 0, 1
+QOI_X2, QOI_X2_PERIODIC, QOI_DENSITY, QOI_X = 0, 1, 2, 3
+INIT_ORIGIN, INIT_COSINE, INIT_POINT = 0, 1, 2
+BG_HOMOGENEOUS, BG_B1, BG_B2 = 0, 1, 2
 PREC_FP64, PREC_FP32_DY64, PREC_FP32_COMP, PREC_FP64_U24 = 0, 1, 2, 3
 MAX_LEVELS = 16
 MAX_BINS = 1024
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_context_create", "mlkd_context_destroy", "mlkd_run_level",
@@ -57,7 +59,9 @@ class Problem(ctypes.Structure):
                 ("tol", ctypes.c_double), ("n_warmup", ctypes.c_int32),
                 ("request", ctypes.c_uint32), ("seed", ctypes.c_uint64),
                 ("n_fixed", ctypes.POINTER(ctypes.c_int64)), ("n_set", ctypes.c_int32),
-                ("reserved_", ctypes.c_int32), ("level_set", ctypes.POINTER(ctypes.c_int32))]
+                ("reserved_", ctypes.c_int32), ("level_set", ctypes.POINTER(ctypes.c_int32)),
+                ("background", ctypes.c_int32), ("reserved2_", ctypes.c_int32),
+                ("bg_a", ctypes.c_double), ("bg_b", ctypes.c_double), ("x0", ctypes.c_double)]
 
 
 class LevelStats(ctypes.Structure):
@@ -87,18 +91,21 @@ class BatchConfig(ctypes.Structure):
     _fields_ = [("pairs_per_thread", ctypes.c_int32), ("substeps_per_launch", ctypes.c_int32),
                 ("use_graph", ctypes.c_int32), ("max_requests", ctypes.c_int32),
                 ("max_nbins", ctypes.c_int32), ("refill_min", ctypes.c_int32),
-                ("publish_wait_spins", ctypes.c_int32), ("test_stall_queues", ctypes.c_int32)]
+                ("publish_wait_spins", ctypes.c_int32), ("test_stall_queues", ctypes.c_int32),
+                ("warp_pair_min_events", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def batch_config(pairs_per_thread=1, substeps_per_launch=256, use_graph=1, max_requests=64,
-                 max_nbins=128, refill_min=0, publish_wait_spins=0, test_stall_queues=0) -> BatchConfig:
+                 max_nbins=128, refill_min=0, publish_wait_spins=0, test_stall_queues=0,
+                 warp_pair_min_events=0) -> BatchConfig:
     c = BatchConfig()
     c.pairs_per_thread, c.substeps_per_launch, c.use_graph = pairs_per_thread, substeps_per_launch, use_graph
     c.max_requests, c.max_nbins, c.refill_min = max_requests, max_nbins, refill_min
     c.publish_wait_spins, c.test_stall_queues = publish_wait_spins, test_stall_queues
+    c.warp_pair_min_events = warp_pair_min_events
     return c
 
 
@@ -227,9 +234,11 @@ def _check(rc, what):
 
 def make_problem(eps, T, dt0, M=2, L=1, qoi=QOI_X2, init=INIT_ORIGIN, nbins=0, lo=-3.0, hi=3.0,
                  tol=0.0, n_warmup=100, precision=PREC_FP64, seed=0, request=0, mu=0.0,
-                 n_fixed=None, level_set=None) -> Problem:
+                 n_fixed=None, level_set=None, background=BG_HOMOGENEOUS, bg_a=0.0, bg_b=0.0,
+                 x0=0.0) -> Problem:
     p = Problem()
     p.eps, p.mu, p.T, p.dt0 = eps, mu, T, dt0
+    p.background, p.bg_a, p.bg_b, p.x0 = background, bg_a, bg_b, x0
     p.M, p.L, p.qoi, p.init, p.nbins, p.precision = M, L, qoi, init, nbins, precision
     p.lo, p.hi, p.tol, p.n_warmup = lo, hi, tol, n_warmup
     p.request, p.seed = request & 0xFFFFFFFF, seed & 0xFFFFFFFFFFFFFFFF
@@ -493,7 +502,7 @@ class Context:
         n = len(problems)
         arr = (Problem * n)(*problems)
         best = BatchConfig()
-        secs = (ctypes.c_double * 16)()
+        secs = (ctypes.c_double * 32)()
         _check(lib().mlkd_autotune_batch(self.handle, arr, n, ctypes.byref(base),
                                          _stream_handle(stream), ctypes.byref(best), secs),
                "mlkd_autotune_batch")

@@ -31,6 +31,7 @@
 
 #include "mlkd_host.h"
 #include "mlkd_pair.cuh"
+#include "mlkd_warp_pair.cuh"
 
 namespace mlkd {
 
@@ -46,6 +47,7 @@ constexpr long long kRoundChunks = (long long)kBL * kMaxChunksPerJob;  // chunks
 constexpr long long kSlotChunks = kRoundChunks;
 constexpr int kPublishSpins = 1 << 22;           // bounded wait for earlier reservations to publish
 constexpr double kSmallRoundEvents = 2e8;        // predicted KD events of a round that goes first (about 2 ms)
+constexpr int kWarpPairEvents = 1024;            // events per pair from which a pair runs on a whole warp
 constexpr int kIdleSpins = 4096;                 // bounded wait for new work: sleeps of up to 64 us, about 0.25 s
 
 struct ReqDesc {
@@ -76,6 +78,7 @@ struct ReqState {
     long long target[kBL];
     long long job_ch[kBL];      // pairs per chunk of this round's job per level
     int32_t job_queue[kBL];     // queue of the level's chunks: 0 main, 1 long chunks, 2 small rounds
+    int32_t job_warp[kBL];      // 1: the level's pairs run one per warp
     long long plan_want[kBL];   // planning scratch: pairs wanted per level
     double plan_epp[kBL];       // planning scratch: events per pair per level
     int32_t counted;            // 1: counted in BatchCtl::running
@@ -85,7 +88,8 @@ struct ReqState {
 struct Chunk {
     int32_t req, level;
     unsigned long long first;
-    int32_t count, pad_;
+    int32_t count;
+    int32_t warp_pair;           // 1: one pair per warp, 32 events per step
 };
 
 // Work queues are rings of chunk ids.  A producer reserves places at *_resv,
@@ -104,7 +108,7 @@ struct BatchCtl {
     unsigned long long events;  // fine + coarse events merged into request sums so far
     unsigned long long events_done;  // fine + coarse events of finished chunks so far
     int32_t running;            // requests with a round in flight
-    int32_t error;              // 1: a publication wait ran out
+    int32_t error;              // 1: a publication wait ran out; 2: a consistency check failed
 };
 // the server reads events .. error in one copy
 static_assert(offsetof(BatchCtl, error) == offsetof(BatchCtl, events) + 20, "BatchCtl tail layout");
@@ -136,6 +140,7 @@ struct BatchLaunch {
     int32_t n_slots;
     int32_t refill_min;          // idle lanes a warp gathers before it restarts them together
     int32_t publish_spins;       // bound of the publication wait
+    int32_t warp_pair_events;    // levels with at least this many events per pair run one pair per warp (0: never)
     int32_t dbg_req;             // per-pair readout of request slot dbg_req, estimator level
     int32_t dbg_level;           // dbg_level (-1: none)
     int32_t pad_;
@@ -414,6 +419,15 @@ __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
             S.job_count[l] = 0;
             long long count = want[l];
             if (count <= 0) continue;
+            // A level whose pairs are long serial chains runs one pair per
+            // warp, 32 events per step; its chunks then hold about
+            // kTargetIters warp steps of pairs, not a multiple of 32.
+            const bool wp = B.warp_pair_events > 0 && epps[l] >= (double)B.warp_pair_events;
+            if (wp) {
+                double c = 32.0 * kTargetIters / (epps[l] + 32.0 * kPairStartIters);
+                tch[l] = c < 1.0 ? 1 : (long long)c;
+            }
+            S.job_warp[l] = wp ? 1 : 0;
             long long ch = tch[l];
             long long nch = (count + ch - 1) / ch;
             if (nch > kMaxChunksPerJob) {
@@ -459,7 +473,7 @@ __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
             c.level = l;
             c.first = (unsigned long long)first;
             c.count = (int32_t)cnt;
-            c.pad_ = 0;
+            c.warp_pair = S.job_warp[l];
             B.chunks[S.job_cb[l] + i] = c;
         }
     }
@@ -665,6 +679,21 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             idle = 0;
             c = __shfl_sync(kFullMask, cn, 0);
             {
+                // Consistency checks of the claimed id and its descriptor
+                // (cheap, once per chunk): a failure stops the loop with
+                // error 2 instead of reading outside the batch region.
+                bool bad = c >= (unsigned long long)B.n_slots * kSlotChunks;
+                if (!bad) {
+                    const Chunk q = B.chunks[c];
+                    bad = q.req < 0 || q.req >= B.n_slots || q.level < 0 || q.level >= kBL ||
+                          q.count <= 0 || q.level > B.req[q.req].L;
+                }
+                if (bad) {
+                    if (lane == 0) atomicExch(&B.ctl->error, 2);
+                    break;
+                }
+            }
+            {
                 // a chunk of a cancelled request is dropped unprocessed
                 const Chunk peek = B.chunks[c];
                 if (*(volatile int32_t *)&B.state[peek.req].status == 4) {
@@ -686,6 +715,35 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             valid = 1;
         }
         bool chunk_done = false;
+        if (ch.warp_pair) {
+            // One pair per warp: every lane holds the pair's state, lane j
+            // takes its event k + 1 + j; the pair's QoI is summed by lane
+            // (pair index mod 32).
+            for (;;) {
+                if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+                if (done[0]) {
+                    if (lane == (int)(st[0].pair_lo & 31u)) finish(0);
+                    done[0] = false;
+                }
+                if (!active[0]) {
+                    if (next >= end) {
+                        chunk_done = true;
+                        break;
+                    }
+                    if (pair_start<Real, 2, ModeRecipe<MODE>::value>(st[0], next, L, B.keys, coupled))
+                        done[0] = true;
+                    else
+                        active[0] = true;
+                    ++next;
+                    continue;
+                }
+                if (warp_pair_step<Real, ModeRecipe<MODE>::value>(st[0], L, B.keys, coupled, lane)) {
+                    active[0] = false;
+                    done[0] = true;
+                }
+                ++iters;
+            }
+        } else
         for (;;) {
             // the budget is checked before the refill, so a resumed slice runs
             // exactly the sequence an unsliced run would
@@ -870,6 +928,7 @@ static bool batch_cfg_ok(const mlkd_batch_config *c)
     if (c->substeps_per_launch < 0) return false;
     if (c->refill_min < 0 || c->refill_min > 32) return false;
     if (c->publish_wait_spins < 0) return false;
+    if (c->warp_pair_min_events < -1) return false;
     if (c->test_stall_queues < 0 || c->test_stall_queues > (1 << 20)) return false;
     if (c->max_requests < 1 || c->max_requests > 4096) return false;
     if (c->max_nbins < 0 || c->max_nbins > 256) return false;
@@ -1006,6 +1065,8 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->publish_spins = cfg->publish_wait_spins > 0 ? cfg->publish_wait_spins : kPublishSpins;
     B->dbg_req = -1;
     B->dbg_level = -1;
+    B->warp_pair_events = cfg->warp_pair_min_events > 0 ? cfg->warp_pair_min_events
+                        : cfg->warp_pair_min_events < 0 ? 0 : kWarpPairEvents;
     B->n_slots = n_slots;
     fill_keys(seed, &B->keys);
 }
@@ -1069,6 +1130,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
                              const mlkd_batch_config *cfg, cudaStream_t s, mlkd_result *results,
                              const BatchDebug *dbg = nullptr)
 {
+    NvtxRange nvtx_range("mlkd_estimate_batch");
     if (!ctx || !problems || n < 1 || !results || !batch_cfg_ok(cfg)) return MLKD_EINVAL;
     if (ctx->server) return MLKD_EBUSY;
     if (n > cfg->max_requests) return MLKD_EINVAL;
@@ -1079,7 +1141,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
     uint64_t seed = 0;
     for (int i = 0; i < n; ++i) {
         Derived d;
-        if (!validate(&problems[i], &d)) return MLKD_EINVAL;
+        if (!validate(&problems[i], &d) || d.per_level_only) return MLKD_EINVAL;
         if (!problems[i].n_fixed && (!(problems[i].tol > 0.0) || problems[i].n_warmup < 2)) return MLKD_EINVAL;
         if (problems[i].nbins > cfg->max_nbins) return MLKD_EINVAL;
         if (i == 0) {
@@ -1201,7 +1263,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         MLKD_CUDA(cudaMemcpyAsync(hh.data(), ctx->arena + BL.hist, hist_bytes, cudaMemcpyDeviceToHost, s));
     }
     MLKD_CUDA(cudaStreamSynchronize(s));
-    if (hctl.error) return MLKD_ETIMEDOUT;
+    if (hctl.error) return hctl.error == 1 ? MLKD_ETIMEDOUT : MLKD_EINTERNAL;
     if (cfg->use_graph) {
         ctx->launches += (unsigned long long)hctl.iterations;
         ctx->other_launches += 2ull * (unsigned long long)hctl.iterations;
@@ -1383,6 +1445,7 @@ static void server_loop(Server *S)
     cudaSetDevice(S->ctx->device);
     const int n = S->cfg.batch.max_requests;
     for (;;) {
+        NvtxRange nvtx_range("mlkd_server_iteration");
         int active = 0;
         {
             std::unique_lock<std::mutex> lk(S->mu);
@@ -1439,7 +1502,7 @@ static void server_loop(Server *S)
         S->stats.events = tail.events;
         S->stats.events_processed = tail.events_done;
         if (tail.error) {
-            S->error = MLKD_ETIMEDOUT;
+            S->error = tail.error == 1 ? MLKD_ETIMEDOUT : MLKD_EINTERNAL;
             S->stop = true;
             S->cv_done.notify_all();
             break;
@@ -1584,12 +1647,14 @@ mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems,
                                 const mlkd_batch_config *base, void *stream,
                                 mlkd_batch_config *best, double *seconds)
 {
+    NvtxRange nvtx_range("mlkd_autotune_batch");
     if (!ctx || !base || !best || !batch_cfg_ok(base)) return MLKD_EINVAL;
     if (ctx->server) return MLKD_EBUSY;
     cudaStream_t s = (cudaStream_t)stream;
     std::vector<mlkd_result> res(n);
     const int ppts[4] = {1, 2, 4, 8};
     const int slices[4] = {16, 64, 256, 0};
+    const int warps[2] = {0, -1};
     double best_t = 1e300;
     *best = *base;
     cudaEvent_t e0, e1;
@@ -1597,11 +1662,13 @@ mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems,
     MLKD_CUDA(cudaEventCreate(&e0));
     MLKD_CUDA(cudaEventCreate(&e1));
     mlkd_status st = MLKD_OK;
+    for (int w = 0; w < 2 && st == MLKD_OK; ++w)
     for (int a = 0; a < 4 && st == MLKD_OK; ++a) {
         for (int b = 0; b < 4 && st == MLKD_OK; ++b) {
             mlkd_batch_config c = *base;
             c.pairs_per_thread = ppts[a];
             c.substeps_per_launch = slices[b];
+            c.warp_pair_min_events = warps[w];
             c.use_graph = 1;
             for (int i = 0; i < n; ++i) res[i].density = nullptr;
             st = run_batch(ctx, problems, n, &c, s, res.data());       // warm (instantiates)
@@ -1615,7 +1682,7 @@ mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems,
             }
             float ms = 0.0f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (seconds) seconds[a * 4 + b] = ms * 1e-3;
+            if (seconds) seconds[w * 16 + a * 4 + b] = ms * 1e-3;
             if (ms * 1e-3 < best_t) {
                 best_t = ms * 1e-3;
                 *best = c;
@@ -1642,7 +1709,7 @@ mlkd_status mlkd_submit(mlkd_context *ctx, const mlkd_problem *problem, uint64_t
     Server *S = ctx->server;
     if (!S) return MLKD_EINVAL;
     Derived d;
-    if (!validate(problem, &d)) return MLKD_EINVAL;
+    if (!validate(problem, &d) || d.per_level_only) return MLKD_EINVAL;
     if (problem->precision != S->cfg.precision || problem->seed != S->cfg.seed) return MLKD_EINVAL;
     if (problem->nbins > S->cfg.batch.max_nbins) return MLKD_EINVAL;
     if (!problem->n_fixed && (!(problem->tol > 0.0) || problem->n_warmup < 2)) return MLKD_EINVAL;

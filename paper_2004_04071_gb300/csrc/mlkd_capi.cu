@@ -36,13 +36,25 @@ Layout arena_layout()
 bool validate(const mlkd_problem *p, Derived *d)
 {
     if (!p) return false;
-    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return false;
+    const bool het = p->background != MLKD_BG_HOMOGENEOUS;
+    if (p->background < MLKD_BG_HOMOGENEOUS || p->background > MLKD_BG_B2) return false;
+    if (het) {
+        if (!(p->bg_b > 0.0) || !std::isfinite(p->bg_b) || !(p->bg_a >= 0.0) || !std::isfinite(p->bg_a))
+            return false;
+        if (p->mu != 0.0) return false;
+    } else if (!(p->eps > 0.0) || !std::isfinite(p->eps)) {
+        return false;
+    }
     if (!(p->T > 0.0) || !(p->dt0 > 0.0) || !std::isfinite(p->T) || !std::isfinite(p->dt0)) return false;
     if (!std::isfinite(p->mu)) return false;
     if (p->M < 2 || p->M > 64) return false;
     if (p->L < 0 || p->L >= MLKD_MAX_LEVELS) return false;
-    if (p->qoi < MLKD_QOI_X2 || p->qoi > MLKD_QOI_DENSITY) return false;
-    if (p->init != MLKD_INIT_ORIGIN && p->init != MLKD_INIT_COSINE) return false;
+    if (p->qoi < MLKD_QOI_X2 || p->qoi > MLKD_QOI_X) return false;
+    if (p->init != MLKD_INIT_ORIGIN && p->init != MLKD_INIT_COSINE && p->init != MLKD_INIT_POINT) return false;
+    if (p->init == MLKD_INIT_POINT && !std::isfinite(p->x0)) return false;
+    if (p->qoi == MLKD_QOI_X && (p->init == MLKD_INIT_COSINE)) return false;
+    // the heterogeneous backgrounds start from a point (the paper's x0 = 1)
+    if (het && p->init == MLKD_INIT_COSINE) return false;
     if (p->precision < MLKD_PREC_FP64 || p->precision > MLKD_PREC_FP64_U24) return false;
     if (p->nbins < 0 || p->nbins > MLKD_MAX_BINS) return false;
     if (p->qoi == MLKD_QOI_DENSITY && p->nbins == 0) return false;
@@ -53,15 +65,22 @@ bool validate(const mlkd_problem *p, Derived *d)
     double nmax = n0;
     for (int l = 0; l < p->L; ++l) nmax *= p->M;
     const bool fp64_state = p->precision == MLKD_PREC_FP64 || p->precision == MLKD_PREC_FP64_U24;
-    const double cap = fp64_state ? 1073741824.0 : 16777216.0;
+    const double cap = fp64_state && !het ? 1073741824.0 : 16777216.0;
     if (nmax > cap) return false;
-    const double R = 1.0 / (p->eps * p->eps);
-    if (!std::isfinite(R) || R <= 0.0) return false;
-    d->R = R;
-    d->sigma = 1.0 / p->eps;
+    if (het) {
+        d->R = p->bg_b;
+        d->sigma = 1.0;
+    } else {
+        const double R = 1.0 / (p->eps * p->eps);
+        if (!std::isfinite(R) || R <= 0.0) return false;
+        d->R = R;
+        d->sigma = 1.0 / p->eps;
+    }
     d->mu = p->mu;
     d->n0 = (long long)n0;
     d->mode = p->precision;
+    d->background = p->background;
+    d->per_level_only = het || p->qoi == MLKD_QOI_X || p->init == MLKD_INIT_POINT;
     d->periodic = p->qoi == MLKD_QOI_X2_PERIODIC || p->init == MLKD_INIT_COSINE;
     if (d->periodic) {
         d->lo = 0.0;
@@ -128,7 +147,13 @@ void fill_launch(const mlkd_problem *p, const Derived &d, int j, uint64_t first,
     P->n = (int32_t)(d.n0 * Ml);
     P->M = d.Mj[j];
     P->periodic = d.periodic ? 1 : 0;
+    P->fkind = p->qoi == MLKD_QOI_X ? 2 : d.periodic ? 1 : 0;
     P->init = p->init;
+    P->x0 = p->init == MLKD_INIT_POINT ? p->x0 : 0.0;
+    P->background = d.background;
+    P->bg_b = p->bg_b;
+    P->bg_a_left = d.background == MLKD_BG_B1 ? p->bg_a : 0.0;
+    P->bg_a_right = p->bg_a;
     P->nbins = p->nbins;
     P->word2 = (uint32_t)level << 24;
     P->request = p->request;
@@ -172,10 +197,10 @@ namespace {
 // Grid of the pair kernel: enough warps for the pairs, at most one full wave
 // of resident blocks; each warp gets an equal contiguous chunk.
 mlkd_status choose_grid(mlkd_context *ctx, int mode, bool coupled, int nbins, uint64_t count,
-                        int *grid, unsigned long long *ppw)
+                        int *grid, unsigned long long *ppw, int background)
 {
     KernelInfo info;
-    if (pair_kernel_info(mode, coupled, nbins, &info) != cudaSuccess) return MLKD_ECUDA;
+    if (pair_kernel_info(mode, coupled, nbins, &info, background) != cudaSuccess) return MLKD_ECUDA;
     const int per_sm = std::max(1, info.blocks_per_sm);
     const long long wave = std::min<long long>((long long)ctx->sm_count * per_sm, kMaxBlocks);
     const unsigned long long warps_needed = (count + 31) / 32;
@@ -214,7 +239,7 @@ mlkd_status enqueue_level(mlkd_context *ctx, const mlkd_problem *p, const Derive
     fill_launch(p, d, level, first, count, &P);
     int grid = 1;
     unsigned long long ppw = 0;
-    mlkd_status st = choose_grid(ctx, d.mode, level > 0, p->nbins, count, &grid, &ppw);
+    mlkd_status st = choose_grid(ctx, d.mode, level > 0, p->nbins, count, &grid, &ppw, d.background);
     if (st != MLKD_OK) return st;
     P.pairs_per_warp = ppw;
     P.partials = ctx->partials;
@@ -272,6 +297,7 @@ const char *mlkd_status_string(int status)
     case MLKD_ETIMEDOUT: return "timed out";
     case MLKD_EBUSY: return "busy";
     case MLKD_ENOTFOUND: return "not found";
+    case MLKD_EINTERNAL: return "device consistency check failed";
     default: return "unknown status";
     }
 }
@@ -404,6 +430,7 @@ mlkd_status mlkd_level_select_opt(const double *V, const double *rho, const doub
 mlkd_status mlkd_level_pilot(mlkd_context *ctx, const mlkd_problem *problem, uint64_t n, void *stream,
                              double *V, double *rho, double *C)
 {
+    NvtxRange nvtx_range("mlkd_level_pilot");
     Derived d;
     if (!ctx || !problem || !V || !rho || !C || n < 2 || !validate(problem, &d)) return MLKD_EINVAL;
     if (problem->qoi == MLKD_QOI_DENSITY || problem->L < 1) return MLKD_EINVAL;
@@ -439,6 +466,7 @@ mlkd_status mlkd_level_pilot(mlkd_context *ctx, const mlkd_problem *problem, uin
 mlkd_status mlkd_level_warmup(mlkd_context *ctx, const mlkd_problem *problem, uint64_t n_warmup,
                               void *stream, double *V, double *Vd, int32_t *tau_out)
 {
+    NvtxRange nvtx_range("mlkd_level_warmup");
     Derived d;
     if (!ctx || !problem || !V || !Vd || !tau_out || n_warmup < 2 || !validate(problem, &d))
         return MLKD_EINVAL;
@@ -525,6 +553,7 @@ mlkd_status mlkd_run_level(mlkd_context *ctx, const mlkd_problem *problem, int l
                            uint64_t first_pair, uint64_t n_pairs, void *stream,
                            mlkd_level_stats *out, uint64_t *hist_out)
 {
+    NvtxRange nvtx_range("mlkd_run_level");
     Derived d;
     if (!ctx || !out || !validate(problem, &d)) return MLKD_EINVAL;
     if (level < 0 || level >= d.J) return MLKD_EINVAL;
@@ -553,6 +582,7 @@ mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int
                              uint64_t first_pair, uint64_t n_pairs, void *stream, double *xf,
                              double *xc, int32_t *kf, int32_t *kc)
 {
+    NvtxRange nvtx_range("mlkd_debug_pairs");
     Derived d;
     if (!ctx || !validate(problem, &d)) return MLKD_EINVAL;
     if (level < 0 || level >= d.J) return MLKD_EINVAL;
@@ -572,8 +602,9 @@ mlkd_status mlkd_debug_coarse_draws(mlkd_context *ctx, const mlkd_problem *probl
                                     void *stream, double *nu_t, double *E_t, double *chi_t,
                                     int32_t *count)
 {
+    NvtxRange nvtx_range("mlkd_debug_coarse_draws");
     Derived d;
-    if (!ctx || !validate(problem, &d)) return MLKD_EINVAL;
+    if (!ctx || !validate(problem, &d) || d.per_level_only) return MLKD_EINVAL;
     if (level < 1 || level >= d.J || per_pair < 1) return MLKD_EINVAL;
     if (!nu_t || !E_t || !chi_t || !count) return MLKD_EINVAL;
     if (n_pairs > (1ull << 31) / (unsigned long long)per_pair) return MLKD_EINVAL;
@@ -595,6 +626,7 @@ static mlkd_status estimate_impl(mlkd_context *ctx, const mlkd_problem *problem,
                                  const mlkd_result *resume, const uint64_t *hist_in, int max_rounds,
                                  void *stream, mlkd_result *out, uint64_t *hist_out)
 {
+    NvtxRange nvtx_range("mlkd_estimate");
     Derived d;
     if (!ctx || !out || !validate(problem, &d)) return MLKD_EINVAL;
     if (max_rounds < 0) return MLKD_EINVAL;
@@ -736,6 +768,7 @@ mlkd_status mlkd_estimate_resumable(mlkd_context *ctx, const mlkd_problem *probl
 mlkd_status mlkd_estimate_sequence(mlkd_context *ctx, const mlkd_problem *problem, int n_tol,
                                    const double *tols, void *stream, mlkd_result *results)
 {
+    NvtxRange nvtx_range("mlkd_estimate_sequence");
     Derived d;
     if (!ctx || !problem || !tols || !results || n_tol < 1 || !validate(problem, &d))
         return MLKD_EINVAL;
@@ -865,7 +898,7 @@ extern "C" mlkd_status mlkd_run_level_noalloc(const mlkd_problem *problem, int l
     int sms = 0;
     MLKD_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
     KernelInfo info;
-    MLKD_CUDA(pair_kernel_info(d.mode, level > 0, problem->nbins, &info));
+    MLKD_CUDA(pair_kernel_info(d.mode, level > 0, problem->nbins, &info, d.background));
     const long long wave = std::min<long long>((long long)sms * std::max(1, info.blocks_per_sm),
                                                MLKD_NOALLOC_MAX_BLOCKS);
     const unsigned long long warps_needed = (n_pairs + 31) / 32;

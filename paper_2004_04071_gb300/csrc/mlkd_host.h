@@ -9,10 +9,21 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mlkd_internal.h"
 #include "../../include/mlkd.h"
 
 namespace mlkd {
+
+// NVTX range over a host call (tracing; header-only NVTX, a no-op unless a
+// profiler or tracer is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 constexpr int kMaxBlocks = 4096;                  // grid cap of the pair kernel
 constexpr size_t kAlign = 256;
@@ -30,6 +41,8 @@ struct Derived {
     double R, sigma, mu;
     long long n0;          // T / dt0
     int mode;
+    int background;        // mlkd_background
+    bool per_level_only;   // a problem the batched and serving forms do not run
     bool periodic;
     double lo, hi, h;
     int J;                 // estimator levels

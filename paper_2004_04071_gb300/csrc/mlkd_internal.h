@@ -49,7 +49,10 @@ struct PairLaunch {
     int32_t nbins;             // 0: no histogram
     uint32_t word2;            // level << 24 (pair_hi xor'ed in per pair)
     uint32_t request;
-    uint32_t pad_;
+    int32_t fkind;             // F: 0 x^2, 1 (x mod 1)^2, 2 x
+    int32_t background;        // 0 homogeneous, 1 B1, 2 B2 (heterogeneous kernel)
+    double x0;                 // start of every path (init 2)
+    double bg_b, bg_a_left, bg_a_right;   // R(x) = b (1 + a_l max(1-x,0) + a_r max(x-1,0))
     PhiloxKeys keys;
     BgParams<double> bd;
     BgParams<float> bf;
@@ -65,7 +68,7 @@ struct KernelInfo {
 };
 
 // Kernel-variant occupancy (blocks per SM with kThreads threads).
-cudaError_t pair_kernel_info(int mode, bool coupled, int nbins, KernelInfo *out);
+cudaError_t pair_kernel_info(int mode, bool coupled, int nbins, KernelInfo *out, int background = 0);
 
 // Launches the pair kernel on `grid` blocks.
 cudaError_t launch_pair_kernel(int mode, bool coupled, const PairLaunch &p, int grid,

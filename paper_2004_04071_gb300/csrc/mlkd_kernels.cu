@@ -12,6 +12,7 @@
 // assignment depends only on the event counts, so results are reproducible.
 #include <cfloat>
 
+#include "mlkd_hetero.cuh"
 #include "mlkd_internal.h"
 #include "mlkd_pair.cuh"
 
@@ -26,11 +27,17 @@ template <> __device__ __forceinline__ const BgParams<double> &level_params<doub
 template <typename Real> struct MinBlocks { static constexpr int value = 8; };
 template <> struct MinBlocks<double> { static constexpr int value = 1; };
 
-template <typename Real, int MODE, bool COUPLED>
+// Pair state of the two physics: the homogeneous background (PHYS 0) and the
+// heterogeneous backgrounds B1/B2 of Sec. 5 (PHYS 1).
+template <typename Real, int PHYS> struct PhysState { typedef PairState<Real> type; };
+template <typename Real> struct PhysState<Real, 1> { typedef HetPairState<Real> type; };
+
+template <typename Real, int MODE, bool COUPLED, int PHYS>
 __global__ void __launch_bounds__(kThreads, MinBlocks<Real>::value)
 pair_kernel(const __grid_constant__ PairLaunch P)
 {
     constexpr int CPL = COUPLED ? 1 : 0;
+    constexpr int RECIPE = ModeRecipe<MODE>::value;
     extern __shared__ unsigned int s_hist[];          // [3][nbins]
     __shared__ double s_red[kWarpsPerBlock][kPartialWords];
 
@@ -51,9 +58,22 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     L.n = P.n;
     L.M = P.M;
     L.m_shift = (P.M & (P.M - 1)) == 0 ? __ffs(P.M) - 1 : -1;
-    L.init = P.init;
+    L.init = P.init == 1 ? 1 : 0;          // a point start is set after pair_start
     L.word2 = P.word2;
     L.request = P.request;
+    HetLevel<Real> H;
+    if constexpr (PHYS == 1) {
+        H.bg.b = (Real)P.bg_b;
+        H.bg.a_left = (Real)P.bg_a_left;
+        H.bg.a_right = (Real)P.bg_a_right;
+        H.bg.dt = bp.dt;
+        H.n = P.n;
+        H.M = P.M;
+        H.m_shift = L.m_shift;
+        H.x0 = (Real)P.x0;
+        H.word2 = P.word2;
+        H.request = P.request;
+    }
 
     Bins bins;
     bins.lo = P.lo;
@@ -78,7 +98,7 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     bool active = false;        // the lane's pair has events left
     bool done = false;          // the lane holds a finished pair not yet summed
     unsigned long long pair = 0;
-    PairState<Real> st;
+    typename PhysState<Real, PHYS>::type st;
     st.fresh = true;
     PairSums<MODE> mom;
     mom.zero();
@@ -86,8 +106,11 @@ pair_kernel(const __grid_constant__ PairLaunch P)
 
     // QoI, sums and histogram of the finished pair.
     auto finish_pair = [&]() {
-        pair_drift<Real, CPL>(st, L, COUPLED);
-        add_pair(mom, st.xf, st.xc, COUPLED, P.periodic != 0);
+        if constexpr (PHYS == 1)
+            het_pair_drift<Real>(st, H, COUPLED);
+        else
+            pair_drift<Real, CPL>(st, L, COUPLED);
+        add_pair_fk(mom, st.xf, st.xc, COUPLED, P.fkind);
         ev_f_sum += st.k;
         ev_c_sum += st.evc;
         if (nbins > 0) {
@@ -121,7 +144,17 @@ pair_kernel(const __grid_constant__ PairLaunch P)
                 const unsigned long long cand = next + rank;
                 if (!active && cand < w_end) {
                     pair = cand;
-                    if (pair_start<Real, CPL, ModeRecipe<MODE>::value>(st, cand, L, P.keys, COUPLED))
+                    bool none;
+                    if constexpr (PHYS == 1) {
+                        none = het_pair_start<Real, RECIPE>(st, cand, H, P.keys, COUPLED);
+                    } else {
+                        none = pair_start<Real, CPL, RECIPE>(st, cand, L, P.keys, COUPLED);
+                        if (P.init == 2) {
+                            st.xf = (Real)P.x0;
+                            st.xc = st.xf;
+                        }
+                    }
+                    if (none)
                         done = true;
                     else
                         active = true;
@@ -134,9 +167,16 @@ pair_kernel(const __grid_constant__ PairLaunch P)
             if (next >= w_end && !__any_sync(kFullMask, done)) break;
             continue;
         }
-        if (active && pair_event<Real, CPL, ModeRecipe<MODE>::value>(st, L, P.keys, COUPLED)) {
-            active = false;
-            done = true;
+        if (active) {
+            bool fin;
+            if constexpr (PHYS == 1)
+                fin = het_pair_event<Real, RECIPE>(st, H, P.keys, COUPLED);
+            else
+                fin = pair_event<Real, CPL, RECIPE>(st, L, P.keys, COUPLED);
+            if (fin) {
+                active = false;
+                done = true;
+            }
         }
     }
 
@@ -382,31 +422,37 @@ namespace {
 
 typedef void (*PairKernelFn)(const PairLaunch);
 
-PairKernelFn pick(int mode, bool coupled)
+template <int PHYS>
+PairKernelFn pick_phys(int mode, bool coupled)
 {
     switch (mode) {
     case kModeFP64:
-        return coupled ? pair_kernel<double, kModeFP64, true> : pair_kernel<double, kModeFP64, false>;
+        return coupled ? pair_kernel<double, kModeFP64, true, PHYS> : pair_kernel<double, kModeFP64, false, PHYS>;
     case kModeFP32DY64:
-        return coupled ? pair_kernel<float, kModeFP32DY64, true>
-                       : pair_kernel<float, kModeFP32DY64, false>;
+        return coupled ? pair_kernel<float, kModeFP32DY64, true, PHYS>
+                       : pair_kernel<float, kModeFP32DY64, false, PHYS>;
     case kModeFP64U24:
-        return coupled ? pair_kernel<double, kModeFP64U24, true>
-                       : pair_kernel<double, kModeFP64U24, false>;
+        return coupled ? pair_kernel<double, kModeFP64U24, true, PHYS>
+                       : pair_kernel<double, kModeFP64U24, false, PHYS>;
     default:
-        return coupled ? pair_kernel<float, kModeFP32Comp, true>
-                       : pair_kernel<float, kModeFP32Comp, false>;
+        return coupled ? pair_kernel<float, kModeFP32Comp, true, PHYS>
+                       : pair_kernel<float, kModeFP32Comp, false, PHYS>;
     }
+}
+
+PairKernelFn pick(int mode, bool coupled, int background)
+{
+    return background ? pick_phys<1>(mode, coupled) : pick_phys<0>(mode, coupled);
 }
 
 }  // namespace
 
-cudaError_t pair_kernel_info(int mode, bool coupled, int nbins, KernelInfo *out)
+cudaError_t pair_kernel_info(int mode, bool coupled, int nbins, KernelInfo *out, int background)
 {
     int blocks = 0;
     const size_t smem = (size_t)3 * nbins * sizeof(unsigned int);
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &blocks, (const void *)pick(mode, coupled), kThreads, smem);
+        &blocks, (const void *)pick(mode, coupled, background), kThreads, smem);
     out->blocks_per_sm = blocks;
     return e;
 }
@@ -415,7 +461,7 @@ cudaError_t launch_pair_kernel(int mode, bool coupled, const PairLaunch &p, int 
                                cudaStream_t stream)
 {
     const size_t smem = (size_t)3 * p.nbins * sizeof(unsigned int);
-    pick(mode, coupled)<<<grid, kThreads, smem, stream>>>(p);
+    pick(mode, coupled, p.background)<<<grid, kThreads, smem, stream>>>(p);
     return cudaGetLastError();
 }
 

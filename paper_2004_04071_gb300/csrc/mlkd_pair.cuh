@@ -298,6 +298,53 @@ __device__ __forceinline__ void add_pair(PairSums<kModeFP32Comp> &ps, float xf, 
     ps.q[5].add(Fc * Fc);
 }
 
+// Linear QoI F(x) = x (the position at T, the paper's test case): Y = x_f -
+// x_c.  fk selects F: 0 x^2, 1 (x mod 1)^2, 2 x.
+__device__ __forceinline__ void add_pair_linear(PairSums<kModeFP64> &ps, double xf, double xc, bool coupled)
+{
+    const double Fc = coupled ? xc : 0.0;
+    const double y = xf - Fc;
+    ps.v[0] += y;
+    ps.v[1] += y * y;
+    ps.v[2] += xf;
+    ps.v[3] += xf * xf;
+    ps.v[4] += Fc;
+    ps.v[5] += Fc * Fc;
+}
+
+__device__ __forceinline__ void add_pair_linear(PairSums<kModeFP32DY64> &ps, float xf, float xc, bool coupled)
+{
+    const float Fc = coupled ? xc : 0.0f;
+    const double y = (double)xf - (double)Fc;
+    ps.sy += y;
+    ps.sy2 += y * y;
+    ps.q[0].add(xf);
+    ps.q[1].add(xf * xf);
+    ps.q[2].add(Fc);
+    ps.q[3].add(Fc * Fc);
+}
+
+__device__ __forceinline__ void add_pair_linear(PairSums<kModeFP32Comp> &ps, float xf, float xc, bool coupled)
+{
+    const float Fc = coupled ? xc : 0.0f;
+    const float y = xf - Fc;
+    ps.q[0].add(y);
+    ps.q[1].add(y * y);
+    ps.q[2].add(xf);
+    ps.q[3].add(xf * xf);
+    ps.q[4].add(Fc);
+    ps.q[5].add(Fc * Fc);
+}
+
+template <typename Sums, typename Real>
+__device__ __forceinline__ void add_pair_fk(Sums &ps, Real xf, Real xc, bool coupled, int fk)
+{
+    if (fk == 2)
+        add_pair_linear(ps, xf, xc, coupled);
+    else
+        add_pair(ps, xf, xc, coupled, fk == 1);
+}
+
 // Histogram bin: floor((x - lo)/h) inside [lo, hi), else -1; periodic
 // positions are first wrapped into [0, 1).  FP64 state divides in FP64; FP32
 // state decides its bins in FP32.

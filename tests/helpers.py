@@ -2,12 +2,15 @@
 import numpy as np
 
 ORACLE_KEYS = ("eps", "T", "dt0", "M", "L", "qoi", "init", "nbins", "lo", "hi", "tol",
-               "n_warmup", "seed", "request", "mu")
+               "n_warmup", "seed", "request", "mu", "x0")
+BG_KEYS = ("background", "bg_a", "bg_b")
 
 
 def oracle_problem(orc, d, recipe=None, **over):
     d = dict(d, **over)
     kw = {k: d[k] for k in ORACLE_KEYS if k in d}
+    if d.get("background"):
+        kw["background"], kw["a"], kw["b"] = d["background"], d.get("bg_a", 0.0), d["bg_b"]
     if "n_fixed" in d and d["n_fixed"] is not None:
         kw["n_fixed"] = list(d["n_fixed"])
     if recipe is not None:
@@ -19,7 +22,7 @@ def oracle_problem(orc, d, recipe=None, **over):
 
 def gpu_problem(mk, d, precision=0, **over):
     d = dict(d, **over)
-    kw = {k: d[k] for k in ORACLE_KEYS if k in d}
+    kw = {k: d[k] for k in ORACLE_KEYS + BG_KEYS if k in d}
     if "n_fixed" in d:
         kw["n_fixed"] = d["n_fixed"]
     if d.get("level_set"):

@@ -56,10 +56,10 @@ def test_binding_names_match_header(built):
 def test_struct_layouts_match_header(built):
     import paper_2004_04071_gb300 as mk
     # mlkd_problem: 4 doubles, 6 int32, 3 doubles, 2 x 32-bit, u64, pointer, 2 int32, pointer
-    assert ctypes.sizeof(mk.Problem) == 4 * 8 + 6 * 4 + 3 * 8 + 8 + 8 + 8 + 8 + 8
+    assert ctypes.sizeof(mk.Problem) == 4 * 8 + 6 * 4 + 3 * 8 + 8 + 8 + 8 + 8 + 8 + 8 + 3 * 8
     assert ctypes.sizeof(mk.LevelStats) == 8 + 6 * 8 + 2 * 8
-    # mlkd_batch_config: 8 int32
-    assert ctypes.sizeof(mk.BatchConfig) == 8 * 4
+    # mlkd_batch_config: 9 int32
+    assert ctypes.sizeof(mk.BatchConfig) == 9 * 4
     assert mk.lib().mlkd_abi_version() == mk.ABI_VERSION
 
 

@@ -174,8 +174,10 @@ def test_autotune_picks_from_grid(mk, ctx):
     best, secs = ctx.autotune_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))
     assert best.pairs_per_thread in (1, 2, 4, 8)
     assert best.substeps_per_launch in (16, 64, 256, 0)
-    assert all(s > 0 for s in secs)
-    assert min(secs) == pytest.approx(secs[[1, 2, 4, 8].index(best.pairs_per_thread) * 4 +
+    assert best.warp_pair_min_events in (0, -1)
+    assert len(secs) == 32 and all(s > 0 for s in secs)
+    assert min(secs) == pytest.approx(secs[[0, -1].index(best.warp_pair_min_events) * 16 +
+                                          [1, 2, 4, 8].index(best.pairs_per_thread) * 4 +
                                           [16, 64, 256, 0].index(best.substeps_per_launch)])
 
 
@@ -223,13 +225,21 @@ def test_round_cut_by_chunk_capacity_continues(mk, ctx):
     d = dict(eps=1e-3, T=1.0, dt0=0.5, M=2, L=9, qoi=1, init=1, nbins=0, seed=7, request=3,
              n_fixed=[1000] * 9 + [600_000])
     p = gpu_problem(mk, d, precision=mk.PREC_FP32_DY64)
-    (b,) = ctx.estimate_batch([p], mk.batch_config(max_requests=64, max_nbins=128))
     r = ctx.estimate(p)
+    # one pair per lane, as the per-level form: sums agree to FP32 contraction
+    (b,) = ctx.estimate_batch([p], mk.batch_config(max_requests=64, max_nbins=128,
+                                                   warp_pair_min_events=-1))
     assert [lv["n"] for lv in b.levels] == d["n_fixed"] == [lv["n"] for lv in r.levels]
     for lb, lr in zip(b.levels, r.levels):
         assert lb["events_f"] == lr["events_f"] and lb["events_c"] == lr["events_c"]
         assert lb["sy"] == pytest.approx(lr["sy"], rel=1e-9, abs=1e-9)
     assert b.estimate == pytest.approx(r.estimate, rel=1e-9, abs=1e-12)
+    # the deep level one pair per warp (the default): the same counts
+    (w,) = ctx.estimate_batch([p], mk.batch_config(max_requests=64, max_nbins=128))
+    assert [lv["n"] for lv in w.levels] == d["n_fixed"]
+    for lw, lr in zip(w.levels, r.levels):
+        assert abs(lw["events_f"] - lr["events_f"]) <= 1e-6 * lr["events_f"] + 2
+        assert abs(lw["events_c"] - lr["events_c"]) <= 1e-6 * lr["events_c"] + 2
 
 
 def test_full_size_periodic_step_matches_per_level_form(mk):
@@ -241,7 +251,7 @@ def test_full_size_periodic_step_matches_per_level_form(mk):
     densities equal to FP32 rounding (separate compilations may round a
     flight's floor differently for a rare pair)."""
     cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=0, use_graph=1, max_requests=16,
-                          max_nbins=128)
+                          max_nbins=128, warp_pair_min_events=-1)
     ctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
     try:
         dicts = [dict(W.periodic_problem(e, seed=0, tol=1e-3), request=i)
@@ -333,3 +343,69 @@ def test_publication_wait_runs_out_and_the_context_recovers(mk, ctx, use_graph):
     for a, b, d in zip(after, fresh, ds):
         assert a.estimate == b.estimate and a.variance == b.variance
         assert a.variance <= d["tol"] ** 2 / 2 * (1 + 1e-6)
+
+
+WARP_PAIR_CASES = {
+    # long diffusive chains (the deep levels of the periodic benchmark)
+    "deep_diffusive": (dict(eps=1e-3, T=1.0, dt0=0.5, M=2, L=9, qoi=1, init=1, nbins=64, lo=0.0,
+                            hi=1.0, seed=2, tol=0.0), 9, 300),
+    # every regime through the warp path (threshold 1 event): kinetic,
+    # mixed, drift, M = 3 and 8, free space with bins, single paths
+    "kinetic": (dict(eps=2.0, T=1.0, dt0=0.25, M=2, L=3, qoi=0, init=0, nbins=0, seed=5, tol=0.0), 3, 2000),
+    "mixed_periodic": (dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=6, qoi=1, init=1, nbins=32, lo=0.0,
+                            hi=1.0, seed=21, tol=0.0), 6, 2000),
+    "M3_drift": (dict(eps=0.2, T=0.6, dt0=0.2, M=3, L=2, qoi=0, init=0, nbins=12, lo=-3.0, hi=3.0,
+                      seed=17, mu=0.4, tol=0.0), 2, 2000),
+    "M8": (dict(eps=0.05, T=1.0, dt0=0.5, M=8, L=2, qoi=0, init=0, nbins=0, seed=13, tol=0.0), 2, 2000),
+    "single_paths": (dict(eps=0.05, T=1.0, dt0=0.5, M=2, L=3, qoi=0, init=0, nbins=0, seed=3, tol=0.0), 0, 2000),
+}
+
+
+@pytest.mark.parametrize("name", sorted(WARP_PAIR_CASES))
+def test_warp_pair_form_matches_oracle_fp64(orc, mk, ctx, name):
+    """Pairs run one per warp (32 events per step: step counts by prefix
+    sum, coarse windows by their step index, window sums by segmented scan)
+    give the oracle's pairs: the same fine and coarse event counts and
+    positions within 1e-12 (the positions' FP sums are formed in another
+    order).  The deep-diffusive case uses the default threshold (its pairs
+    average more than 1024 events); the others force every level through
+    the warp path."""
+    d, level, n = WARP_PAIR_CASES[name]
+    thr = 0 if name == "deep_diffusive" else 1
+    nf = [n] * (d["L"] + 1)
+    p = gpu_problem(mk, d, precision=mk.PREC_FP64, n_fixed=nf)
+    cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=0, max_requests=64, max_nbins=128,
+                          warp_pair_min_events=thr)
+    _, xf, xc, kf, kc = ctx.debug_batch_pairs(p, cfg, level)
+    xf_o, xc_o, kf_o, kc_o = orc.pairs(oracle_problem(orc, d), level, 0, n, threads=16)
+    assert np.array_equal(kf, kf_o) and np.array_equal(kc, kc_o)
+    for g, o in ((xf, xf_o), (xc, xc_o)):
+        assert np.all(np.abs(g - o) <= 1e-12 * np.maximum(1.0, np.abs(o))), np.max(np.abs(g - o))
+
+
+def test_warp_pair_form_fp32_and_slices(orc, mk, ctx):
+    """FP32 pairs of the warp path against the oracle on the 24-bit stream
+    within the FP32 per-pair bound; and sliced launches (16 steps per
+    launch, so pairs are stored and resumed mid-chain) equal the unsliced
+    run bit for bit."""
+    import fp32_bounds as B
+    d, level, n = WARP_PAIR_CASES["deep_diffusive"]
+    nf = [n] * (d["L"] + 1)
+    p = gpu_problem(mk, d, precision=mk.PREC_FP32_COMP, n_fixed=nf)
+    full = mk.batch_config(pairs_per_thread=1, substeps_per_launch=0, max_requests=64, max_nbins=128)
+    r0, xf, xc, kf, kc = ctx.debug_batch_pairs(p, full, level)
+    xf_o, xc_o, kf_o, kc_o = orc.pairs(oracle_problem(orc, d, recipe=orc.RECIPE_24), level, 0, n,
+                                       threads=16)
+    same = (kf == kf_o) & (kc == kc_o)
+    assert (~same).sum() <= max(1, 1e-3 * n)
+    ev = kf_o + kc_o
+    for g, o in ((xf, xf_o), (xc, xc_o)):
+        assert np.all(np.abs(g - o)[same] <= B.pair_delta(o, ev)[same])
+    for ppt, sl in ((1, 16), (2, 64)):
+        cfg = mk.batch_config(pairs_per_thread=ppt, substeps_per_launch=sl, max_requests=64,
+                              max_nbins=128)
+        r1, xf1, xc1, kf1, kc1 = ctx.debug_batch_pairs(p, cfg, level)
+        if ppt == 1:
+            assert np.array_equal(xf1, xf) and np.array_equal(xc1, xc)
+            assert r1.estimate == r0.estimate
+        assert np.array_equal(kf1, kf) and np.array_equal(kc1, kc)
