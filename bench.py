@@ -49,7 +49,8 @@ INST_PER_COARSE_EVENT = 50.0
 # kernel, with a hash of the kernel sources they were taken on; the bench
 # line reports them only while the sources still have that hash.
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "batch_pair_kernel_periodic.md")
-KERNEL_SOURCES = ("mlkd_batch.cu", "mlkd_pair.cuh", "mlkd_device.cuh", "mlkd_internal.h")
+KERNEL_SOURCES = ("mlkd_batch.cu", "mlkd_pair.cuh", "mlkd_warp_pair.cuh", "mlkd_device.cuh",
+                  "mlkd_internal.h")
 TTT_RUNS = 11
 # N_l of the benchmark's adaptive pilot at tol 1e-3 (eps = 1, 0.1, 1e-3; as
 # measured on GB300 with the FP32_COMP batched form), for the fixed ncu case.
