@@ -335,8 +335,8 @@ typedef struct {
     int32_t use_graph;           /* 1: one CUDA graph with a device-side loop                 */
     int32_t max_requests;        /* request slots of the batch region (<= 4096)             */
     int32_t max_nbins;           /* histogram bins per request (<= 256)                      */
-    int32_t refill_min;          /* a warp sums and restarts finished pairs once this many of
-                                    its lanes are idle (1..32; 0: library default)           */
+    int32_t refill_min;          /* a warp hands started pairs to its idle lanes once this
+                                    many are idle (1..32; 0: library default, 2)             */
     int32_t publish_wait_spins;  /* bound of the device wait for earlier reservations of a
                                     work queue to be published (0: library default, 2^22);
                                     a wait that runs out ends the call with MLKD_ETIMEDOUT   */

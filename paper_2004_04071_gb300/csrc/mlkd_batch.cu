@@ -151,6 +151,9 @@ struct BatchLaunch {
 };
 
 constexpr int kMaxPPT = 8;
+// Idle lanes a warp gathers before it hands them started pairs from its pool
+// (measured on the periodic benchmark: 2 and 3 best, 1 and 4 within 1 %).
+constexpr int kBatchRefillMin = 2;
 constexpr size_t kMaxLanes = 256ull * 16 * kThreads;   // lane slots: up to 256 SMs x 16 blocks
 
 // Lane words of T, stored word-major so that a warp's 32 lanes write 32
@@ -174,9 +177,34 @@ template <typename T> __device__ __forceinline__ void get_words(T &v, const uint
     w += (int)(sizeof(T) / 4);
 }
 
+// Per-warp pools of the one-pair-per-lane loop.  New pairs are started 32 at
+// a time in one pass with every lane busy (Philox block 0, the initial
+// position, the first flight) and handed out as lanes fall idle; finished
+// pairs are queued and summed 32 at a time.  A lane whose pair reaches T thus
+// takes a new one at once, and the start and summation paths no longer run
+// for only the few lanes that finished in the same iteration.
+template <typename Real> struct StartPool {
+    Real x0[32], v0[32], q0[32];
+    int32_t off[32];                 // pair index - the chunk's first pair index
+};
+template <typename Real> struct FinishPool {
+    Real xf[64], xc[64];             // both paths at T
+    uint32_t kf[64], kc[64];         // fine and coarse events
+};
+// A lane's share of its warp's pools in a stored slice.
+template <typename Real> struct PoolWords {
+    Real x0, v0, q0;
+    int32_t off;
+    Real xf[2], xc[2];
+    uint32_t kf[2], kc[2];
+    uint32_t counts;                 // entries: started | handed out << 8 | finished << 16
+    uint32_t pad_;
+};
+
 template <typename Real, int MODE, int PPT> constexpr int lane_words()
 {
-    return (int)((PPT * sizeof(PairState<Real>) + sizeof(PairSums<MODE>) + 2 * sizeof(unsigned long long)) / 4) + 1;
+    return (int)((PPT * sizeof(PairState<Real>) + sizeof(PairSums<MODE>) + 2 * sizeof(unsigned long long) +
+                  sizeof(PoolWords<Real>)) / 4) + 1;
 }
 
 // Blocks per SM of the batched pair kernel by pair states per lane.  Five
@@ -521,12 +549,35 @@ template <int MODE> struct LaneSums {
     uint32_t pad_[2];
 };
 
+// A warp's bookkeeping of its current chunk and pools (all warp-uniform).  It
+// lives in shared memory and is read (volatile) where it is used, so that the
+// registers of the event loop hold only pair states and level constants.
+struct WarpCtx {
+    unsigned long long c;            // chunk id
+    unsigned long long first, end;   // the chunk's pair range
+    unsigned long long next;         // next pair of the chunk to start
+    double blo, bhi, bh;             // histogram range and bin width (FP64 state)
+    float blo_f, bhi_f, binv_h_f;    // the same for FP32 state
+    int32_t req, level, warp_pair, nbins, per;
+    int32_t sp_n, sp_i, fp_n;        // start pool: started, handed out; finish pool: queued
+};
+
+__device__ __forceinline__ unsigned lanemask_lt()
+{
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
 template <typename Real, int MODE, int PPT>
 __global__ void __launch_bounds__(kThreads, (BatchMinBlocks<Real, PPT>::value))
 batch_pair_kernel(const __grid_constant__ BatchLaunch B)
 {
     extern __shared__ unsigned int s_hist_all[];        // [warps][3 * max_nbins]
     __shared__ LaneSums<MODE> s_sums[kThreads];
+    __shared__ StartPool<Real> s_start[kWarpsPerBlock];
+    __shared__ FinishPool<Real> s_finish[kWarpsPerBlock];
+    __shared__ WarpCtx s_ctx[kWarpsPerBlock];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const size_t gw = (size_t)blockIdx.x * kWarpsPerBlock + warp;
@@ -536,18 +587,21 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     WarpHdr *hdr = B.hdr + gw;
 
     int valid = hdr->valid;
-    unsigned long long c = hdr->c;
-    unsigned long long next = hdr->next;                 // warp-uniform
     int iters = 0;
     int idle = 0;
+    StartPool<Real> &SP = s_start[warp];
+    FinishPool<Real> &FP = s_finish[warp];
+    // warp-uniform bookkeeping, read from shared memory where it is needed
+    volatile WarpCtx &X = s_ctx[warp];
+    X.c = hdr->c;
+    X.next = hdr->next;
+    X.sp_n = 0;
+    X.sp_i = 0;
+    X.fp_n = 0;
+    __syncwarp();
 
-    Chunk ch;
-    const ReqDesc *D = nullptr;
     LevelCtx<Real> L;
-    Bins bins;
-    bool coupled = false, per = false;
-    int nbins = 0;
-    unsigned long long end = 0;
+    bool coupled = false;
     PairState<Real> st[PPT];
     bool active[PPT];           // the lane's pair has events left
     bool done[PPT];             // the lane holds a pair that reached T but is not yet summed
@@ -556,12 +610,19 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     unsigned long long &ev_c_sum = s_sums[threadIdx.x].ev_c;
 
     auto load_chunk = [&]() {
-        ch = B.chunks[c];
-        D = &B.req[ch.req];
+        const Chunk ch = B.chunks[X.c];
+        const ReqDesc *D = &B.req[ch.req];
         const int level = ch.level;
+        const int nbins = D->nbins;
         coupled = level > 0;
-        per = D->periodic != 0;
-        nbins = D->nbins;
+        __syncwarp();
+        X.req = ch.req;
+        X.level = level;
+        X.first = ch.first;
+        X.end = ch.first + (unsigned long long)ch.count;
+        X.warp_pair = ch.warp_pair;
+        X.nbins = nbins;
+        X.per = D->periodic != 0;
         {
             const BgParams<Real> &bp = req_params<Real>(*D, level);
             L.bg.R = bp.R;
@@ -578,23 +639,21 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             L.init = D->init;
             L.word2 = (uint32_t)D->level_of[level] << 24;
             L.request = D->request;
-            bins.lo = D->bd[level].lo;
-            bins.hi = D->bd[level].hi;
-            bins.h = D->h;
-            bins.lo_f = D->bf[level].lo;
-            bins.hi_f = D->bf[level].hi;
-            bins.inv_h_f = D->bf[level].inv_h;
-            bins.nbins = nbins;
-            bins.periodic = per;
+            X.blo = D->bd[level].lo;
+            X.bhi = D->bd[level].hi;
+            X.bh = D->h;
+            X.blo_f = D->bf[level].lo;
+            X.bhi_f = D->bf[level].hi;
+            X.binv_h_f = D->bf[level].inv_h;
         }
-        end = ch.first + (unsigned long long)ch.count;
         for (int i = lane; i < 3 * nbins; i += 32) wh[i] = 0u;
         __syncwarp();
     };
     auto flush_hist = [&]() {
         __syncwarp();
+        const int nbins = X.nbins;
         if (nbins > 0) {
-            unsigned long long *gh = B.hist + ((size_t)ch.req * kBL + ch.level) * 3 * B.max_nbins;
+            unsigned long long *gh = B.hist + ((size_t)X.req * kBL + X.level) * 3 * B.max_nbins;
             for (int i = lane; i < 3 * nbins; i += 32) {
                 const unsigned int v = wh[i];
                 if (v) atomicAdd(&gh[i], (unsigned long long)v);
@@ -602,31 +661,162 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         }
         __syncwarp();
     };
-    auto finish = [&](int j) {
-        pair_drift<Real, 2>(st[j], L, coupled);
-        add_pair(mom, st[j].xf, st[j].xc, coupled, per);
-        ev_f_sum += st[j].k;
-        ev_c_sum += st[j].evc;
+    // the sums, event counts and histogram counts of one pair at T
+    auto account = [&](Real xf, Real xc, uint32_t kf, uint32_t kc) {
+        add_pair(mom, xf, xc, coupled, X.per != 0);
+        ev_f_sum += kf;
+        ev_c_sum += kc;
+        const int nbins = X.nbins;
         if (nbins > 0) {
-            const int bf = bins(st[j].xf);
+            Bins bins;
+            bins.lo = X.blo;
+            bins.hi = X.bhi;
+            bins.h = X.bh;
+            bins.lo_f = X.blo_f;
+            bins.hi_f = X.bhi_f;
+            bins.inv_h_f = X.binv_h_f;
+            bins.nbins = nbins;
+            bins.periodic = X.per != 0;
+            const int bf = bins(xf);
             if (bf >= 0) atomicAdd(&wh[bf], 1u);
             if (coupled) {
-                const int bc = bins(st[j].xc);
+                const int bc = bins(xc);
                 if (bc >= 0) atomicAdd(&wh[nbins + bc], 1u);
                 if (bc >= 0 && bc == bf) atomicAdd(&wh[2 * nbins + bf], 1u);
             }
         }
-        if (B.dbg_xf && ch.req == B.dbg_req && ch.level == B.dbg_level) {
-            // validation readout: this pair's final state, by its pair index
-            const unsigned long long p = ((unsigned long long)(st[j].word2 ^ L.word2) << 32) | st[j].pair_lo;
-            if (p < B.dbg_n) {
-                B.dbg_xf[p] = (double)st[j].xf;
-                B.dbg_xc[p] = coupled ? (double)st[j].xc : 0.0;
-                B.dbg_kf[p] = (int32_t)st[j].k;
-                B.dbg_kc[p] = (int32_t)st[j].evc;
-            }
+    };
+    // validation readout: one pair's final state, by its pair index
+    auto dbg_record = [&](unsigned long long p, Real xf, Real xc, uint32_t kf, uint32_t kc) {
+        if (B.dbg_xf && X.req == B.dbg_req && X.level == B.dbg_level && p < B.dbg_n) {
+            B.dbg_xf[p] = (double)xf;
+            B.dbg_xc[p] = coupled ? (double)xc : 0.0;
+            B.dbg_kf[p] = (int32_t)kf;
+            B.dbg_kc[p] = (int32_t)kc;
         }
+    };
+    auto pair_index = [&](const PairState<Real> &q) {
+        return ((unsigned long long)(q.word2 ^ L.word2) << 32) | q.pair_lo;
+    };
+    auto finish = [&](int j) {
+        pair_drift<Real, 2>(st[j], L, coupled);
+        const Real xc = coupled ? st[j].xc : Real(0);
+        account(st[j].xf, xc, st[j].k, st[j].evc);
+        dbg_record(pair_index(st[j]), st[j].xf, xc, st[j].k, st[j].evc);
         done[j] = false;
+    };
+    // Sum the first cnt entries of the finish pool (lane i takes entry i) and
+    // move the rest to the front.  All lanes call it.
+    auto fp_process = [&](int cnt) {
+        __syncwarp();
+        if (lane < cnt) account(FP.xf[lane], FP.xc[lane], FP.kf[lane], FP.kc[lane]);
+        const int rest = X.fp_n - cnt;
+        Real a = Real(0), b = Real(0);
+        uint32_t ka = 0u, kb = 0u;
+        if (lane < rest) {
+            a = FP.xf[cnt + lane];
+            b = FP.xc[cnt + lane];
+            ka = FP.kf[cnt + lane];
+            kb = FP.kc[cnt + lane];
+        }
+        __syncwarp();
+        if (lane < rest) {
+            FP.xf[lane] = a;
+            FP.xc[lane] = b;
+            FP.kf[lane] = ka;
+            FP.kc[lane] = kb;
+        }
+        X.fp_n = rest;
+        __syncwarp();
+    };
+    // Queue the pairs of the lanes with f set, in lane order; sum a full
+    // pool of 32.  All lanes call it.
+    auto fp_push = [&](bool f, Real xf, Real xc, uint32_t kf, uint32_t kc) {
+        const unsigned m = __ballot_sync(kFullMask, f);
+        const int n0 = X.fp_n;
+        if (f) {
+            const int i = n0 + __popc(m & lanemask_lt());
+            FP.xf[i] = xf;
+            FP.xc[i] = xc;
+            FP.kf[i] = kf;
+            FP.kc[i] = kc;
+        }
+        __syncwarp();
+        X.fp_n = n0 + __popc(m);
+        __syncwarp();
+        if (n0 + __popc(m) >= 32) fp_process(32);
+    };
+    // Start the next min(32, end - next) pairs of the chunk, one per lane.  A
+    // pair with no collision before T is finished at once (both paths drift
+    // to T); the others go to the start pool in pair order.  All lanes call
+    // it, with the start pool empty.
+    auto refill = [&]() {
+        __syncwarp();
+        const unsigned long long nx = X.next, first = X.first;
+        const unsigned long long rem = X.end - nx;
+        const int nav = rem < 32ull ? (int)rem : 32;
+        const unsigned long long pr = nx + (unsigned long long)lane;
+        const bool have = lane < nav;
+        Real x0 = Real(0), v0 = Real(0), q0 = Real(0);
+        if (have) pair_start_values<Real, ModeRecipe<MODE>::value>(x0, v0, q0, pr, L, B.keys);
+        const bool dead = have && !(q0 < (Real)L.n);
+        Real xT = Real(0);
+        if (dead) {
+            xT = x0 + v0 * ((Real)L.n * L.bg.dt);          // pair_drift from t = 0
+            dbg_record(pr, xT, xT, 0u, 0u);
+        }
+        fp_push(dead, xT, coupled ? xT : Real(0), 0u, 0u);
+        const bool live = have && !dead;
+        const unsigned lm = __ballot_sync(kFullMask, live);
+        if (live) {
+            const int i = __popc(lm & lanemask_lt());
+            SP.x0[i] = x0;
+            SP.v0[i] = v0;
+            SP.q0[i] = q0;
+            SP.off[i] = (int32_t)(pr - first);
+        }
+        __syncwarp();
+        X.sp_n = __popc(lm);
+        X.sp_i = 0;
+        X.next = nx + (unsigned long long)nav;
+        __syncwarp();
+    };
+    auto put_pools = [&](int &w) {
+        PoolWords<Real> pw;
+        pw.x0 = SP.x0[lane];
+        pw.v0 = SP.v0[lane];
+        pw.q0 = SP.q0[lane];
+        pw.off = SP.off[lane];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            pw.xf[h] = FP.xf[32 * h + lane];
+            pw.xc[h] = FP.xc[32 * h + lane];
+            pw.kf[h] = FP.kf[32 * h + lane];
+            pw.kc[h] = FP.kc[32 * h + lane];
+        }
+        pw.counts = (uint32_t)X.sp_n | ((uint32_t)X.sp_i << 8) | ((uint32_t)X.fp_n << 16);
+        pw.pad_ = 0u;
+        put_words(pw, lw, stride, w);
+    };
+    auto get_pools = [&](int &w) {
+        PoolWords<Real> pw;
+        get_words(pw, lw, stride, w);
+        SP.x0[lane] = pw.x0;
+        SP.v0[lane] = pw.v0;
+        SP.q0[lane] = pw.q0;
+        SP.off[lane] = pw.off;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            FP.xf[32 * h + lane] = pw.xf[h];
+            FP.xc[32 * h + lane] = pw.xc[h];
+            FP.kf[32 * h + lane] = pw.kf[h];
+            FP.kc[32 * h + lane] = pw.kc[h];
+        }
+        __syncwarp();
+        X.sp_n = (int)(pw.counts & 0xffu);
+        X.sp_i = (int)((pw.counts >> 8) & 0xffu);
+        X.fp_n = (int)((pw.counts >> 16) & 0xffu);
+        __syncwarp();
     };
 
     if (valid) {                                      // resume the stored chunk
@@ -644,6 +834,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             active[j] = (bits >> j) & 1u;
             done[j] = (bits >> (kMaxPPT + j)) & 1u;
         }
+        get_pools(w);
     }
 
     for (;;) {
@@ -677,7 +868,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                 continue;
             }
             idle = 0;
-            c = __shfl_sync(kFullMask, cn, 0);
+            const unsigned long long c = __shfl_sync(kFullMask, cn, 0);
             {
                 // Consistency checks of the claimed id and its descriptor
                 // (cheap, once per chunk): a failure stops the loop with
@@ -701,8 +892,14 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                     continue;
                 }
             }
+            X.c = c;
+            __syncwarp();
             load_chunk();
-            next = ch.first;
+            X.next = X.first;
+            X.sp_n = 0;
+            X.sp_i = 0;
+            X.fp_n = 0;
+            __syncwarp();
             mom.zero();
             ev_f_sum = 0;
             ev_c_sum = 0;
@@ -715,7 +912,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             valid = 1;
         }
         bool chunk_done = false;
-        if (ch.warp_pair) {
+        if (X.warp_pair) {
             // One pair per warp: every lane holds the pair's state, lane j
             // takes its event k + 1 + j; the pair's QoI is summed by lane
             // (pair index mod 32).
@@ -726,15 +923,18 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                     done[0] = false;
                 }
                 if (!active[0]) {
-                    if (next >= end) {
+                    const unsigned long long nx = X.next;
+                    if (nx >= X.end) {
                         chunk_done = true;
                         break;
                     }
-                    if (pair_start<Real, 2, ModeRecipe<MODE>::value>(st[0], next, L, B.keys, coupled))
+                    if (pair_start<Real, 2, ModeRecipe<MODE>::value>(st[0], nx, L, B.keys, coupled))
                         done[0] = true;
                     else
                         active[0] = true;
-                    ++next;
+                    __syncwarp();
+                    X.next = nx + 1;
+                    __syncwarp();
                     continue;
                 }
                 if (warp_pair_step<Real, ModeRecipe<MODE>::value>(st[0], L, B.keys, coupled, lane)) {
@@ -745,52 +945,76 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             }
         } else
         for (;;) {
-            // the budget is checked before the refill, so a resumed slice runs
-            // exactly the sequence an unsliced run would
+            // the budget is checked before the pools are touched, so a
+            // resumed slice runs exactly the sequence an unsliced run would
             if (B.slice_iters > 0 && iters >= B.slice_iters) break;
-            // Lanes whose pair reached T wait, idle, until refill_min of
-            // them (or the whole warp) can be summed and restarted in one
-            // pass: the summation and the start of a pair then run once for
-            // many lanes instead of once per finishing lane.
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
-                const unsigned idle = __ballot_sync(kFullMask, !active[j]);
-                if (idle != 0u && (__popc(idle) >= B.refill_min || idle == kFullMask)) {
-                    if (done[j]) finish(j);
-                    if (next < end) {
-                        const unsigned rank = __popc(idle & ((1u << lane) - 1u));
-                        const unsigned long long cand = next + rank;
-                        if (!active[j] && cand < end) {
-                            if (pair_start<Real, 2, ModeRecipe<MODE>::value>(st[j], cand, L, B.keys, coupled))
-                                done[j] = true;
-                            else
-                                active[j] = true;
+                // pairs that reached T in the last iteration: to the finish pool
+                if (__any_sync(kFullMask, done[j])) {
+                    Real xf = Real(0), xc = Real(0);
+                    if (done[j]) {
+                        pair_drift<Real, 2>(st[j], L, coupled);
+                        xf = st[j].xf;
+                        xc = coupled ? st[j].xc : Real(0);
+                        dbg_record(pair_index(st[j]), xf, xc, st[j].k, st[j].evc);
+                    }
+                    fp_push(done[j], xf, xc, st[j].k, st[j].evc);
+                    done[j] = false;
+                }
+                // idle lanes take started pairs, in lane order, once refill_min
+                // of them are idle (or all); the pool is refilled from the chunk
+                unsigned im = __ballot_sync(kFullMask, !active[j]);
+                if (im != 0u && (__popc(im) >= B.refill_min || im == kFullMask)) {
+                    while (im != 0u) {
+                        const int si = X.sp_i, sn = X.sp_n;
+                        if (si == sn) {
+                            if (X.next >= X.end) break;
+                            refill();
+                            continue;
                         }
-                        next += __popc(idle);
-                        if (next > end) next = end;
+                        const int avail = sn - si;
+                        const int rank = __popc(im & lanemask_lt());
+                        if (!active[j] && rank < avail) {
+                            const int e = si + rank;
+                            pair_init<Real, 2>(st[j], X.first + (unsigned long long)SP.off[e], SP.x0[e],
+                                               SP.v0[e], SP.q0[e], L, coupled);
+                            active[j] = true;
+                        }
+                        const int took = __popc(im) < avail ? __popc(im) : avail;
+                        __syncwarp();
+                        X.sp_i = si + took;
+                        __syncwarp();
+                        im = __ballot_sync(kFullMask, !active[j]);
                     }
                 }
             }
-            bool any_local = false, any_done = false;
+            bool any_local = false;
 #pragma unroll
-            for (int j = 0; j < PPT; ++j) {
-                any_local |= active[j];
-                any_done |= done[j];
-            }
+            for (int j = 0; j < PPT; ++j) any_local |= active[j];
             if (!__any_sync(kFullMask, any_local)) {
-                if (next >= end && !__any_sync(kFullMask, any_done)) {
+                // every lane idle with nothing to hand out: the chunk is done
+                if (X.next >= X.end && X.sp_i == X.sp_n) {
+                    const int nf = X.fp_n;
+                    if (nf > 0) fp_process(nf);
                     chunk_done = true;
                     break;
                 }
                 continue;
             }
+            // events until a pair reaches T (or the slice budget is spent)
+            for (;;) {
+                bool any_done = false;
 #pragma unroll
-            for (int j = 0; j < PPT; ++j)
-                if (active[j] && pair_event<Real, 2, ModeRecipe<MODE>::value>(st[j], L, B.keys, coupled)) {
-                    active[j] = false;
-                    done[j] = true;
-                }
-            ++iters;
+                for (int j = 0; j < PPT; ++j)
+                    if (active[j] && pair_event<Real, 2, ModeRecipe<MODE>::value>(st[j], L, B.keys, coupled)) {
+                        active[j] = false;
+                        done[j] = true;
+                        any_done = true;
+                    }
+                ++iters;
+                if (__any_sync(kFullMask, any_done) || (B.slice_iters > 0 && iters >= B.slice_iters)) break;
+            }
         }
         if (!chunk_done) {
             // budget spent inside the chunk: store it for the next slice
@@ -805,11 +1029,12 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             for (int j = 0; j < PPT; ++j)
                 bits |= ((active[j] ? 1u : 0u) << j) | ((done[j] ? 1u : 0u) << (kMaxPPT + j));
             put_words(bits, lw, stride, w);
+            put_pools(w);
             flush_hist();
             if (lane == 0) {
                 hdr->valid = 1;
-                hdr->c = c;
-                hdr->next = next;
+                hdr->c = X.c;
+                hdr->next = X.next;
             }
             return;
         }
@@ -821,7 +1046,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             ev_c_sum += __shfl_down_sync(kFullMask, ev_c_sum, off);
         }
         if (lane == 0) {
-            double *row = B.rows + (size_t)c * kPartialWords;
+            double *row = B.rows + (size_t)X.c * kPartialWords;
 #pragma unroll
             for (int j = 0; j < 6; ++j) row[j] = mom.value(j);
             row[6] = (double)ev_f_sum;
@@ -832,11 +1057,12 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         // the row and the histogram counts are visible before the count
         // drops; the warp that takes it to zero completes the round
         __threadfence();
+        const int req = X.req;
         int last = 0;
-        if (lane == 0) last = atomicSub(&B.state[ch.req].pending, 1) == 1;
+        if (lane == 0) last = atomicSub(&B.state[req].pending, 1) == 1;
         if (__shfl_sync(kFullMask, last, 0)) {
             __threadfence();
-            if (*(volatile int32_t *)&B.state[ch.req].status == 2) warp_round_complete(B, ch.req, lane);
+            if (*(volatile int32_t *)&B.state[req].status == 2) warp_round_complete(B, req, lane);
         }
         valid = 0;
     }
@@ -1061,7 +1287,7 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->ring_mask = BL.ring - 1;
     B->max_nbins = cfg->max_nbins > 0 ? cfg->max_nbins : 1;
     B->slice_iters = cfg->substeps_per_launch;
-    B->refill_min = cfg->refill_min > 0 ? cfg->refill_min : kRefillMin;
+    B->refill_min = cfg->refill_min > 0 ? cfg->refill_min : kBatchRefillMin;
     B->publish_spins = cfg->publish_wait_spins > 0 ? cfg->publish_wait_spins : kPublishSpins;
     B->dbg_req = -1;
     B->dbg_level = -1;

@@ -58,34 +58,57 @@ __device__ __forceinline__ int next_coarse_end(const LevelCtx<Real> &L, int base
 template <typename Real, int CPL>
 __device__ __forceinline__ bool pair_is_coupled(bool runtime) { return CPL == 2 ? runtime : CPL == 1; }
 
+// Alg. 1 / Alg. 2 initialisation values of pair p: x_0, v_0 and the first
+// flight in fine-step units (nu_0, E_0 and the initial-position uniform of
+// Philox block 0), shared by both paths.
+template <typename Real, int RECIPE = 0>
+__device__ __forceinline__ void pair_start_values(Real &x0, Real &v0, Real &q0, unsigned long long p,
+                                                  const LevelCtx<Real> &L, const PhiloxKeys &keys)
+{
+    const Draw<Real> d0 = draw_r<Real, RECIPE>(0u, (uint32_t)p, L.word2 ^ (uint32_t)(p >> 32),
+                                               L.request, keys);
+    x0 = L.init ? cosine_inverse<Real>(d0.u4) : Real(0);
+    v0 = L.bg.mu + L.bg.sigma * d0.nu;
+    q0 = d0.E * L.bg.inv_Rdt;
+}
+
+// The state of pair p at t = 0 from its initialisation values.  Returns true
+// if the pair has no collision before T (already finished).
+template <typename Real, int CPL>
+__device__ __forceinline__ bool pair_init(PairState<Real> &st, unsigned long long p, Real x0, Real v0,
+                                          Real q0, const LevelCtx<Real> &L, bool coupled_rt)
+{
+    const bool coupled = pair_is_coupled<Real, CPL>(coupled_rt);
+    st.pair_lo = (uint32_t)p;
+    st.word2 = L.word2 ^ (uint32_t)(p >> 32);
+    st.xf = x0;
+    st.vf = v0;
+    st.qf = q0;
+    st.i_f = 0;
+    st.k = 0;
+    st.evc = 0;
+    if (coupled) {
+        st.xc = x0;
+        st.vc = v0;
+        st.qc = q0;
+        st.ic = 0;
+        st.num = Real(0);
+        st.den = Real(0);
+        st.fresh = true;
+        if (q0 < (Real)L.n) st.Ec = next_coarse_end(L, 0, (int)q0);
+    }
+    return !(q0 < (Real)L.n);
+}
+
 // Returns true if the pair has no collision before T (already finished).
 template <typename Real, int CPL, int RECIPE = 0>
 __device__ __forceinline__ bool pair_start(PairState<Real> &st, unsigned long long p,
                                            const LevelCtx<Real> &L, const PhiloxKeys &keys,
                                            bool coupled_rt)
 {
-    const bool coupled = pair_is_coupled<Real, CPL>(coupled_rt);
-    st.pair_lo = (uint32_t)p;
-    st.word2 = L.word2 ^ (uint32_t)(p >> 32);
-    const Draw<Real> d0 = draw_r<Real, RECIPE>(0u, st.pair_lo, st.word2, L.request, keys);
-    const Real x0 = L.init ? cosine_inverse<Real>(d0.u4) : Real(0);
-    st.xf = x0;
-    st.vf = L.bg.mu + L.bg.sigma * d0.nu;
-    st.qf = d0.E * L.bg.inv_Rdt;
-    st.i_f = 0;
-    st.k = 0;
-    st.evc = 0;
-    if (coupled) {
-        st.xc = x0;
-        st.vc = st.vf;
-        st.qc = st.qf;
-        st.ic = 0;
-        st.num = Real(0);
-        st.den = Real(0);
-        st.fresh = true;
-        if (st.qf < (Real)L.n) st.Ec = next_coarse_end(L, 0, (int)st.qf);
-    }
-    return !(st.qf < (Real)L.n);
+    Real x0, v0, q0;
+    pair_start_values<Real, RECIPE>(x0, v0, q0, p, L, keys);
+    return pair_init<Real, CPL>(st, p, x0, v0, q0, L, coupled_rt);
 }
 
 // One fine event; returns true when the pair has reached T.

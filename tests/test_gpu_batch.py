@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import gpu_problem, oracle_problem
+from helpers import fp64_close, gpu_problem, oracle_problem
 
 pytestmark = pytest.mark.gpu
 
@@ -409,3 +409,46 @@ def test_warp_pair_form_fp32_and_slices(orc, mk, ctx):
             assert np.array_equal(xf1, xf) and np.array_equal(xc1, xc)
             assert r1.estimate == r0.estimate
         assert np.array_equal(kf1, kf) and np.array_equal(kc1, kc)
+
+
+LANE_POOL_CASES = {
+    # R = 1/4 over T = 1: about 78 % of the pairs have no collision before T
+    # and are finished in the start pass itself
+    "kinetic_dead_starts": (dict(eps=2.0, T=1.0, dt0=0.25, M=2, L=3, qoi=0, init=0, nbins=16, lo=-3.0,
+                                 hi=3.0, seed=8, tol=0.0), 2, 3001),
+    "kinetic_single_paths": (dict(eps=2.0, T=1.0, dt0=0.25, M=2, L=3, qoi=0, init=0, nbins=16,
+                                  lo=-3.0, hi=3.0, seed=8, tol=0.0), 0, 3001),
+    "mixed_periodic": (dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=6, qoi=1, init=1, nbins=32, lo=0.0,
+                            hi=1.0, seed=21, tol=0.0), 4, 2001),
+}
+
+
+@pytest.mark.parametrize("name", sorted(LANE_POOL_CASES))
+def test_lane_form_pools_match_oracle_fp64(orc, mk, ctx, name):
+    """One pair per lane, with pairs started 32 at a time into a pool and
+    finished pairs summed 32 at a time: every pair (those finished in the
+    start pass included) is the oracle's pair, whatever the pairs per
+    thread, the idle-lane threshold and the slice length.  The same
+    configuration sliced or not gives the same sums bit for bit; another
+    threshold or pairs-per-thread setting changes only their order."""
+    d, level, n = LANE_POOL_CASES[name]
+    nf = [n] * (d["L"] + 1)
+    p = gpu_problem(mk, d, precision=mk.PREC_FP64, n_fixed=nf)
+    xf_o, xc_o, kf_o, kc_o = orc.pairs(oracle_problem(orc, d), level, 0, n, threads=16)
+    runs = {}
+    for ppt, sl, rm in ((1, 0, 0), (1, 7, 0), (2, 0, 1), (2, 13, 1), (4, 5, 32), (1, 0, 3)):
+        cfg = mk.batch_config(pairs_per_thread=ppt, substeps_per_launch=sl, max_requests=64,
+                              max_nbins=128, refill_min=rm, warp_pair_min_events=-1)
+        r, xf, xc, kf, kc = ctx.debug_batch_pairs(p, cfg, level)
+        assert np.array_equal(kf, kf_o) and np.array_equal(kc, kc_o), (ppt, sl, rm)
+        assert fp64_close(xf, xf_o).all() and fp64_close(xc, xc_o).all(), (ppt, sl, rm)
+        runs[(ppt, sl, rm)] = r
+    ref = runs[(1, 0, 0)]
+    for key, r in runs.items():
+        same_order = (key[0], key[2]) in ((1, 0), (2, 1)) and key[1] > 0
+        base = ref if key[0] == 1 else runs[(2, 0, 1)]
+        if same_order:
+            assert r.estimate == base.estimate and r.variance == base.variance, key
+        assert r.estimate == pytest.approx(ref.estimate, rel=1e-12, abs=1e-15), key
+        for la, lb in zip(r.levels, ref.levels):
+            assert la["events_f"] == lb["events_f"] and la["events_c"] == lb["events_c"]
