@@ -113,7 +113,7 @@ def parse():
     ap.add_argument("--eps", type=float, default=None,
                     help="kernelcase batch: only the estimate of this eps (default: all three)")
     ap.add_argument("--warp-pair", type=int, default=0,
-                    help="kernelcase batch: warp_pair_min_events of the batch configuration "
+                    help="kernelcase batch and serving: warp_pair_min_events of the batch configuration "
                          "(0: library default; -1: one pair per lane everywhere)")
     ap.add_argument("--scale", type=int, default=0,
                     help="kernelcase: log2 scale of the pair counts (batch: 3 is the full step)")
@@ -582,7 +582,8 @@ def _gpu_setup(args, slots=64, nbins=128, substeps=256):
     import paper_2004_04071_gb300 as mk
     torch.cuda.set_device(0)
     cfg = mk.batch_config(pairs_per_thread=1, substeps_per_launch=substeps, use_graph=1,
-                          max_requests=slots, max_nbins=nbins)
+                          max_requests=slots, max_nbins=nbins,
+                          warp_pair_min_events=getattr(args, "warp_pair", 0))
     ctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(cfg))
     return torch, mk, ctx, cfg
 

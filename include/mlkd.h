@@ -379,12 +379,12 @@ MLKD_API mlkd_status mlkd_debug_batch_pairs(mlkd_context *ctx, const mlkd_proble
                                             int32_t *kf, int32_t *kc);
 
 /* Autotuner: times mlkd_estimate_batch on these problems for every
- * warp_pair_min_events in {0 (library default), -1 (one pair per lane
- * everywhere)}, pairs_per_thread in {1, 2, 4, 8} and substeps_per_launch in
- * {16, 64, 256, 0 (unbounded)} (graph form), and writes the fastest
- * configuration to *best (its other fields copied from *base).  seconds[32],
- * if not NULL, receives the times in that nesting order (warp-pair setting
- * outermost, substeps innermost). */
+ * warp_pair_min_events in {0 (library default, 1024), -1 (one pair per lane
+ * everywhere), 4096}, pairs_per_thread in {1, 2, 4, 8} and
+ * substeps_per_launch in {16, 64, 256, 0 (unbounded)} (graph form), and
+ * writes the fastest configuration to *best (its other fields copied from
+ * *base).  seconds[48], if not NULL, receives the times in that nesting
+ * order (warp-pair setting outermost, substeps innermost). */
 MLKD_API mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
                                          const mlkd_batch_config *base, void *stream,
                                          mlkd_batch_config *best, double *seconds);

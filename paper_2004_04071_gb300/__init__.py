@@ -502,7 +502,7 @@ class Context:
         n = len(problems)
         arr = (Problem * n)(*problems)
         best = BatchConfig()
-        secs = (ctypes.c_double * 32)()
+        secs = (ctypes.c_double * 48)()
         _check(lib().mlkd_autotune_batch(self.handle, arr, n, ctypes.byref(base),
                                          _stream_handle(stream), ctypes.byref(best), secs),
                "mlkd_autotune_batch")

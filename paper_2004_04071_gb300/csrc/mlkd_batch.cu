@@ -1880,7 +1880,7 @@ mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems,
     std::vector<mlkd_result> res(n);
     const int ppts[4] = {1, 2, 4, 8};
     const int slices[4] = {16, 64, 256, 0};
-    const int warps[2] = {0, -1};
+    const int warps[3] = {0, -1, 4 * kWarpPairEvents};
     double best_t = 1e300;
     *best = *base;
     cudaEvent_t e0, e1;
@@ -1888,7 +1888,7 @@ mlkd_status mlkd_autotune_batch(mlkd_context *ctx, const mlkd_problem *problems,
     MLKD_CUDA(cudaEventCreate(&e0));
     MLKD_CUDA(cudaEventCreate(&e1));
     mlkd_status st = MLKD_OK;
-    for (int w = 0; w < 2 && st == MLKD_OK; ++w)
+    for (int w = 0; w < 3 && st == MLKD_OK; ++w)
     for (int a = 0; a < 4 && st == MLKD_OK; ++a) {
         for (int b = 0; b < 4 && st == MLKD_OK; ++b) {
             mlkd_batch_config c = *base;

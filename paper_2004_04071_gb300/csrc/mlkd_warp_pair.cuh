@@ -66,11 +66,21 @@ __device__ __forceinline__ bool warp_pair_step(PairState<Real> &st, const LevelC
     const int n = L.n;
     const Real qpc = A::min_(qp, (Real)n);
     const int sq = (int)qpc;
+    // In the diffusive regime every flight is shorter than a fine step
+    // (R dt >> 1): each event then advances one step, the prefix sum is the
+    // lane index, and a coarse window holds at most M events.  The scans
+    // below take that shortcut when it holds for the whole step; their
+    // results are the same values either way.
+    const bool one_step = __all_sync(kFullMask, qp < Real(1) && qn < Real(1));
     int ia = sq + 1;                                           // inclusive prefix -> index after
+    if (one_step) {
+        ia = lane + 1;
+    } else {
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int up = __shfl_up_sync(kFullMask, ia, off);
-        if (lane >= off) ia = min(ia + up, n + 1);
+        for (int off = 1; off < 32; off <<= 1) {
+            const int up = __shfl_up_sync(kFullMask, ia, off);
+            if (lane >= off) ia = min(ia + up, n + 1);
+        }
     }
     ia = min(st.i_f + ia, n + 1);
     const int ib = ia - (sq + 1);                              // index before this event
@@ -108,14 +118,16 @@ __device__ __forceinline__ bool warp_pair_step(PairState<Real> &st, const LevelC
                 cn += ah * d.nu;
                 cd += ah * ah;
             }
-            // segmented inclusive scan; a window starts after each trigger
+            // segmented inclusive scan; a window starts after each trigger.
+            // With one step per event a window spans at most M lanes, and
+            // the scan is complete after the offsets below M.
             bool head = lane == 0 || ((tmask >> (lane - 1)) & 1u);
             if (lane == 0) {
                 cn += st.num;
                 cd += st.den;
             }
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
+            const int span = one_step && L.M < 32 ? L.M : 32;
+            for (int off = 1; off < span; off <<= 1) {
                 const Real nu_ = __shfl_up_sync(kFullMask, cn, off);
                 const Real du_ = __shfl_up_sync(kFullMask, cd, off);
                 const int hu = __shfl_up_sync(kFullMask, (int)head, off);

@@ -174,9 +174,9 @@ def test_autotune_picks_from_grid(mk, ctx):
     best, secs = ctx.autotune_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))
     assert best.pairs_per_thread in (1, 2, 4, 8)
     assert best.substeps_per_launch in (16, 64, 256, 0)
-    assert best.warp_pair_min_events in (0, -1)
-    assert len(secs) == 32 and all(s > 0 for s in secs)
-    assert min(secs) == pytest.approx(secs[[0, -1].index(best.warp_pair_min_events) * 16 +
+    assert best.warp_pair_min_events in (0, -1, 4096)
+    assert len(secs) == 48 and all(s > 0 for s in secs)
+    assert min(secs) == pytest.approx(secs[[0, -1, 4096].index(best.warp_pair_min_events) * 16 +
                                           [1, 2, 4, 8].index(best.pairs_per_thread) * 4 +
                                           [16, 64, 256, 0].index(best.substeps_per_launch)])
 
