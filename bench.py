@@ -97,24 +97,27 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", default="fp32comp", choices=["fp32", "fp32comp", "fp64"])
-    ap.add_argument("--form", default="batch", choices=["batch", "plain"],
-                    help="batched persistent form (default) or the per-level form")
+    ap.add_argument("--form", default="batch", choices=["batch", "plain", "het"],
+                    help="batched persistent form (default) or the per-level form; kernelcase "
+                         "het: per-level launches over background B1")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--oracle-ttt-seconds", type=float, default=90.0,
                     help="budget of the oracle's time to tolerance (0: skip it)")
     ap.add_argument("--workload", default="periodic",
                     choices=["periodic", "twolevel", "precision", "batched64", "serving",
-                             "complexity", "kernelcase"],
+                             "complexity", "hetero", "kernelcase"],
                     help="periodic: the headline (full periodic MLMC); the others measure the "
-                         "two-level, precision, batched and serving configurations, and the "
-                         "cost-tolerance slope of the Sec. 5.3 protocol; kernelcase: fixed "
-                         "launches for ncu captures")
+                         "two-level, precision, batched and serving configurations, the "
+                         "cost-tolerance slope of the Sec. 5.3 protocol and the heterogeneous "
+                         "backgrounds B1/B2 of Sec. 5; kernelcase: fixed launches for ncu captures")
     ap.add_argument("--eps", type=float, default=None,
                     help="kernelcase batch: only the estimate of this eps (default: all three)")
     ap.add_argument("--warp-pair", type=int, default=0,
                     help="kernelcase batch and serving: warp_pair_min_events of the batch configuration "
                          "(0: library default; -1: one pair per lane everywhere)")
+    ap.add_argument("--het-tol", type=float, default=1e-4,
+                    help="hetero: RMSE tolerance of the estimates of E[x(T)]")
     ap.add_argument("--scale", type=int, default=0,
                     help="kernelcase: log2 scale of the pair counts (batch: 3 is the full step)")
     ap.add_argument("--requests", type=int, default=2000, help="serving: requests in the stream")
@@ -833,6 +836,65 @@ def run_complexity(args):
     ctx.close()
 
 
+HET_CASE = dict(eps=1.0, T=1.0, dt0=1.0, M=2, L=12, x0=1.0, bg_a=10.0, bg_b=1000.0)
+
+
+def run_hetero(args):
+    """Heterogeneous backgrounds B1 and B2 of Sec. 5 (a = 10, b = 1000, the
+    background of Table hypothesis): x(0) = 1, T = 1, mu = 0, sigma = 1, QoI
+    x(T), dt_l = T 2^-l, M = 2, L = 12.  For each background: the adaptive
+    estimate of E[x(T)] to RMSE --het-tol in FP32 (per-level form; median
+    of 5 runs) and in plain FP64, its KD events per second, and the oracle's
+    time to tolerance on the same problem on all host cores.  The KD
+    coefficients are the homogeneous ones at the local rate, a stand-in for
+    the corrected coefficients that the paper does not print."""
+    import torch
+    import paper_2004_04071_gb300 as mk
+    torch.cuda.set_device(0)
+    ctx = mk.Context(0)
+    cores = os.cpu_count() or 1
+    out = {"metric": "heterogeneous backgrounds B1/B2 (a=10, b=1000): time to tolerance and events/s",
+           "unit": "s", "higher_is_better": False, "data": "synthetic (Philox streams; analytic "
+           "backgrounds of Sec. 5; homogeneous KD coefficients at the local rate)",
+           "tol": args.het_tol, "config": dict(HET_CASE, qoi="x(T)", init="point"), "backgrounds": {}}
+    for name, bg in (("B1", mk.BG_B1), ("B2", mk.BG_B2)):
+        d = dict(HET_CASE, background=bg, qoi=mk.QOI_X, init=mk.INIT_POINT, tol=args.het_tol, seed=0)
+        p32 = mk.make_problem(precision=mk.PREC_FP32_COMP, **d)
+        ctx.estimate(p32)                                    # warm-up (module load, arena)
+        ts, r = [], None
+        for _ in range(5):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = ctx.estimate(p32)
+            ts.append(time.perf_counter() - t0)
+        t32 = statistics.median(ts)
+        ev = sum(lv["events_f"] + lv["events_c"] for lv in r.levels)
+        t0 = time.perf_counter()
+        r64 = ctx.estimate(mk.make_problem(precision=mk.PREC_FP64, **d))
+        t64 = time.perf_counter() - t0
+        rec = {"time_to_tolerance_s": t32, "runs_s": ts, "events": ev, "events_per_s": ev / t32,
+               "estimate": r.estimate, "variance": r.variance,
+               "met": r.variance <= args.het_tol ** 2 / 2 * (1 + 1e-9),
+               "n": [lv["n"] for lv in r.levels],
+               "time_to_tolerance_plain_fp64_s": t64, "estimate_fp64": r64.estimate,
+               "speedup_vs_plain_fp64": t64 / t32}
+        if args.oracle_ttt_seconds > 0:
+            import oracle as O
+            po = O.Problem(eps=1.0, T=1.0, dt0=1.0, M=2, L=HET_CASE["L"], qoi=O.QOI_X,
+                           init=O.INIT_POINT, x0=1.0, tol=args.het_tol, seed=0, background=bg,
+                           a=HET_CASE["bg_a"], b=HET_CASE["bg_b"])
+            t0 = time.perf_counter()
+            ro = O.estimate(po, threads=cores)
+            to = time.perf_counter() - t0
+            rec["oracle"] = {"time_to_tolerance_s": to, "cores": cores, "estimate": ro.estimate,
+                             "variance": ro.variance, "n": [lv.n for lv in ro.levels],
+                             "kind": "oracle", "ratio_to_gpu_fp32": to / t32}
+        out["backgrounds"][name] = rec
+    out["value"] = sum(b["time_to_tolerance_s"] for b in out["backgrounds"].values())
+    print(json.dumps(out), flush=True)
+    ctx.close()
+
+
 def run_kernelcase(args):
     """Fixed pair-kernel launches for ncu captures (no timing, one JSON line).
 
@@ -863,6 +925,14 @@ def run_kernelcase(args):
         rs = ctx.estimate_batch(probs, cfg)
         out["launches"] = [{"eps": EPS_SET[i], "events": sum(lv["events_f"] + lv["events_c"] for lv in r.levels)}
                            for i, r in zip(sel, rs)]
+    elif args.form == "het":
+        ctx = mk.Context(0)
+        for level in (4, 8, 12):
+            d = dict(HET_CASE, background=mk.BG_B1, qoi=mk.QOI_X, init=mk.INIT_POINT, seed=0)
+            p = mk.make_problem(precision=prec, **d)
+            st = ctx.run_level(p, level, 0, (1 << 18) << args.scale)
+            out["launches"].append({"background": "B1", "level": level, "pairs": (1 << 18) << args.scale,
+                                    "events_f": st["events_f"], "events_c": st["events_c"]})
     else:
         ctx = mk.Context(0)
         for eps, level, n in ((0.1, 8, 1 << 20), (1e-3, 6, 1 << 20), (0.1, 0, 1 << 22)):
@@ -883,7 +953,7 @@ def main():
     else:
         {"twolevel": run_twolevel, "precision": run_precision, "batched64": run_batched64,
          "serving": run_serving, "complexity": run_complexity,
-         "kernelcase": run_kernelcase}[args.workload](args)
+         "hetero": run_hetero, "kernelcase": run_kernelcase}[args.workload](args)
 
 
 if __name__ == "__main__":

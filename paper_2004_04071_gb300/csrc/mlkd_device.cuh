@@ -50,6 +50,9 @@ template <> struct Arith<float> {
     static __device__ __forceinline__ float max_(float a, float b) { return fmaxf(a, b); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
     static __device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+    // a / b to about 2 ulp (|b| below 2^126), for quotients whose error the
+    // FP32 per-pair bound absorbs
+    static __device__ __forceinline__ float div_(float a, float b) { return __fdividef(a, b); }
     // sqrt of x >= 0 from y = x * rsqrt(x) and one Newton correction
     // y + (x - y^2) rsqrt(x)/2 (Heron's step), without a branch; 0 for x <= 0.
     // The raw product alone is biased by up to about 2^-22 relative, which
@@ -121,6 +124,7 @@ template <> struct Arith<double> {
     static __device__ __forceinline__ double max_(double a, double b) { return fmax(a, b); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
     static __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+    static __device__ __forceinline__ double div_(double a, double b) { return a / b; }
     static __device__ __forceinline__ double sqrt_pos_(double x) { return x > 0.0 ? sqrt(x) : 0.0; }
     static __device__ __forceinline__ double cbrt_(double x) { return cbrt(x); }
     static __device__ __forceinline__ void sincospi_(double x, double *s, double *c) { sincospi(x, s, c); }

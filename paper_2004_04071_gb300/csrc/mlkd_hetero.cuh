@@ -50,7 +50,7 @@ template <typename Real> struct HetBg {
     __device__ __forceinline__ Real kink(Real x0, Real v) const
     {
         if (v == Real(0) || x0 == Real(1)) return Real(-1);
-        return (Real(1) - x0) / (v * dt);
+        return Arith<Real>::div_(Real(1) - x0, v * dt);
     }
     // optical depth over u >= 0 steps from x0 (eq. intinv's integral)
     __device__ Real depth_fwd(Real x0, Real v, Real u) const
@@ -72,10 +72,10 @@ template <typename Real> struct HetBg {
     }
     __device__ __forceinline__ static Real piece_root(Real rho, Real s, Real E)
     {
-        if (s == Real(0)) return E / rho;
+        if (s == Real(0)) return Arith<Real>::div_(E, rho);
         Real disc = rho * rho + Real(2) * s * E;
         if (disc < Real(0)) disc = Real(0);
-        return Real(2) * E / (rho + Arith<Real>::sqrt_(disc));
+        return Arith<Real>::div_(Real(2) * E, rho + Arith<Real>::sqrt_pos_(disc));
     }
     // eq. intinv: steps u with depth E from x0 at velocity v
     __device__ Real flight(Real x0, Real v, Real E) const
@@ -122,7 +122,7 @@ __device__ __forceinline__ void het_kd(Real R, Real theta, Real v1, Real &a, Rea
 {
     Background<Real> bg;
     bg.R = R;
-    bg.invR = Real(1) / R;
+    bg.invR = Arith<Real>::div_(Real(1), R);
     bg.mu = Real(0);
     bg.sigma = Real(1);
     bg.two_c2 = Real(2) * bg.invR * bg.invR;
@@ -219,7 +219,7 @@ __device__ __forceinline__ bool het_pair_event(HetPairState<Real> &st, const Het
 
     // Sec. 3.2 aggregation: beta of this phase (rate Rloc), then alpha of
     // the new phase if the window goes on
-    const Real invR = Real(1) / Rloc;
+    const Real invR = Arith<Real>::div_(Real(1), Rloc);
     const Real hp = hs < Real(1) ? hs * hs * A::h_series(hs) : A::exp_(-hs) + hs - Real(1);
     const Real beta = A::sqrt_pos_(Real(2) * hp) * invR;          // eq. weights-beta, sigma = 1
     if (st.fresh) {

@@ -22,10 +22,13 @@ template <typename Real> __device__ __forceinline__ const BgParams<Real> &level_
 template <> __device__ __forceinline__ const BgParams<float> &level_params<float>(const PairLaunch &P) { return P.bf; }
 template <> __device__ __forceinline__ const BgParams<double> &level_params<double>(const PairLaunch &P) { return P.bd; }
 
-// Blocks per SM the register allocation must allow: FP32 state fits 64
-// registers (8 blocks of 128 threads); the FP64 form is bound by the FP64 pipe.
-template <typename Real> struct MinBlocks { static constexpr int value = 8; };
-template <> struct MinBlocks<double> { static constexpr int value = 1; };
+// Blocks per SM the register allocation must allow: FP32 state of the
+// homogeneous background fits 64 registers (8 blocks of 128 threads); the
+// heterogeneous pair state does not, and at 64 registers its kernel kept the
+// FP64 pipe 21-83 % busy (ncu) without a line of FP64 arithmetic, so it gets
+// 128 (4 blocks); the FP64 form is bound by the FP64 pipe.
+template <typename Real, int PHYS> struct MinBlocks { static constexpr int value = PHYS == 1 ? 4 : 8; };
+template <int PHYS> struct MinBlocks<double, PHYS> { static constexpr int value = 1; };
 
 // Pair state of the two physics: the homogeneous background (PHYS 0) and the
 // heterogeneous backgrounds B1/B2 of Sec. 5 (PHYS 1).
@@ -33,7 +36,7 @@ template <typename Real, int PHYS> struct PhysState { typedef PairState<Real> ty
 template <typename Real> struct PhysState<Real, 1> { typedef HetPairState<Real> type; };
 
 template <typename Real, int MODE, bool COUPLED, int PHYS>
-__global__ void __launch_bounds__(kThreads, MinBlocks<Real>::value)
+__global__ void __launch_bounds__(kThreads, (MinBlocks<Real, PHYS>::value))
 pair_kernel(const __grid_constant__ PairLaunch P)
 {
     constexpr int CPL = COUPLED ? 1 : 0;
