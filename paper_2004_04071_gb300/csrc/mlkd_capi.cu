@@ -23,10 +23,12 @@ Layout arena_layout()
 {
     Layout L;
     size_t off = 0;
-    L.partials = off;  off = align_up(off + (size_t)kMaxBlocks * kPartialWords * sizeof(double));
-    L.tmp_stats = off; off = align_up(off + sizeof(DevLevelStats));
+    // one scratch slot (block partials, level sums, histogram) per level, so
+    // that the levels of a round can run at the same time
+    L.partials = off;  off = align_up(off + (size_t)MLKD_MAX_LEVELS * kMaxBlocks * kPartialWords * sizeof(double));
+    L.tmp_stats = off; off = align_up(off + MLKD_MAX_LEVELS * sizeof(DevLevelStats));
     L.acc_stats = off; off = align_up(off + MLKD_MAX_LEVELS * sizeof(DevLevelStats));
-    L.tmp_hist = off;  off = align_up(off + 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
+    L.tmp_hist = off;  off = align_up(off + (size_t)MLKD_MAX_LEVELS * 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
     L.acc_hist = off;  off = align_up(off + (size_t)MLKD_MAX_LEVELS * 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
     L.control = off;   off = align_up(off + sizeof(DevControl));
     L.total = off;
@@ -214,12 +216,13 @@ mlkd_status choose_grid(mlkd_context *ctx, int mode, bool coupled, int nbins, ui
 
 }  // namespace
 
-// Adds the elapsed time of every recorded pair-kernel launch; the stream of
-// those launches has been synchronised by the caller.
+// Adds the elapsed time of every recorded pair-kernel launch (waiting for
+// each to end; the launches may be on several streams).
 mlkd_status mlkd::harvest_timing(mlkd_context *ctx)
 {
     for (int i = 0; i < ctx->pending; ++i) {
         float ms = 0.0f;
+        MLKD_CUDA(cudaEventSynchronize(ctx->ev_stop[i]));
         MLKD_CUDA(cudaEventElapsedTime(&ms, ctx->ev_start[i], ctx->ev_stop[i]));
         ctx->kernel_ms += ms;
         ++ctx->launches;
@@ -233,8 +236,13 @@ namespace {
 // Enqueues one level run: pair kernel + fixed-order finalize (+ accumulation).
 mlkd_status enqueue_level(mlkd_context *ctx, const mlkd_problem *p, const Derived &d, int level,
                           uint64_t first, uint64_t count, cudaStream_t stream,
-                          bool accumulate, double *dxf, double *dxc, int32_t *dkf, int32_t *dkc)
+                          bool accumulate, double *dxf, double *dxc, int32_t *dkf, int32_t *dkc,
+                          int slot = 0)
 {
+    // this launch's scratch slot: concurrent launches use different slots
+    double *partials = ctx->partials + (size_t)slot * kMaxBlocks * kPartialWords;
+    DevLevelStats *tmp_stats = ctx->tmp_stats + slot;
+    unsigned long long *tmp_hist = ctx->tmp_hist + (size_t)slot * 3 * MLKD_MAX_BINS;
     PairLaunch P;
     fill_launch(p, d, level, first, count, &P);
     int grid = 1;
@@ -242,28 +250,27 @@ mlkd_status enqueue_level(mlkd_context *ctx, const mlkd_problem *p, const Derive
     mlkd_status st = choose_grid(ctx, d.mode, level > 0, p->nbins, count, &grid, &ppw, d.background);
     if (st != MLKD_OK) return st;
     P.pairs_per_warp = ppw;
-    P.partials = ctx->partials;
-    P.hist = p->nbins > 0 ? ctx->tmp_hist : nullptr;
+    P.partials = partials;
+    P.hist = p->nbins > 0 ? tmp_hist : nullptr;
     P.dbg_xf = dxf;
     P.dbg_xc = dxc;
     P.dbg_kf = dkf;
     P.dbg_kc = dkc;
     if (p->nbins > 0)
-        MLKD_CUDA(cudaMemsetAsync(ctx->tmp_hist, 0, 3 * (size_t)p->nbins * sizeof(unsigned long long), stream));
+        MLKD_CUDA(cudaMemsetAsync(tmp_hist, 0, 3 * (size_t)p->nbins * sizeof(unsigned long long), stream));
     const bool timed = ctx->timing && ctx->events_made;
     if (timed && ctx->pending == kTimingRing) {
-        MLKD_CUDA(cudaStreamSynchronize(stream));
         mlkd_status st2 = harvest_timing(ctx);
         if (st2 != MLKD_OK) return st2;
     }
     if (timed) MLKD_CUDA(cudaEventRecord(ctx->ev_start[ctx->pending], stream));
     MLKD_CUDA(launch_pair_kernel(d.mode, level > 0, P, grid, stream));
     if (timed) MLKD_CUDA(cudaEventRecord(ctx->ev_stop[ctx->pending++], stream));
-    MLKD_CUDA(launch_finalize(ctx->partials, grid, (long long)count, ctx->tmp_stats,
+    MLKD_CUDA(launch_finalize(partials, grid, (long long)count, tmp_stats,
                               accumulate ? ctx->acc_stats + level : nullptr, stream));
     ++ctx->other_launches;
     if (accumulate && p->nbins > 0) {
-        MLKD_CUDA(launch_hist_accumulate(ctx->tmp_hist, ctx->acc_hist + (size_t)level * 3 * p->nbins,
+        MLKD_CUDA(launch_hist_accumulate(tmp_hist, ctx->acc_hist + (size_t)level * 3 * p->nbins,
                                          3 * p->nbins, stream));
         ++ctx->other_launches;
     }
@@ -335,6 +342,7 @@ mlkd_status mlkd_context_create(int device, void *arena, size_t arena_bytes, mlk
     c->kernel_ms = 0.0;
     c->batch = nullptr;
     c->server = nullptr;
+    c->streams_made = false;
     c->arena = (char *)arena;
     c->arena_bytes = arena_bytes;
     c->L = L;
@@ -354,12 +362,19 @@ void mlkd_context_destroy(mlkd_context *ctx)
     cudaSetDevice(ctx->device);
     mlkd::server_release(ctx);
     mlkd::batch_release(ctx);
+    if (ctx->events_made || ctx->streams_made) cudaDeviceSynchronize();
     if (ctx->events_made) {
-        cudaDeviceSynchronize();
         for (int i = 0; i < kTimingRing; ++i) {
             cudaEventDestroy(ctx->ev_start[i]);
             cudaEventDestroy(ctx->ev_stop[i]);
         }
+    }
+    if (ctx->streams_made) {
+        for (int l = 0; l < MLKD_MAX_LEVELS; ++l) {
+            cudaStreamDestroy(ctx->level_stream[l]);
+            cudaEventDestroy(ctx->level_done[l]);
+        }
+        cudaEventDestroy(ctx->round_start);
     }
     delete ctx;
 }
@@ -621,6 +636,19 @@ mlkd_status mlkd_debug_coarse_draws(mlkd_context *ctx, const mlkd_problem *probl
 
 }  // extern "C"
 
+// Streams and events of the concurrent per-level rounds, made once per context.
+static mlkd_status ensure_level_streams(mlkd_context *ctx)
+{
+    if (ctx->streams_made) return MLKD_OK;
+    MLKD_CUDA(cudaEventCreateWithFlags(&ctx->round_start, cudaEventDisableTiming));
+    for (int l = 0; l < MLKD_MAX_LEVELS; ++l) {
+        MLKD_CUDA(cudaStreamCreateWithFlags(&ctx->level_stream[l], cudaStreamNonBlocking));
+        MLKD_CUDA(cudaEventCreateWithFlags(&ctx->level_done[l], cudaEventDisableTiming));
+    }
+    ctx->streams_made = true;
+    return MLKD_OK;
+}
+
 // Adaptive MLMC (Sec. 4.1) with an optional starting state and a round limit.
 static mlkd_status estimate_impl(mlkd_context *ctx, const mlkd_problem *problem,
                                  const mlkd_result *resume, const uint64_t *hist_in, int max_rounds,
@@ -671,12 +699,31 @@ static mlkd_status estimate_impl(mlkd_context *ctx, const mlkd_problem *problem,
         rounds = resume->rounds;
     }
 
-    auto run = [&](int l, long long target) -> mlkd_status {
-        if (target <= have[l]) return MLKD_OK;
-        mlkd_status st = enqueue_level(ctx, problem, d, l, (uint64_t)have[l],
-                                       (uint64_t)(target - have[l]), s, true, nullptr, nullptr,
-                                       nullptr, nullptr);
-        if (st == MLKD_OK) have[l] = target;
+    // One round: every level l with want[l] > have[l] runs its new pairs.
+    // The levels are independent (own pairs, own scratch slot, own sums), so
+    // they run at the same time, each on its level stream, between an event
+    // recorded on the caller's stream and the caller's stream waiting for
+    // all of them.  A round of small deep levels then lasts about as long as
+    // its longest chain instead of the sum of the levels.
+    MLKD_CUDA(ensure_level_streams(ctx));
+    auto round = [&](const long long *want) -> mlkd_status {
+        MLKD_CUDA(cudaEventRecord(ctx->round_start, s));
+        bool used[MLKD_MAX_LEVELS] = {false};
+        mlkd_status st = MLKD_OK;
+        for (int l = 0; l < nl && st == MLKD_OK; ++l) {
+            if (want[l] <= have[l]) continue;
+            cudaStream_t ls = ctx->level_stream[l];
+            MLKD_CUDA(cudaStreamWaitEvent(ls, ctx->round_start, 0));
+            used[l] = true;
+            st = enqueue_level(ctx, problem, d, l, (uint64_t)have[l], (uint64_t)(want[l] - have[l]), ls,
+                               true, nullptr, nullptr, nullptr, nullptr, l);
+            if (st == MLKD_OK) have[l] = want[l];
+        }
+        for (int l = 0; l < nl; ++l) {
+            if (!used[l]) continue;
+            MLKD_CUDA(cudaEventRecord(ctx->level_done[l], ctx->level_stream[l]));
+            MLKD_CUDA(cudaStreamWaitEvent(s, ctx->level_done[l], 0));
+        }
         return st;
     };
     auto control = [&]() -> mlkd_status {
@@ -689,27 +736,29 @@ static mlkd_status estimate_impl(mlkd_context *ctx, const mlkd_problem *problem,
     };
 
     mlkd_status st;
+    long long want[MLKD_MAX_LEVELS];
     if (problem->n_fixed) {
         for (int l = 0; l < nl; ++l) {
             if (problem->n_fixed[l] < 0) return MLKD_EINVAL;
-            if ((st = run(l, problem->n_fixed[l])) != MLKD_OK) return st;
+            want[l] = problem->n_fixed[l];
         }
+        if ((st = round(want)) != MLKD_OK) return st;
         if ((st = control()) != MLKD_OK) return st;
     } else {
-        if (!resume)
-            for (int l = 0; l < nl; ++l)
-                if ((st = run(l, problem->n_warmup)) != MLKD_OK) return st;
+        if (!resume) {
+            for (int l = 0; l < nl; ++l) want[l] = problem->n_warmup;
+            if ((st = round(want)) != MLKD_OK) return st;
+        }
         for (;;) {
             if ((st = control()) != MLKD_OK) return st;
             if (rounds >= max_rounds) break;           // stop; resumable from here
             bool grew = false;
             for (int l = 0; l < nl; ++l) {
-                if (ctl.target[l] > have[l]) {
-                    if ((st = run(l, ctl.target[l])) != MLKD_OK) return st;
-                    grew = true;
-                }
+                want[l] = ctl.target[l];
+                grew = grew || ctl.target[l] > have[l];
             }
             if (!grew) break;
+            if ((st = round(want)) != MLKD_OK) return st;
             ++rounds;
         }
     }

@@ -88,6 +88,12 @@ struct mlkd_context {
     mlkd::DevControl *control;
     mlkd::BatchCache *batch;    // lazily created by the batched form
     mlkd::Server *server;       // running serving form, or null
+    // the per-level estimate runs the levels of a round on these streams
+    // (created on first use), forked from and joined to the caller's stream
+    bool streams_made;
+    cudaStream_t level_stream[MLKD_MAX_LEVELS];
+    cudaEvent_t level_done[MLKD_MAX_LEVELS];
+    cudaEvent_t round_start;
 };
 
 #define MLKD_CUDA(call)                                  \

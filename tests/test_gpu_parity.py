@@ -153,6 +153,26 @@ def test_reproducible(mk, ctx):
     assert a["sy"] == b["sy"] and a["sy2"] == b["sy2"] and a["events_c"] == b["events_c"]
 
 
+@pytest.mark.parametrize("case", ["periodic_density", "hetero_B1"])
+def test_estimate_reproducible(mk, ctx, case):
+    """The adaptive per-level estimate runs the levels of each round at the
+    same time on separate streams; the result, per-level sums and histograms
+    included, is the same bit for bit from run to run (FP32 state)."""
+    if case == "periodic_density":
+        d = dict(eps=0.1, T=1.0, dt0=0.5, M=2, L=6, qoi=2, init=1, nbins=32, lo=0.0, hi=1.0,
+                 tol=0.02, seed=4)
+    else:
+        d = dict(eps=1.0, T=1.0, dt0=1.0, M=2, L=8, qoi=3, init=2, x0=1.0, nbins=0, tol=1e-3,
+                 seed=4, background=1, bg_a=10.0, bg_b=1000.0)
+    pg = gpu_problem(mk, d, precision=mk.PREC_FP32_COMP)
+    runs = [ctx.estimate(pg) for _ in range(3)]
+    for r in runs[1:]:
+        assert r.estimate == runs[0].estimate and r.variance == runs[0].variance
+        assert r.levels == runs[0].levels
+        if runs[0].density is not None:
+            assert np.array_equal(r.density, runs[0].density)
+
+
 def test_estimate_fixed_two_level(orc, mk, ctx):
     """The two-level free-space problem with N_0 = 10^4, N_1 = 2000."""
     d = dict(W.TWO_LEVEL)
