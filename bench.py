@@ -907,7 +907,7 @@ def run_kernelcase(args):
     --form plain: three per-level launches on the periodic problem --
     eps = 0.1 level 8 (mixed regime), eps = 1e-3 level 6 (deep diffusive),
     eps = 0.1 level 0 (start-dominated) -- of 2^(20+scale) pairs (2^(22+scale)
-    for level 0).  Device memory: the 4.6 MB context arena."""
+    for level 0).  Device memory: the 5 MB context arena."""
     import torch
     import paper_2004_04071_gb300 as mk
     torch.cuda.set_device(0)
