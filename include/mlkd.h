@@ -72,7 +72,8 @@ typedef enum { MLKD_QOI_X2 = 0, MLKD_QOI_X2_PERIODIC = 1, MLKD_QOI_DENSITY = 2,
 /* Initial position: x = 0, or density proportional to 1 + cos(2 pi x) on the
  * periodic unit interval (inverse CDF of a uniform). */
 typedef enum { MLKD_INIT_ORIGIN = 0, MLKD_INIT_COSINE = 1, MLKD_INIT_POINT = 2 } mlkd_init;
-/* MLKD_INIT_POINT: every path starts at problem.x0 (per-level calls only). */
+/* MLKD_INIT_POINT: every path starts at problem.x0 (per-level calls, and the
+ * batched form for the heterogeneous backgrounds). */
 
 /* Background of the collisions.  HOMOGENEOUS: the diffusive scaling of eps
  * (R = 1/eps^2, sigma = 1/eps, mean velocity mu).  B1 / B2: the
@@ -84,8 +85,11 @@ typedef enum { MLKD_INIT_ORIGIN = 0, MLKD_INIT_COSINE = 1, MLKD_INIT_POINT = 2 }
  * advection/diffusion (and the Sec. 3.2 weights) at the rate of the
  * collision point, a stand-in for them.  Flights solve eq. intinv exactly per
  * linear piece, and the coarse flight follows eq. epsilon-update.  Per-level
- * calls only (mlkd_run_level, mlkd_estimate, mlkd_debug_pairs); the finest
- * level has at most 2^24 fine steps. */
+ * calls (mlkd_run_level, mlkd_estimate, mlkd_debug_pairs) and the batched
+ * form (mlkd_estimate_batch, mlkd_debug_batch_pairs, mlkd_autotune_batch: one
+ * pair per lane, whatever pairs_per_thread and warp_pair_min_events say), not
+ * the server or mlkd_debug_coarse_draws; the finest level has at most 2^24 fine
+ * steps. */
 typedef enum { MLKD_BG_HOMOGENEOUS = 0, MLKD_BG_B1 = 1, MLKD_BG_B2 = 2 } mlkd_background;
 
 /* Arithmetic of the pair state.  FP64: state and sums in FP64 (53-bit
@@ -358,7 +362,8 @@ MLKD_API size_t mlkd_batch_workspace_bytes(const mlkd_batch_config *cfg);
  * rounds until eqs. Nopt1/Noptj are met, or n_fixed) in the batched form and
  * writes results[i] for problems[i].  All problems must share precision and
  * seed (request ids separate their streams), have nbins <= cfg->max_nbins,
- * and n <= cfg->max_requests; the context arena must hold
+ * and n <= cfg->max_requests, and be all homogeneous or all heterogeneous
+ * (MLKD_EINVAL otherwise); the context arena must hold
  * mlkd_batch_workspace_bytes(cfg).  Synchronous. */
 MLKD_API mlkd_status mlkd_estimate_batch(mlkd_context *ctx, const mlkd_problem *problems, int n,
                                          const mlkd_batch_config *cfg, void *stream,

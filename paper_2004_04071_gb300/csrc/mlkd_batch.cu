@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "mlkd_host.h"
+#include "mlkd_hetero.cuh"
 #include "mlkd_pair.cuh"
 #include "mlkd_warp_pair.cuh"
 
@@ -60,7 +61,9 @@ struct ReqDesc {
     int32_t level_of[kBL];      // fine level of estimator level j (Philox counter word)
     int32_t L, M, init, nbins, periodic, density, n_warmup, use_fixed;
     uint32_t request;
-    int32_t pad_;
+    int32_t fkind;              // QoI F: 0 x^2, 1 (x mod 1)^2, 2 x
+    int32_t background, pad_;   // mlkd_background
+    double x0, bg_b, bg_a_left, bg_a_right;   // heterogeneous backgrounds
 };
 
 struct ReqState {
@@ -185,6 +188,7 @@ template <typename T> __device__ __forceinline__ void get_words(T &v, const uint
 // for only the few lanes that finished in the same iteration.
 template <typename Real> struct StartPool {
     Real x0[32], v0[32], q0[32];
+    Real e0[32];                     // E_0 (heterogeneous backgrounds)
     int32_t off[32];                 // pair index - the chunk's first pair index
 };
 template <typename Real> struct FinishPool {
@@ -193,7 +197,7 @@ template <typename Real> struct FinishPool {
 };
 // A lane's share of its warp's pools in a stored slice.
 template <typename Real> struct PoolWords {
-    Real x0, v0, q0;
+    Real x0, v0, q0, e0;
     int32_t off;
     Real xf[2], xc[2];
     uint32_t kf[2], kc[2];
@@ -201,10 +205,15 @@ template <typename Real> struct PoolWords {
     uint32_t pad_;
 };
 
-template <typename Real, int MODE, int PPT> constexpr int lane_words()
+// Pair state of the two physics: the homogeneous background (PHYS 0) and the
+// heterogeneous backgrounds B1/B2 of Sec. 5 (PHYS 1).
+template <typename Real, int PHYS> struct BatchState { typedef PairState<Real> type; };
+template <typename Real> struct BatchState<Real, 1> { typedef HetPairState<Real> type; };
+
+template <typename Real, int MODE, int PPT, int PHYS = 0> constexpr int lane_words()
 {
-    return (int)((PPT * sizeof(PairState<Real>) + sizeof(PairSums<MODE>) + 2 * sizeof(unsigned long long) +
-                  sizeof(PoolWords<Real>)) / 4) + 1;
+    return (int)((PPT * sizeof(typename BatchState<Real, PHYS>::type) + sizeof(PairSums<MODE>) +
+                  2 * sizeof(unsigned long long) + sizeof(PoolWords<Real>)) / 4) + 1;
 }
 
 // Blocks per SM of the batched pair kernel by pair states per lane.  Five
@@ -449,8 +458,10 @@ __device__ __noinline__ void warp_plan(const BatchLaunch &B, int r, int lane)
             if (count <= 0) continue;
             // A level whose pairs are long serial chains runs one pair per
             // warp, 32 events per step; its chunks then hold about
-            // kTargetIters warp steps of pairs, not a multiple of 32.
-            const bool wp = B.warp_pair_events > 0 && epps[l] >= (double)B.warp_pair_events;
+            // kTargetIters warp steps of pairs, not a multiple of 32.  (The
+            // heterogeneous backgrounds always run one pair per lane.)
+            const bool wp = B.warp_pair_events > 0 && epps[l] >= (double)B.warp_pair_events &&
+                            D.background == 0;
             if (wp) {
                 double c = 32.0 * kTargetIters / (epps[l] + 32.0 * kPairStartIters);
                 tch[l] = c < 1.0 ? 1 : (long long)c;
@@ -558,7 +569,7 @@ struct WarpCtx {
     unsigned long long next;         // next pair of the chunk to start
     double blo, bhi, bh;             // histogram range and bin width (FP64 state)
     float blo_f, bhi_f, binv_h_f;    // the same for FP32 state
-    int32_t req, level, warp_pair, nbins, per;
+    int32_t req, level, warp_pair, nbins, per, fkind;
     int32_t sp_n, sp_i, fp_n;        // start pool: started, handed out; finish pool: queued
 };
 
@@ -569,10 +580,12 @@ __device__ __forceinline__ unsigned lanemask_lt()
     return m;
 }
 
-template <typename Real, int MODE, int PPT>
+template <typename Real, int MODE, int PPT, int PHYS = 0>
 __global__ void __launch_bounds__(kThreads, (BatchMinBlocks<Real, PPT>::value))
 batch_pair_kernel(const __grid_constant__ BatchLaunch B)
 {
+    static_assert(PHYS == 0 || PPT == 1, "the heterogeneous backgrounds run one pair per lane");
+    constexpr int RECIPE = ModeRecipe<MODE>::value;
     extern __shared__ unsigned int s_hist_all[];        // [warps][3 * max_nbins]
     __shared__ LaneSums<MODE> s_sums[kThreads];
     __shared__ StartPool<Real> s_start[kWarpsPerBlock];
@@ -601,8 +614,9 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     __syncwarp();
 
     LevelCtx<Real> L;
+    HetLevel<Real> H;           // PHYS 1: the level in the heterogeneous background
     bool coupled = false;
-    PairState<Real> st[PPT];
+    typename BatchState<Real, PHYS>::type st[PPT];
     bool active[PPT];           // the lane's pair has events left
     bool done[PPT];             // the lane holds a pair that reached T but is not yet summed
     PairSums<MODE> &mom = s_sums[threadIdx.x].mom;
@@ -623,6 +637,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         X.warp_pair = ch.warp_pair;
         X.nbins = nbins;
         X.per = D->periodic != 0;
+        X.fkind = D->fkind;
         {
             const BgParams<Real> &bp = req_params<Real>(*D, level);
             L.bg.R = bp.R;
@@ -639,6 +654,18 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             L.init = D->init;
             L.word2 = (uint32_t)D->level_of[level] << 24;
             L.request = D->request;
+            if constexpr (PHYS == 1) {
+                H.bg.b = (Real)D->bg_b;
+                H.bg.a_left = (Real)D->bg_a_left;
+                H.bg.a_right = (Real)D->bg_a_right;
+                H.bg.dt = bp.dt;
+                H.n = L.n;
+                H.M = L.M;
+                H.m_shift = L.m_shift;
+                H.x0 = (Real)D->x0;
+                H.word2 = L.word2;
+                H.request = L.request;
+            }
             X.blo = D->bd[level].lo;
             X.bhi = D->bd[level].hi;
             X.bh = D->h;
@@ -663,7 +690,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     };
     // the sums, event counts and histogram counts of one pair at T
     auto account = [&](Real xf, Real xc, uint32_t kf, uint32_t kc) {
-        add_pair(mom, xf, xc, coupled, X.per != 0);
+        add_pair_fk(mom, xf, xc, coupled, X.fkind);
         ev_f_sum += kf;
         ev_c_sum += kc;
         const int nbins = X.nbins;
@@ -695,11 +722,24 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             B.dbg_kc[p] = (int32_t)kc;
         }
     };
-    auto pair_index = [&](const PairState<Real> &q) {
+    auto pair_index = [&](const auto &q) {
         return ((unsigned long long)(q.word2 ^ L.word2) << 32) | q.pair_lo;
     };
+    // the physics' steps: final drift to T and one event
+    auto drift = [&](int j) {
+        if constexpr (PHYS == 1)
+            het_pair_drift<Real>(st[j], H, coupled);
+        else
+            pair_drift<Real, 2>(st[j], L, coupled);
+    };
+    auto event = [&](int j) -> bool {
+        if constexpr (PHYS == 1)
+            return het_pair_event<Real, RECIPE>(st[j], H, B.keys, coupled);
+        else
+            return pair_event<Real, 2, RECIPE>(st[j], L, B.keys, coupled);
+    };
     auto finish = [&](int j) {
-        pair_drift<Real, 2>(st[j], L, coupled);
+        drift(j);
         const Real xc = coupled ? st[j].xc : Real(0);
         account(st[j].xf, xc, st[j].k, st[j].evc);
         dbg_record(pair_index(st[j]), st[j].xf, xc, st[j].k, st[j].evc);
@@ -757,8 +797,15 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         const int nav = rem < 32ull ? (int)rem : 32;
         const unsigned long long pr = nx + (unsigned long long)lane;
         const bool have = lane < nav;
-        Real x0 = Real(0), v0 = Real(0), q0 = Real(0);
-        if (have) pair_start_values<Real, ModeRecipe<MODE>::value>(x0, v0, q0, pr, L, B.keys);
+        Real x0 = Real(0), v0 = Real(0), q0 = Real(0), e0 = Real(0);
+        if (have) {
+            if constexpr (PHYS == 1) {
+                x0 = H.x0;
+                het_start_values<Real, RECIPE>(v0, e0, q0, pr, H, B.keys);
+            } else {
+                pair_start_values<Real, RECIPE>(x0, v0, q0, pr, L, B.keys);
+            }
+        }
         const bool dead = have && !(q0 < (Real)L.n);
         Real xT = Real(0);
         if (dead) {
@@ -773,6 +820,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             SP.x0[i] = x0;
             SP.v0[i] = v0;
             SP.q0[i] = q0;
+            SP.e0[i] = e0;
             SP.off[i] = (int32_t)(pr - first);
         }
         __syncwarp();
@@ -786,6 +834,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         pw.x0 = SP.x0[lane];
         pw.v0 = SP.v0[lane];
         pw.q0 = SP.q0[lane];
+        pw.e0 = SP.e0[lane];
         pw.off = SP.off[lane];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -804,6 +853,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         SP.x0[lane] = pw.x0;
         SP.v0[lane] = pw.v0;
         SP.q0[lane] = pw.q0;
+        SP.e0[lane] = pw.e0;
         SP.off[lane] = pw.off;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -912,7 +962,8 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             valid = 1;
         }
         bool chunk_done = false;
-        if (X.warp_pair) {
+        if (PHYS == 0 && X.warp_pair) {
+          if constexpr (PHYS == 0) {
             // One pair per warp: every lane holds the pair's state, lane j
             // takes its event k + 1 + j; the pair's QoI is summed by lane
             // (pair index mod 32).
@@ -943,6 +994,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                 }
                 ++iters;
             }
+          }
         } else
         for (;;) {
             // the budget is checked before the pools are touched, so a
@@ -954,7 +1006,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                 if (__any_sync(kFullMask, done[j])) {
                     Real xf = Real(0), xc = Real(0);
                     if (done[j]) {
-                        pair_drift<Real, 2>(st[j], L, coupled);
+                        drift(j);
                         xf = st[j].xf;
                         xc = coupled ? st[j].xc : Real(0);
                         dbg_record(pair_index(st[j]), xf, xc, st[j].k, st[j].evc);
@@ -977,8 +1029,11 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                         const int rank = __popc(im & lanemask_lt());
                         if (!active[j] && rank < avail) {
                             const int e = si + rank;
-                            pair_init<Real, 2>(st[j], X.first + (unsigned long long)SP.off[e], SP.x0[e],
-                                               SP.v0[e], SP.q0[e], L, coupled);
+                            const unsigned long long pe = X.first + (unsigned long long)SP.off[e];
+                            if constexpr (PHYS == 1)
+                                het_pair_init<Real>(st[j], pe, SP.v0[e], SP.e0[e], SP.q0[e], H, coupled);
+                            else
+                                pair_init<Real, 2>(st[j], pe, SP.x0[e], SP.v0[e], SP.q0[e], L, coupled);
                             active[j] = true;
                         }
                         const int took = __popc(im) < avail ? __popc(im) : avail;
@@ -1007,7 +1062,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                 bool any_done = false;
 #pragma unroll
                 for (int j = 0; j < PPT; ++j)
-                    if (active[j] && pair_event<Real, 2, ModeRecipe<MODE>::value>(st[j], L, B.keys, coupled)) {
+                    if (active[j] && event(j)) {
                         active[j] = false;
                         done[j] = true;
                         any_done = true;
@@ -1184,8 +1239,10 @@ static BatchLayout batch_layout(const mlkd_batch_config *c)
     B.ctl = off;   off = align_up(off + sizeof(BatchCtl));
     B.live = off;  off = align_up(off + sizeof(int));
     B.hdr = off;   off = align_up(off + (kMaxLanes / 32) * sizeof(WarpHdr));
-    const size_t words = (size_t)std::max(lane_words<float, kModeFP32Comp, kMaxPPT>(),
-                                          lane_words<double, kModeFP64, 1>());
+    const size_t words = (size_t)std::max(std::max(lane_words<float, kModeFP32Comp, kMaxPPT>(),
+                                                   lane_words<double, kModeFP64, 1>()),
+                                          std::max(lane_words<float, kModeFP32Comp, 1, 1>(),
+                                                   lane_words<double, kModeFP64, 1, 1>()));
     B.lanes = off; off = align_up(off + words * kMaxLanes * sizeof(uint32_t));
     B.status = off; off = align_up(off + (size_t)c->max_requests * sizeof(int32_t));
     B.total = off;
@@ -1213,8 +1270,21 @@ void batch_release(mlkd_context *ctx)
 
 typedef void (*BatchKernelFn)(const BatchLaunch);
 
-static BatchKernelFn pick_batch(int mode, int ppt)
+// Kernel id: the precision mode, plus kPhysHet for the heterogeneous
+// backgrounds (one pair per lane).
+constexpr int kPhysHet = 16;
+
+static BatchKernelFn pick_batch(int kid, int ppt)
 {
+    if (kid & kPhysHet) {
+        switch (kid & ~kPhysHet) {
+        case kModeFP64: return batch_pair_kernel<double, kModeFP64, 1, 1>;
+        case kModeFP64U24: return batch_pair_kernel<double, kModeFP64U24, 1, 1>;
+        case kModeFP32DY64: return batch_pair_kernel<float, kModeFP32DY64, 1, 1>;
+        default: return batch_pair_kernel<float, kModeFP32Comp, 1, 1>;
+        }
+    }
+    const int mode = kid;
     switch (mode) {
     case kModeFP64:
         return batch_pair_kernel<double, kModeFP64, 1>;
@@ -1245,6 +1315,14 @@ static void fill_desc(const mlkd_problem *p, const Derived &d, ReqDesc *D)
         D->M_level[l] = P.M;
         D->level_of[l] = d.lev[l];
         D->n_fixed[l] = p->n_fixed ? p->n_fixed[l] : 0;
+        if (l == 0) {
+            D->fkind = P.fkind;
+            D->background = P.background;
+            D->x0 = P.x0;
+            D->bg_b = P.bg_b;
+            D->bg_a_left = P.bg_a_left;
+            D->bg_a_right = P.bg_a_right;
+        }
     }
     D->tol = p->tol;
     D->h = d.h;
@@ -1365,9 +1443,12 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
     std::vector<ReqDesc> desc(n);
     int mode = -1;
     uint64_t seed = 0;
+    const bool het = problems[0].background != MLKD_BG_HOMOGENEOUS;
     for (int i = 0; i < n; ++i) {
         Derived d;
         if (!validate(&problems[i], &d) || d.per_level_only) return MLKD_EINVAL;
+        // one call holds either homogeneous or heterogeneous problems
+        if ((problems[i].background != MLKD_BG_HOMOGENEOUS) != het) return MLKD_EINVAL;
         if (!problems[i].n_fixed && (!(problems[i].tol > 0.0) || problems[i].n_warmup < 2)) return MLKD_EINVAL;
         if (problems[i].nbins > cfg->max_nbins) return MLKD_EINVAL;
         if (i == 0) {
@@ -1378,7 +1459,8 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         }
         fill_desc(&problems[i], d, &desc[i]);
     }
-    const int ppt = (mode == kModeFP64 || mode == kModeFP64U24) ? 1 : cfg->pairs_per_thread;
+    const int ppt = (mode == kModeFP64 || mode == kModeFP64U24 || het) ? 1 : cfg->pairs_per_thread;
+    const int kid = mode | (het ? kPhysHet : 0);
     const auto t0 = std::chrono::steady_clock::now();
     MLKD_CUDA(cudaSetDevice(ctx->device));
 
@@ -1411,13 +1493,13 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         batch_release(ctx);          // a graph with the readout is not kept for later calls
     }
     int grid = 0;
-    mlkd_status st = batch_grid(ctx, mode, ppt, cfg->max_nbins, &grid);
+    mlkd_status st = batch_grid(ctx, kid, ppt, cfg->max_nbins, &grid);
     if (st != MLKD_OK) return st;
     int *live_dev = (int *)(ctx->arena + BL.live);
 
     if (cfg->use_graph) {
         BatchCache *bc = ctx->batch;
-        const bool reuse = bc && bc->exec && bc->mode == mode && bc->seed == seed && bc->n_slots == n &&
+        const bool reuse = bc && bc->exec && bc->mode == kid && bc->seed == seed && bc->n_slots == n &&
                            std::memcmp(&bc->cfg, cfg, sizeof(*cfg)) == 0 && bc->stream == s;
         if (!reuse) {
             batch_release(ctx);
@@ -1445,7 +1527,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
                 cudaStreamDestroy(cs);
                 return MLKD_ECUDA;
             }
-            st = enqueue_body(ctx, B, mode, ppt, grid, h, 1, nullptr, cs);
+            st = enqueue_body(ctx, B, kid, ppt, grid, h, 1, nullptr, cs);
             cudaGraph_t captured = nullptr;
             e = cudaStreamEndCapture(cs, &captured);
             cudaStreamDestroy(cs);
@@ -1455,7 +1537,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
             ctx->launches -= 1;   // the capture launched nothing
             MLKD_CUDA(cudaGraphInstantiate(&bc->exec, g, 0));
             bc->cfg = *cfg;
-            bc->mode = mode;
+            bc->mode = kid;
             bc->seed = seed;
             bc->n_slots = n;
             bc->stream = s;
@@ -1467,7 +1549,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         }
     } else {
         for (int it = 0; it < 1000000; ++it) {
-            st = enqueue_body(ctx, B, mode, ppt, grid, 0, 0, live_dev, s);
+            st = enqueue_body(ctx, B, kid, ppt, grid, 0, 0, live_dev, s);
             if (st != MLKD_OK) return st;
             int live = 0;
             MLKD_CUDA(cudaMemcpyAsync(&live, live_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1936,6 +2018,7 @@ mlkd_status mlkd_submit(mlkd_context *ctx, const mlkd_problem *problem, uint64_t
     if (!S) return MLKD_EINVAL;
     Derived d;
     if (!validate(problem, &d) || d.per_level_only) return MLKD_EINVAL;
+    if (d.background != MLKD_BG_HOMOGENEOUS) return MLKD_EINVAL;    // the server runs the homogeneous kernel
     if (problem->precision != S->cfg.precision || problem->seed != S->cfg.seed) return MLKD_EINVAL;
     if (problem->nbins > S->cfg.batch.max_nbins) return MLKD_EINVAL;
     if (!problem->n_fixed && (!(problem->tol > 0.0) || problem->n_warmup < 2)) return MLKD_EINVAL;

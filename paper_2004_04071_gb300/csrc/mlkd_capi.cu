@@ -82,7 +82,9 @@ bool validate(const mlkd_problem *p, Derived *d)
     d->n0 = (long long)n0;
     d->mode = p->precision;
     d->background = p->background;
-    d->per_level_only = het || p->qoi == MLKD_QOI_X || p->init == MLKD_INIT_POINT;
+    // x(T) and a point start run in the batched form for the heterogeneous
+    // backgrounds (whose test case they are), and only per level otherwise
+    d->per_level_only = !het && (p->qoi == MLKD_QOI_X || p->init == MLKD_INIT_POINT);
     d->periodic = p->qoi == MLKD_QOI_X2_PERIODIC || p->init == MLKD_INIT_COSINE;
     if (d->periodic) {
         d->lo = 0.0;
@@ -619,7 +621,8 @@ mlkd_status mlkd_debug_coarse_draws(mlkd_context *ctx, const mlkd_problem *probl
 {
     NvtxRange nvtx_range("mlkd_debug_coarse_draws");
     Derived d;
-    if (!ctx || !validate(problem, &d) || d.per_level_only) return MLKD_EINVAL;
+    if (!ctx || !validate(problem, &d) || d.per_level_only || d.background != MLKD_BG_HOMOGENEOUS)
+        return MLKD_EINVAL;
     if (level < 1 || level >= d.J || per_pair < 1) return MLKD_EINVAL;
     if (!nu_t || !E_t || !chi_t || !count) return MLKD_EINVAL;
     if (n_pairs > (1ull << 31) / (unsigned long long)per_pair) return MLKD_EINVAL;

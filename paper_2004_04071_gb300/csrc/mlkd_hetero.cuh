@@ -160,19 +160,31 @@ __device__ __forceinline__ void het_keep_output(HetPairState<Real> &st, const He
     }
 }
 
-// Alg. 1 / Alg. 2 initialisation; returns true if there is nothing to do.
+// Alg. 1 / Alg. 2 initialisation values of pair p: v_0 = nu_0 (mu = 0,
+// sigma = 1), E_0 and its flight from x_0 (eq. intinv), shared by both paths.
 template <typename Real, int RECIPE>
-__device__ __forceinline__ bool het_pair_start(HetPairState<Real> &st, unsigned long long p,
-                                               const HetLevel<Real> &L, const PhiloxKeys &keys,
-                                               bool coupled)
+__device__ __forceinline__ void het_start_values(Real &v0, Real &e0, Real &q0, unsigned long long p,
+                                                 const HetLevel<Real> &L, const PhiloxKeys &keys)
+{
+    const Draw<Real> d0 = draw_r<Real, RECIPE>(0u, (uint32_t)p, L.word2 ^ (uint32_t)(p >> 32),
+                                               L.request, keys);
+    v0 = d0.nu;
+    e0 = d0.E;
+    q0 = L.bg.flight(L.x0, v0, e0);
+}
+
+// The state of pair p at t = 0 from its initialisation values; returns true
+// if there is nothing to do (no collision of either path before T).
+template <typename Real>
+__device__ __forceinline__ bool het_pair_init(HetPairState<Real> &st, unsigned long long p, Real v0,
+                                              Real e0, Real q0, const HetLevel<Real> &L, bool coupled)
 {
     st.pair_lo = (uint32_t)p;
     st.word2 = L.word2 ^ (uint32_t)(p >> 32);
-    const Draw<Real> d0 = draw_r<Real, RECIPE>(0u, st.pair_lo, st.word2, L.request, keys);
     st.xf = L.x0;
-    st.vf = d0.nu;
-    st.Ef = d0.E;
-    st.qf = L.bg.flight(st.xf, st.vf, d0.E);
+    st.vf = v0;
+    st.Ef = e0;
+    st.qf = q0;
     st.i_f = 0;
     st.k = 0;
     st.evc = 0;
@@ -186,6 +198,17 @@ __device__ __forceinline__ bool het_pair_start(HetPairState<Real> &st, unsigned 
     st.fresh = true;
     het_keep_output(st, L);
     return het_fine_done(st, L) && (!coupled || het_coarse_done(st, L));
+}
+
+// Alg. 1 / Alg. 2 initialisation; returns true if there is nothing to do.
+template <typename Real, int RECIPE>
+__device__ __forceinline__ bool het_pair_start(HetPairState<Real> &st, unsigned long long p,
+                                               const HetLevel<Real> &L, const PhiloxKeys &keys,
+                                               bool coupled)
+{
+    Real v0, e0, q0;
+    het_start_values<Real, RECIPE>(v0, e0, q0, p, L, keys);
+    return het_pair_init(st, p, v0, e0, q0, L, coupled);
 }
 
 // One fine KD step, the window terms and, when the window closes, the

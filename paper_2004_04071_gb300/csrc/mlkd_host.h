@@ -42,7 +42,8 @@ struct Derived {
     long long n0;          // T / dt0
     int mode;
     int background;        // mlkd_background
-    bool per_level_only;   // a problem the batched and serving forms do not run
+    bool per_level_only;   // a problem the batched and serving forms do not run (the
+                           // heterogeneous backgrounds run batched, but not served)
     bool periodic;
     double lo, hi, h;
     int J;                 // estimator levels

@@ -159,3 +159,97 @@ def test_a_zero_matches_the_homogeneous_path(mk, ctx):
                                  P(ec, ctypes.c_int64)) == 0
         assert np.array_equal(kf_h, ef) and np.array_equal(kc_h, ec)
         assert fp64_close(xf_h, xf).all() and fp64_close(xc_h, xc).all()
+
+
+BATCH_CASES = ["B1_a10_b100", "B2_a20_b10", "B2_a2_b1000_M4"]
+
+
+@pytest.mark.parametrize("name", BATCH_CASES)
+def test_batched_pairs_match_oracle_fp64(orc, mk, ctx, name):
+    """The batched form runs the heterogeneous pairs one per lane, started
+    from the warp's pool: every pair of every level is the oracle's (equal
+    event counts, positions to 1e-12), and slicing the launch or another
+    idle-lane threshold changes no pair."""
+    d = CASES[name]
+    n = 2001
+    nf = [n] * (d["L"] + 1)
+    pg = gpu_problem(mk, dict(d, n_fixed=nf), precision=mk.PREC_FP64)
+    po = oracle_problem(orc, d)
+    bctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(mk.batch_config(max_requests=64,
+                                                                                 max_nbins=128)))
+    try:
+        for level in sorted({0, 1, d["L"]}):
+            xf_o, xc_o, kf_o, kc_o = orc.pairs(po, level, 0, n, threads=16)
+            base = None
+            for sl, rm in ((0, 0), (7, 1), (64, 32)):
+                cfg = mk.batch_config(pairs_per_thread=2, substeps_per_launch=sl, max_requests=64,
+                                      max_nbins=128, refill_min=rm)
+                r, xf, xc, kf, kc = bctx.debug_batch_pairs(pg, cfg, level)
+                assert np.array_equal(kf, kf_o) and np.array_equal(kc, kc_o), (name, level, sl)
+                assert fp64_close(xf, xf_o).all() and fp64_close(xc, xc_o).all(), (name, level, sl)
+                if base is None:
+                    base = (xf, xc)
+                else:
+                    assert np.array_equal(xf, base[0]) and np.array_equal(xc, base[1])
+    finally:
+        bctx.close()
+
+
+def test_batched_estimates_match_per_level_form(mk, ctx):
+    """B1 and B2 estimated together in one batched call (FP64, adaptive): the
+    same N_l in every level and the same estimates, to FP64 rounding of the
+    sums, as the per-level form one problem at a time."""
+    ds = [dict(CASES["B1_a10_b100"], tol=0.01, L=3, request=3),
+          dict(CASES["B2_a20_b10"], tol=0.01, L=3, request=4, seed=0)]
+    probs = [gpu_problem(mk, d, precision=mk.PREC_FP64) for d in ds]
+    bctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(mk.batch_config(max_requests=64,
+                                                                                 max_nbins=128)))
+    try:
+        rb = bctx.estimate_batch(probs, mk.batch_config(max_requests=64, max_nbins=128))
+    finally:
+        bctx.close()
+    for p, b in zip(probs, rb):
+        r = ctx.estimate(p)
+        assert [lv["n"] for lv in b.levels] == [lv["n"] for lv in r.levels]
+        assert [lv["events_f"] for lv in b.levels] == [lv["events_f"] for lv in r.levels]
+        assert b.estimate == pytest.approx(r.estimate, rel=1e-12, abs=1e-14)
+        assert b.variance == pytest.approx(r.variance, rel=1e-9)
+
+
+def test_batched_fp32_pairs_within_bound(orc, mk, ctx):
+    """FP32 pairs of the batched form against the oracle on the 24-bit stream
+    within the per-pair FP32 bound; pairs whose event sequence differs stay
+    rare."""
+    d = CASES["B2_a20_b10"]
+    n = 20000
+    nf = [n] * (d["L"] + 1)
+    pg = gpu_problem(mk, dict(d, n_fixed=nf), precision=mk.PREC_FP32_COMP)
+    po = oracle_problem(orc, d, recipe=orc.RECIPE_24)
+    bctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(mk.batch_config(max_requests=64,
+                                                                                 max_nbins=128)))
+    try:
+        for level in (0, 2, d["L"]):
+            _, xf, xc, kf, kc = bctx.debug_batch_pairs(pg, mk.batch_config(max_requests=64, max_nbins=128),
+                                                      level)
+            xf_o, xc_o, kf_o, kc_o = orc.pairs(po, level, 0, n, threads=16)
+            same = (kf == kf_o) & (kc == kc_o)
+            assert (~same).sum() <= 1e-3 * n
+            ev = kf_o + kc_o
+            for g, o in ((xf, xf_o), (xc, xc_o)):
+                assert np.all(np.abs(g - o)[same] <= B.pair_delta(o, ev)[same])
+    finally:
+        bctx.close()
+
+
+def test_mixed_batch_is_rejected(mk):
+    """One batched call holds either homogeneous or heterogeneous problems."""
+    het = gpu_problem(mk, dict(CASES["B1_a10_b100"], tol=0.01), precision=mk.PREC_FP64)
+    hom = gpu_problem(mk, dict(eps=0.5, T=0.5, dt0=0.1, M=2, L=2, qoi=0, init=0, nbins=0, tol=0.01,
+                               seed=0), precision=mk.PREC_FP64)
+    bctx = mk.Context(0, arena_bytes=mk.batch_workspace_bytes(mk.batch_config(max_requests=64,
+                                                                                 max_nbins=128)))
+    try:
+        with pytest.raises(mk.MlkdError):
+            bctx.estimate_batch([het, hom], mk.batch_config(max_requests=64, max_nbins=128))
+    finally:
+        bctx.close()
