@@ -53,10 +53,11 @@ KERNEL_SOURCES = ("mlkd_batch.cu", "mlkd_pair.cuh", "mlkd_warp_pair.cuh", "mlkd_
                   "mlkd_internal.h")
 TTT_RUNS = 11
 # N_l of the benchmark's adaptive pilot at tol 1e-3 (eps = 1, 0.1, 1e-3; as
-# measured on GB300 with the FP32_COMP batched form), for the fixed ncu case.
-PILOT_N_FIXED = [[352000, 181600],
-                 [9000000, 3040000, 2560000, 3144000, 2544000, 2000000, 1584000, 1352000, 800000],
-                 [6280000, 800, 800, 800, 800, 800, 800, 800, 800, 800, 18320, 19440, 20800]]
+# measured on GB300 with the FP32_COMP batched form): the workload of the
+# fixed kernel case and of the reference arm's oracle sample.
+PILOT_N_FIXED = [[351986, 181831],
+                 [9003929, 3045177, 2556430, 3143927, 2544690, 1996396, 1586634, 1349951, 802694],
+                 [6284046, 100, 100, 101, 125, 162, 264, 385, 544, 766, 18804, 19460, 20769]]
 SMSP_PER_SM = 4
 LANES = 32
 
@@ -462,16 +463,14 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def oracle_sample(cpu_seconds: float, fixed=None, threads=None):
+def oracle_sample(cpu_seconds: float, fixed, threads=None):
     """Times the oracle on a bounded sample of the workload.  Each round runs,
     for every eps and level, a slice of pairs proportional to that level's
-    N_l (at least 32), continuing the pair index where the last round
-    stopped; rounds repeat until about `cpu_seconds` have passed, on
+    N_l in `fixed` (at least 32), continuing the pair index where the last
+    round stopped; rounds repeat until about `cpu_seconds` have passed, on
     `threads` host threads (default: all cores)."""
     import oracle as O
     threads = threads or os.cpu_count() or 1
-    if fixed is None:
-        fixed = [[max(100, 2 ** (12 - l)) for l in range(W.periodic_levels(e) + 1)] for e in EPS_SET]
     total = float(sum(sum(n) for n in fixed))
     per_round = 2e5                                   # pairs per round over all levels
     probs = []
@@ -493,7 +492,7 @@ def oracle_sample(cpu_seconds: float, fixed=None, threads=None):
         if dt >= cpu_seconds:
             break
     pairs = sum(sum(x) for x in nxt)
-    return {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+    return {"value": ev / dt, "unit": UNIT, "cores": threads, "kind": "oracle", "seconds": dt,
             "sample": "%d rounds over every eps and level of the workload, pairs per level "
                       "proportional to N_l (>= 32): %d pairs, %d events in %.1f s"
                       % (rounds, pairs, ev, dt)}
@@ -553,17 +552,19 @@ def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
+    # the GPU arm's workload: the benchmark's N_l per estimate and level
     per_step = max(1.0, min(15.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        oracle_sample(per_step / 4)
-    vals, evs, secs = [], 0, 0.0
+        oracle_sample(per_step / 4, PILOT_N_FIXED)
+    vals, secs = [], []
     last = None
     for _ in range(args.steps):
-        last = oracle_sample(per_step)
+        last = oracle_sample(per_step, PILOT_N_FIXED)
         vals.append(last["value"])
+        secs.append(last["seconds"])
     value = statistics.mean(vals)
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic (Philox streams; analytic homogeneous background)",
            "config": {"workload": "periodic full MLMC, eps in {1,0.1,1e-3}, T=1, dt0=0.5, M=2, "
