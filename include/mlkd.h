@@ -169,6 +169,23 @@ MLKD_API const char *mlkd_status_string(int status);
 /* MLKD_ABI_VERSION of the loaded library. */
 MLKD_API int mlkd_abi_version(void);
 
+/* Debug build.  libmlkd_checked.so is the same library compiled with device
+ * checks: indexes into the kernels' shared-memory pools, histograms, block
+ * partial rows, debug outputs and stored slice words are checked before use.
+ * A failed check records its source line, clamps the index into bounds (no
+ * out-of-bounds access, no trap) and the synchronising call that ran the
+ * kernel (mlkd_run_level, mlkd_estimate*, mlkd_estimate_batch, the debug
+ * readouts) returns MLKD_EINTERNAL.  mlkd_device_checks returns 1 in that
+ * library and 0 in the normal one, and writes the line of the last failed
+ * check (0: none) to *last_line if it is not NULL. */
+MLKD_API int mlkd_device_checks(uint32_t *last_line);
+
+/* Debug build only: launches one kernel on `device` whose device check fails
+ * on purpose and returns what the checks report (MLKD_EINTERNAL when the
+ * failure was recorded and found).  The normal library returns
+ * MLKD_ENOTFOUND. */
+MLKD_API mlkd_status mlkd_debug_check_selftest(int device);
+
 /* Bytes of device arena a context needs to run this problem with
  * mlkd_run_level / mlkd_estimate / mlkd_debug_pairs.  Returns 0 if the
  * problem is invalid. */

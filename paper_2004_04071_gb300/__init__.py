@@ -14,7 +14,9 @@ from dataclasses import dataclass
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libmlkd.so")
+# MLKD_CHECKED=1 loads the debug build, the same library with device checks
+LIB_PATH = os.path.join(_HERE, "_lib", "libmlkd_checked.so" if os.environ.get("MLKD_CHECKED") == "1"
+                        else "libmlkd.so")
 
 MLKD_OK = 0
 MLKD_EINVAL = -1
@@ -41,7 +43,8 @@ EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_poll", "mlkd_cancel", "mlkd_server_stats_get", "mlkd_server_stop",
             "mlkd_debug_transforms", "mlkd_level_select", "mlkd_estimate_resumable",
             "mlkd_level_select_opt", "mlkd_level_pilot", "mlkd_level_warmup",
-            "mlkd_estimate_sequence", "mlkd_debug_batch_pairs", "mlkd_debug_coarse_draws"]
+            "mlkd_estimate_sequence", "mlkd_debug_batch_pairs", "mlkd_debug_coarse_draws",
+            "mlkd_device_checks", "mlkd_debug_check_selftest"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -150,6 +153,10 @@ def lib():
         if L.mlkd_abi_version() != ABI_VERSION:
             raise RuntimeError("libmlkd.so has ABI version %d, the binding expects %d; rebuild it"
                                % (L.mlkd_abi_version(), ABI_VERSION))
+        L.mlkd_device_checks.argtypes = [P(ctypes.c_uint32)]
+        L.mlkd_device_checks.restype = ctypes.c_int
+        L.mlkd_debug_check_selftest.argtypes = [ctypes.c_int]
+        L.mlkd_debug_check_selftest.restype = ctypes.c_int
         L.mlkd_workspace_bytes.argtypes = [P(Problem)]
         L.mlkd_workspace_bytes.restype = ctypes.c_size_t
         L.mlkd_context_create.argtypes = [ctypes.c_int, vp, ctypes.c_size_t, P(vp)]
@@ -261,6 +268,20 @@ def debug_transforms(words_dev, log_dev=None, sin_dev=None, cos_dev=None, stream
     ptr = lambda t: vp(t.data_ptr()) if t is not None else vp(0)
     _check(lib().mlkd_debug_transforms(ptr(words_dev), words_dev.numel(), ptr(log_dev), ptr(sin_dev),
                                        ptr(cos_dev), _stream_handle(stream)), "mlkd_debug_transforms")
+
+
+def device_checks():
+    """mlkd_device_checks: (1 in the debug build with device checks, else 0;
+    source line of the last failed check, 0 if none)."""
+    line = ctypes.c_uint32()
+    on = lib().mlkd_device_checks(ctypes.byref(line))
+    return int(on), int(line.value)
+
+
+def debug_check_selftest(device: int = 0) -> int:
+    """mlkd_debug_check_selftest: the status the checks report for a kernel
+    whose check fails on purpose (debug build: MLKD_EINTERNAL)."""
+    return int(lib().mlkd_debug_check_selftest(device))
 
 
 def level_select(V, Vd):

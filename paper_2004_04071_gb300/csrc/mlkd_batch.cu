@@ -134,6 +134,7 @@ struct BatchLaunch {
     WarpHdr *hdr;                // [grid warps]
     int32_t *status_out;         // [slots]: status after the scheduler (host-readable copy)
     uint32_t *lane_words;        // [words][grid lanes]: pair states and sums per lane
+    int32_t lane_word_count;     // words allocated per lane
     unsigned long long *q_ids;   // [ring]: queue of chunk ids
     unsigned long long *l_ids;   // [ring]: queue of long chunks' ids
     unsigned long long *p_ids;   // [ring]: queue of the chunks of small rounds
@@ -599,6 +600,11 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     unsigned int *wh = s_hist_all + (size_t)warp * 3 * B.max_nbins;
     WarpHdr *hdr = B.hdr + gw;
 
+    // the stored slice state of this instantiation fits the words per lane
+    if (!MLKD_DCHECK(lane_words<Real, MODE, PPT, PHYS>() <= B.lane_word_count)) {
+        if (threadIdx.x == 0) atomicExch(&B.ctl->error, 2);
+        return;
+    }
     int valid = hdr->valid;
     int iters = 0;
     int idle = 0;
@@ -694,7 +700,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         ev_f_sum += kf;
         ev_c_sum += kc;
         const int nbins = X.nbins;
-        if (nbins > 0) {
+        if (nbins > 0 && MLKD_DCHECK(nbins <= B.max_nbins)) {
             Bins bins;
             bins.lo = X.blo;
             bins.hi = X.bhi;
@@ -705,9 +711,10 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             bins.nbins = nbins;
             bins.periodic = X.per != 0;
             const int bf = bins(xf);
-            if (bf >= 0) atomicAdd(&wh[bf], 1u);
+            if (bf >= 0 && MLKD_DCHECK(bf < nbins)) atomicAdd(&wh[bf], 1u);
             if (coupled) {
                 const int bc = bins(xc);
+                if (!MLKD_DCHECK(bc < nbins)) return;
                 if (bc >= 0) atomicAdd(&wh[nbins + bc], 1u);
                 if (bc >= 0 && bc == bf) atomicAdd(&wh[2 * nbins + bf], 1u);
             }
@@ -749,8 +756,10 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     // move the rest to the front.  All lanes call it.
     auto fp_process = [&](int cnt) {
         __syncwarp();
+        if (!MLKD_DCHECK(cnt >= 0 && cnt <= 32)) cnt = 0;
         if (lane < cnt) account(FP.xf[lane], FP.xc[lane], FP.kf[lane], FP.kc[lane]);
-        const int rest = X.fp_n - cnt;
+        int rest = X.fp_n - cnt;
+        if (!MLKD_DCHECK(rest >= 0 && rest <= 32)) rest = 0;
         Real a = Real(0), b = Real(0);
         uint32_t ka = 0u, kb = 0u;
         if (lane < rest) {
@@ -775,7 +784,8 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         const unsigned m = __ballot_sync(kFullMask, f);
         const int n0 = X.fp_n;
         if (f) {
-            const int i = n0 + __popc(m & lanemask_lt());
+            int i = n0 + __popc(m & lanemask_lt());
+            if (!MLKD_DCHECK(i < 64)) i = 63;
             FP.xf[i] = xf;
             FP.xc[i] = xc;
             FP.kf[i] = kf;
@@ -1028,7 +1038,8 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                         const int avail = sn - si;
                         const int rank = __popc(im & lanemask_lt());
                         if (!active[j] && rank < avail) {
-                            const int e = si + rank;
+                            int e = si + rank;
+                            if (!MLKD_DCHECK(e < 32)) e = 31;
                             const unsigned long long pe = X.first + (unsigned long long)SP.off[e];
                             if constexpr (PHYS == 1)
                                 het_pair_init<Real>(st[j], pe, SP.v0[e], SP.e0[e], SP.q0[e], H, coupled);
@@ -1198,6 +1209,7 @@ __global__ void batch_post_kernel(BatchCtl *ctl, int *live_out, cudaGraphConditi
 // ---------------------------------------------------------------------------
 struct BatchLayout {
     size_t desc, state, chunks, rows, qids, lids, pids, hist, ctl, live, hdr, lanes, status, total;
+    size_t words;                // lane words per lane
     unsigned long long ring;
 };
 
@@ -1243,6 +1255,7 @@ static BatchLayout batch_layout(const mlkd_batch_config *c)
                                                    lane_words<double, kModeFP64, 1>()),
                                           std::max(lane_words<float, kModeFP32Comp, 1, 1>(),
                                                    lane_words<double, kModeFP64, 1, 1>()));
+    B.words = words;
     B.lanes = off; off = align_up(off + words * kMaxLanes * sizeof(uint32_t));
     B.status = off; off = align_up(off + (size_t)c->max_requests * sizeof(int32_t));
     B.total = off;
@@ -1358,6 +1371,7 @@ static void make_launch(mlkd_context *ctx, const BatchLayout &BL, const mlkd_bat
     B->ctl = (BatchCtl *)(ctx->arena + BL.ctl);
     B->hdr = (WarpHdr *)(ctx->arena + BL.hdr);
     B->lane_words = (uint32_t *)(ctx->arena + BL.lanes);
+    B->lane_word_count = (int32_t)BL.words;
     B->q_ids = (unsigned long long *)(ctx->arena + BL.qids);
     B->l_ids = (unsigned long long *)(ctx->arena + BL.lids);
     B->p_ids = (unsigned long long *)(ctx->arena + BL.pids);
@@ -1620,7 +1634,7 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         }
         o->seconds = secs;
     }
-    return MLKD_OK;
+    return device_checks();
 }
 
 // ---------------------------------------------------------------------------
@@ -1917,6 +1931,22 @@ static mlkd_status server_start(mlkd_context *ctx, const mlkd_server_config *cfg
     ctx->server = S;
     S->th = std::thread(server_loop, S);
     return MLKD_OK;
+}
+
+cudaError_t check_word_batch(unsigned *line)
+{
+    *line = 0u;
+#ifdef MLKD_CHECKS
+    cudaError_t e = cudaMemcpyFromSymbol(line, g_mlkd_check_line, sizeof(unsigned));
+    if (e != cudaSuccess) return e;
+    if (*line) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_mlkd_check_line, &zero, sizeof(unsigned));
+    }
+    return e;
+#else
+    return cudaSuccess;
+#endif
 }
 
 }  // namespace mlkd

@@ -218,6 +218,22 @@ mlkd_status choose_grid(mlkd_context *ctx, int mode, bool coupled, int nbins, ui
 
 }  // namespace
 
+static unsigned g_last_check_line = 0;   // source line of the last failed device check
+
+mlkd_status mlkd::device_checks()
+{
+#ifdef MLKD_CHECKS
+    unsigned a = 0u, b = 0u;
+    MLKD_CUDA(check_word_kernels(&a));
+    MLKD_CUDA(check_word_batch(&b));
+    if (a || b) {
+        g_last_check_line = a ? a : b;
+        return MLKD_EINTERNAL;
+    }
+#endif
+    return MLKD_OK;
+}
+
 // Adds the elapsed time of every recorded pair-kernel launch (waiting for
 // each to end; the launches may be on several streams).
 mlkd_status mlkd::harvest_timing(mlkd_context *ctx)
@@ -253,6 +269,7 @@ mlkd_status enqueue_level(mlkd_context *ctx, const mlkd_problem *p, const Derive
     if (st != MLKD_OK) return st;
     P.pairs_per_warp = ppw;
     P.partials = partials;
+    P.partial_rows = kMaxBlocks;
     P.hist = p->nbins > 0 ? tmp_hist : nullptr;
     P.dbg_xf = dxf;
     P.dbg_xc = dxc;
@@ -295,6 +312,29 @@ void to_host_stats(const DevLevelStats &s, mlkd_level_stats *o)
 }  // namespace
 
 extern "C" {
+
+int mlkd_device_checks(uint32_t *last_line)
+{
+    if (last_line) *last_line = g_last_check_line;
+#ifdef MLKD_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+mlkd_status mlkd_debug_check_selftest(int device)
+{
+#ifdef MLKD_CHECKS
+    MLKD_CUDA(cudaSetDevice(device));
+    MLKD_CUDA(launch_check_selftest(0));
+    MLKD_CUDA(cudaDeviceSynchronize());
+    return device_checks();
+#else
+    (void)device;
+    return MLKD_ENOTFOUND;
+#endif
+}
 
 const char *mlkd_status_string(int status)
 {
@@ -592,7 +632,8 @@ mlkd_status mlkd_run_level(mlkd_context *ctx, const mlkd_problem *problem, int l
                                   cudaMemcpyDeviceToHost, s));
     MLKD_CUDA(cudaStreamSynchronize(s));
     to_host_stats(hs, out);
-    return harvest_timing(ctx);
+    st = harvest_timing(ctx);
+    return st != MLKD_OK ? st : device_checks();
 }
 
 mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int level,
@@ -798,7 +839,8 @@ static mlkd_status estimate_impl(mlkd_context *ctx, const mlkd_problem *problem,
         out->cost_level[l] = ctl.cost_level[l];
     }
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    return harvest_timing(ctx);
+    const mlkd_status hst = harvest_timing(ctx);
+    return hst != MLKD_OK ? hst : device_checks();
 }
 
 extern "C" {
@@ -963,6 +1005,7 @@ extern "C" mlkd_status mlkd_run_level_noalloc(const mlkd_problem *problem, int l
     fill_launch(problem, d, level, first_pair, n_pairs, &P);
     P.pairs_per_warp = (n_pairs + warps - 1) / warps;
     P.partials = (double *)scratch;
+    P.partial_rows = MLKD_NOALLOC_MAX_BLOCKS;
     P.hist = problem->nbins > 0 ? (unsigned long long *)(scratch + kNoAllocHistOffset) : nullptr;
     DevLevelStats *dstats = (DevLevelStats *)(scratch + kNoAllocStatsOffset);
     if (problem->nbins > 0)   // counters keep the previous call's values

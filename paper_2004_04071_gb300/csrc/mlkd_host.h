@@ -69,6 +69,9 @@ namespace mlkd {
 void batch_release(mlkd_context *ctx);   // frees the batch graph cache (host side)
 void server_release(mlkd_context *ctx);  // stops a running server
 mlkd_status harvest_timing(mlkd_context *ctx);
+// Debug builds: MLKD_EINTERNAL if a device check failed since the last call
+// (the caller has synchronised); MLKD_OK always in normal builds.
+mlkd_status device_checks();
 }
 
 struct mlkd_context {

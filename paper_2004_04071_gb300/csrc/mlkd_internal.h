@@ -15,6 +15,33 @@ constexpr int kPartialWords = 8;       // sy, sy2, sqf, sqf2, sqc, sqc2, ev_f, e
 
 enum Mode { kModeFP64 = 0, kModeFP32DY64 = 1, kModeFP32Comp = 2, kModeFP64U24 = 3 };
 
+// Device checks of the debug build (compiled with -DMLKD_CHECKS, the library
+// libmlkd_checked.so).  MLKD_DCHECK(c) evaluates c; if it is false it records
+// the source line in this translation unit's check word (the first failure
+// wins) and yields false, so that the caller clamps its index into bounds and
+// goes on: a failed check never touches memory out of bounds, traps or
+// stops the kernel.  The host reads the words after each synchronising call
+// and returns MLKD_EINTERNAL.  In normal builds MLKD_DCHECK(c) is the
+// constant true and compiles to nothing.
+#ifdef MLKD_CHECKS
+static __device__ unsigned int g_mlkd_check_line;
+__device__ __forceinline__ bool check_record(bool ok, int line)
+{
+    if (!ok) atomicCAS(&g_mlkd_check_line, 0u, (unsigned)line);
+    return ok;
+}
+#define MLKD_DCHECK(...) (::mlkd::check_record((__VA_ARGS__), __LINE__))
+#else
+#define MLKD_DCHECK(...) true
+#endif
+
+// Reads and clears the check word of one translation unit (0: no failure;
+// always 0 in normal builds).
+cudaError_t check_word_kernels(unsigned *line);
+cudaError_t check_word_batch(unsigned *line);
+// Launches one kernel whose check fails on purpose (checked builds only).
+cudaError_t launch_check_selftest(cudaStream_t stream);
+
 // Random-number recipe of a mode: 1 = 24-bit uniforms in FP64 arithmetic.
 template <int MODE> struct ModeRecipe { static constexpr int value = MODE == kModeFP64U24 ? 1 : 0; };
 
@@ -58,6 +85,7 @@ struct PairLaunch {
     BgParams<float> bf;
     unsigned long long first_pair, n_pairs, pairs_per_warp;
     double *partials;                  // [gridDim.x][kPartialWords]
+    int32_t partial_rows;              // rows the partials buffer holds (>= gridDim.x)
     unsigned long long *hist;          // [3][nbins] fine, coarse, both; or null
     double *dbg_xf, *dbg_xc;           // optional per-pair outputs
     int32_t *dbg_kf, *dbg_kc;

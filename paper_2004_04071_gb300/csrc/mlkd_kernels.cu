@@ -117,15 +117,17 @@ pair_kernel(const __grid_constant__ PairLaunch P)
         ev_f_sum += st.k;
         ev_c_sum += st.evc;
         if (nbins > 0) {
-            const int bf = bins(st.xf);
+            int bf = bins(st.xf);
+            if (!MLKD_DCHECK(bf < nbins)) bf = -1;
             if (bf >= 0) atomicAdd(&s_hist[bf], 1u);
             if (COUPLED) {
-                const int bc = bins(st.xc);
+                int bc = bins(st.xc);
+                if (!MLKD_DCHECK(bc < nbins)) bc = -1;
                 if (bc >= 0) atomicAdd(&s_hist[nbins + bc], 1u);
                 if (bc >= 0 && bc == bf) atomicAdd(&s_hist[2 * nbins + bf], 1u);
             }
         }
-        if (P.dbg_xf) {
+        if (P.dbg_xf && MLKD_DCHECK(pair - P.first_pair < P.n_pairs)) {
             const unsigned long long j = pair - P.first_pair;
             P.dbg_xf[j] = (double)st.xf;
             if (P.dbg_xc) P.dbg_xc[j] = COUPLED ? (double)st.xc : 0.0;
@@ -198,7 +200,7 @@ pair_kernel(const __grid_constant__ PairLaunch P)
         s_red[warp][7] = (double)ev_c_sum;
     }
     __syncthreads();
-    if (threadIdx.x < kPartialWords) {
+    if (threadIdx.x < kPartialWords && MLKD_DCHECK(blockIdx.x < (unsigned)P.partial_rows)) {
         double acc = 0.0;
 #pragma unroll
         for (int w = 0; w < kWarpsPerBlock; ++w) acc += s_red[w][threadIdx.x];
@@ -499,6 +501,43 @@ cudaError_t launch_hist_accumulate(const unsigned long long *hist, unsigned long
     if (count <= 0) return cudaSuccess;
     hist_accumulate_kernel<<<(count + 255) / 256, 256, 0, stream>>>(hist, acc, count);
     return cudaGetLastError();
+}
+
+#ifdef MLKD_CHECKS
+__global__ void check_selftest_kernel(int n)
+{
+    // a check that fails on purpose: the index stays clamped, nothing is written
+    int i = n;
+    if (!MLKD_DCHECK(i < 0)) i = 0;
+    (void)i;
+}
+#endif
+
+cudaError_t launch_check_selftest(cudaStream_t stream)
+{
+#ifdef MLKD_CHECKS
+    check_selftest_kernel<<<1, 32, 0, stream>>>(1);
+    return cudaGetLastError();
+#else
+    (void)stream;
+    return cudaErrorNotSupported;
+#endif
+}
+
+cudaError_t check_word_kernels(unsigned *line)
+{
+    *line = 0u;
+#ifdef MLKD_CHECKS
+    cudaError_t e = cudaMemcpyFromSymbol(line, g_mlkd_check_line, sizeof(unsigned));
+    if (e != cudaSuccess) return e;
+    if (*line) {
+        const unsigned zero = 0u;
+        e = cudaMemcpyToSymbol(g_mlkd_check_line, &zero, sizeof(unsigned));
+    }
+    return e;
+#else
+    return cudaSuccess;
+#endif
 }
 
 }  // namespace mlkd
