@@ -310,6 +310,20 @@ MLKD_API mlkd_status mlkd_level_warmup(mlkd_context *ctx, const mlkd_problem *pr
                                        uint64_t n_warmup, void *stream, double *V, double *Vd,
                                        int32_t *tau_out);
 
+/* Validation aid: the KD coefficients of eqs. advection/diffusion and the
+ * aggregation quantities of Sec. 3.2 exactly as the pair kernels compute them
+ * in `precision` (FP64 state for MLKD_PREC_FP64 and _FP64_U24, FP32 state for
+ * the FP32 modes), for a background (R > 0, mu, sigma >= 0) and n pairs
+ * (theta_i, dv_i = v'_i - mu) of device FP64 arrays.  Writes, as FP64 device
+ * arrays of n: a, d, hs = h(R theta) = e^{-s} + s - 1, om = 1 - e^{-s} and
+ * beta_hat_sq = 2 h(h(s)) = (beta R / sigma)^2 (eq. weights-beta).  The level
+ * constants are prepared as for a launch (1/R and 2 sigma^2/R^2 in FP64,
+ * rounded once).  Synchronous. */
+MLKD_API mlkd_status mlkd_debug_kd_coeffs(int precision, double R, double mu, double sigma,
+                                         const double *theta, const double *dv, uint64_t n,
+                                         double *a, double *d, double *hs, double *om,
+                                         double *beta_hat_sq, void *stream);
+
 /* Validation aid: the FP32 variate transforms of the pair kernel applied to
  * n 32-bit Philox output words (device array `words`).  With the 24-bit
  * uniform u = ((w >> 8) + 1) 2^-24 of each word it writes log u, sin 2 pi u and

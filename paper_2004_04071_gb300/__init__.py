@@ -44,7 +44,7 @@ EXPORTED = ["mlkd_status_string", "mlkd_abi_version", "mlkd_workspace_bytes",
             "mlkd_debug_transforms", "mlkd_level_select", "mlkd_estimate_resumable",
             "mlkd_level_select_opt", "mlkd_level_pilot", "mlkd_level_warmup",
             "mlkd_estimate_sequence", "mlkd_debug_batch_pairs", "mlkd_debug_coarse_draws",
-            "mlkd_device_checks", "mlkd_debug_check_selftest"]
+            "mlkd_device_checks", "mlkd_debug_check_selftest", "mlkd_debug_kd_coeffs"]
 NOALLOC_MAX_BINS = 256
 
 
@@ -157,6 +157,9 @@ def lib():
         L.mlkd_device_checks.restype = ctypes.c_int
         L.mlkd_debug_check_selftest.argtypes = [ctypes.c_int]
         L.mlkd_debug_check_selftest.restype = ctypes.c_int
+        L.mlkd_debug_kd_coeffs.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, vp, vp, u64, vp, vp, vp, vp, vp, vp]
+        L.mlkd_debug_kd_coeffs.restype = ctypes.c_int
         L.mlkd_workspace_bytes.argtypes = [P(Problem)]
         L.mlkd_workspace_bytes.restype = ctypes.c_size_t
         L.mlkd_context_create.argtypes = [ctypes.c_int, vp, ctypes.c_size_t, P(vp)]
@@ -282,6 +285,19 @@ def debug_check_selftest(device: int = 0) -> int:
     """mlkd_debug_check_selftest: the status the checks report for a kernel
     whose check fails on purpose (debug build: MLKD_EINTERNAL)."""
     return int(lib().mlkd_debug_check_selftest(device))
+
+
+def debug_kd_coeffs(precision, R, mu, sigma, theta_dev, dv_dev, stream=None):
+    """mlkd_debug_kd_coeffs on torch FP64 device tensors: returns the device
+    tensors (a, d, hs, om, beta_hat_sq)."""
+    import torch
+    n = theta_dev.numel()
+    outs = [torch.empty(n, dtype=torch.float64, device=theta_dev.device) for _ in range(5)]
+    vp = ctypes.c_void_p
+    _check(lib().mlkd_debug_kd_coeffs(precision, R, mu, sigma, vp(theta_dev.data_ptr()),
+                                      vp(dv_dev.data_ptr()), n, *[vp(t.data_ptr()) for t in outs],
+                                      _stream_handle(stream)), "mlkd_debug_kd_coeffs")
+    return tuple(outs)
 
 
 def level_select(V, Vd):

@@ -572,6 +572,21 @@ mlkd_status mlkd_debug_transforms(const uint32_t *words, uint64_t n, float *log_
     return MLKD_OK;
 }
 
+mlkd_status mlkd_debug_kd_coeffs(int precision, double R, double mu, double sigma,
+                                 const double *theta, const double *dv, uint64_t n, double *a,
+                                 double *d, double *hs, double *om, double *beta_hat_sq,
+                                 void *stream)
+{
+    if (precision < MLKD_PREC_FP64 || precision > MLKD_PREC_FP64_U24) return MLKD_EINVAL;
+    if (!(R > 0.0) || !std::isfinite(R) || !std::isfinite(mu) || !(sigma >= 0.0)) return MLKD_EINVAL;
+    if (n > 0 && (!theta || !dv || !a || !d || !hs || !om || !beta_hat_sq)) return MLKD_EINVAL;
+    const int fp64 = precision == MLKD_PREC_FP64 || precision == MLKD_PREC_FP64_U24;
+    cudaStream_t s = (cudaStream_t)stream;
+    MLKD_CUDA(launch_debug_kd(fp64, R, mu, sigma, theta, dv, n, a, d, hs, om, beta_hat_sq, s));
+    MLKD_CUDA(cudaStreamSynchronize(s));
+    return device_checks();
+}
+
 mlkd_status mlkd_context_set_timing(mlkd_context *ctx, int enable)
 {
     if (!ctx) return MLKD_EINVAL;

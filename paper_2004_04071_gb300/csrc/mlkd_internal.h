@@ -127,6 +127,9 @@ cudaError_t launch_coarse_draws(int mode, const PairLaunch &p, int per_pair, dou
                                 double *chi, int32_t *count, cudaStream_t stream);
 
 // FP32 variate transforms of n words (validation).
+cudaError_t launch_debug_kd(int fp64, double R, double mu, double sigma, const double *theta,
+                            const double *dv, unsigned long long n, double *a, double *d, double *hs,
+                            double *om, double *bh2, cudaStream_t stream);
 cudaError_t launch_debug_transforms(const uint32_t *words, unsigned long long n, float *log_u,
                                     float *sn, float *cs, cudaStream_t stream);
 

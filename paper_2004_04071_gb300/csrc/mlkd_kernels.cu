@@ -336,6 +336,47 @@ cudaError_t launch_coarse_draws(int mode, const PairLaunch &p, int per_pair, dou
     return cudaGetLastError();
 }
 
+// KD coefficients of eqs. advection/diffusion and the aggregation quantities
+// exactly as the pair kernels compute them in precision Real, for given
+// (theta, v' - mu); the level constants are prepared as for a launch (FP64 on
+// the host, rounded once to Real).
+template <typename Real>
+__global__ void debug_kd_kernel(double R, double mu, double sigma, const double *theta,
+                                const double *dv, unsigned long long n, double *a, double *d,
+                                double *hs, double *om, double *bh2)
+{
+    Background<Real> bg;
+    bg.R = (Real)R;
+    bg.invR = (Real)(1.0 / R);
+    bg.mu = (Real)mu;
+    bg.sigma = (Real)sigma;
+    bg.two_c2 = (Real)(2.0 * sigma * sigma / (R * R));
+    for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        Real ai, di, hsi, omi;
+        bg.kd_coeffs((Real)theta[i], (Real)dv[i], ai, di, hsi, omi);
+        a[i] = (double)ai;
+        d[i] = (double)di;
+        hs[i] = (double)hsi;
+        om[i] = (double)omi;
+        bh2[i] = (double)bg.beta_hat_sq(hsi);
+    }
+}
+
+cudaError_t launch_debug_kd(int fp64, double R, double mu, double sigma, const double *theta,
+                            const double *dv, unsigned long long n, double *a, double *d, double *hs,
+                            double *om, double *bh2, cudaStream_t stream)
+{
+    if (n == 0) return cudaSuccess;
+    const unsigned long long blocks = (n + 255) / 256;
+    const unsigned g = (unsigned)(blocks < 65536 ? blocks : 65536);
+    if (fp64)
+        debug_kd_kernel<double><<<g, 256, 0, stream>>>(R, mu, sigma, theta, dv, n, a, d, hs, om, bh2);
+    else
+        debug_kd_kernel<float><<<g, 256, 0, stream>>>(R, mu, sigma, theta, dv, n, a, d, hs, om, bh2);
+    return cudaGetLastError();
+}
+
 __global__ void debug_transforms_kernel(const uint32_t *words, unsigned long long n, float *log_u,
                                         float *sn, float *cs)
 {
