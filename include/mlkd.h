@@ -175,7 +175,10 @@ MLKD_API int mlkd_abi_version(void);
  * A failed check records its source line, clamps the index into bounds (no
  * out-of-bounds access, no trap) and the synchronising call that ran the
  * kernel (mlkd_run_level, mlkd_estimate*, mlkd_estimate_batch, the debug
- * readouts) returns MLKD_EINTERNAL.  mlkd_device_checks returns 1 in that
+ * readouts) returns MLKD_EINTERNAL.  Its arena layout also has 256 canary
+ * bytes after every region, compared after those calls (MLKD_EINTERNAL if
+ * one changed), so it needs a little more arena (mlkd_workspace_bytes and
+ * mlkd_batch_workspace_bytes of that library say how much).  mlkd_device_checks returns 1 in that
  * library and 0 in the normal one, and writes the line of the last failed
  * check (0: none) to *last_line if it is not NULL. */
 MLKD_API int mlkd_device_checks(uint32_t *last_line);

@@ -1211,6 +1211,8 @@ struct BatchLayout {
     size_t desc, state, chunks, rows, qids, lids, pids, hist, ctl, live, hdr, lanes, status, total;
     size_t words;                // lane words per lane
     unsigned long long ring;
+    size_t guard[kMaxGuards];    // canary offsets (debug build)
+    int n_guard;
 };
 
 static bool batch_cfg_ok(const mlkd_batch_config *c)
@@ -1240,24 +1242,35 @@ static BatchLayout batch_layout(const mlkd_batch_config *c)
     while (ring < 2 * ids) ring <<= 1;
     B.ring = ring;
     size_t off = arena_layout().total;
-    B.desc = off;  off = align_up(off + (size_t)c->max_requests * sizeof(ReqDesc));
-    B.state = off; off = align_up(off + (size_t)c->max_requests * sizeof(ReqState));
-    B.chunks = off; off = align_up(off + (size_t)ids * sizeof(Chunk));
-    B.rows = off;  off = align_up(off + (size_t)ids * kPartialWords * sizeof(double));
-    B.qids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
-    B.lids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
-    B.pids = off;  off = align_up(off + (size_t)ring * sizeof(unsigned long long));
-    B.hist = off;  off = align_up(off + (size_t)c->max_requests * kBL * 3 * (size_t)(c->max_nbins > 0 ? c->max_nbins : 1) * sizeof(unsigned long long));
-    B.ctl = off;   off = align_up(off + sizeof(BatchCtl));
-    B.live = off;  off = align_up(off + sizeof(int));
-    B.hdr = off;   off = align_up(off + (kMaxLanes / 32) * sizeof(WarpHdr));
+    B.n_guard = 0;
+    // a region of `bytes` at the current offset, then (debug build) its canary
+    auto place = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        if (kGuardBytes) {
+            B.guard[B.n_guard++] = off;
+            off += kGuardBytes;
+        }
+        return at;
+    };
+    B.desc = place((size_t)c->max_requests * sizeof(ReqDesc));
+    B.state = place((size_t)c->max_requests * sizeof(ReqState));
+    B.chunks = place((size_t)ids * sizeof(Chunk));
+    B.rows = place((size_t)ids * kPartialWords * sizeof(double));
+    B.qids = place((size_t)ring * sizeof(unsigned long long));
+    B.lids = place((size_t)ring * sizeof(unsigned long long));
+    B.pids = place((size_t)ring * sizeof(unsigned long long));
+    B.hist = place((size_t)c->max_requests * kBL * 3 * (size_t)(c->max_nbins > 0 ? c->max_nbins : 1) * sizeof(unsigned long long));
+    B.ctl = place(sizeof(BatchCtl));
+    B.live = place(sizeof(int));
+    B.hdr = place((kMaxLanes / 32) * sizeof(WarpHdr));
     const size_t words = (size_t)std::max(std::max(lane_words<float, kModeFP32Comp, kMaxPPT>(),
                                                    lane_words<double, kModeFP64, 1>()),
                                           std::max(lane_words<float, kModeFP32Comp, 1, 1>(),
                                                    lane_words<double, kModeFP64, 1, 1>()));
     B.words = words;
-    B.lanes = off; off = align_up(off + words * kMaxLanes * sizeof(uint32_t));
-    B.status = off; off = align_up(off + (size_t)c->max_requests * sizeof(int32_t));
+    B.lanes = place(words * kMaxLanes * sizeof(uint32_t));
+    B.status = place((size_t)c->max_requests * sizeof(int32_t));
     B.total = off;
     return B;
 }
@@ -1492,6 +1505,8 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
     {
         const mlkd_status hs = stall_queues(ctx->arena + BL.ctl, cfg->test_stall_queues, s);
         if (hs != MLKD_OK) return hs;
+        const mlkd_status gs = guards_write(ctx->arena, BL.guard, BL.n_guard, s);
+        if (gs != MLKD_OK) return gs;
     }
 
     BatchLaunch B;
@@ -1634,7 +1649,10 @@ static mlkd_status run_batch(mlkd_context *ctx, const mlkd_problem *problems, in
         }
         o->seconds = secs;
     }
-    return device_checks();
+    mlkd_status cs = device_checks();
+    if (cs == MLKD_OK) cs = guards_check(ctx->arena, BL.guard, BL.n_guard);
+    if (cs == MLKD_OK) cs = guards_check(ctx->arena, ctx->L.guard, ctx->L.n_guard);
+    return cs;
 }
 
 // ---------------------------------------------------------------------------

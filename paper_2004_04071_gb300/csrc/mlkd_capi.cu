@@ -22,17 +22,47 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 Layout arena_layout()
 {
     Layout L;
+    L.n_guard = 0;
     size_t off = 0;
+    // a region of `bytes` at the current offset, then (debug build) its canary
+    auto place = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes);
+        if (kGuardBytes) {
+            L.guard[L.n_guard++] = off;
+            off += kGuardBytes;
+        }
+        return at;
+    };
     // one scratch slot (block partials, level sums, histogram) per level, so
     // that the levels of a round can run at the same time
-    L.partials = off;  off = align_up(off + (size_t)MLKD_MAX_LEVELS * kMaxBlocks * kPartialWords * sizeof(double));
-    L.tmp_stats = off; off = align_up(off + MLKD_MAX_LEVELS * sizeof(DevLevelStats));
-    L.acc_stats = off; off = align_up(off + MLKD_MAX_LEVELS * sizeof(DevLevelStats));
-    L.tmp_hist = off;  off = align_up(off + (size_t)MLKD_MAX_LEVELS * 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
-    L.acc_hist = off;  off = align_up(off + (size_t)MLKD_MAX_LEVELS * 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
-    L.control = off;   off = align_up(off + sizeof(DevControl));
+    L.partials = place((size_t)MLKD_MAX_LEVELS * kMaxBlocks * kPartialWords * sizeof(double));
+    L.tmp_stats = place(MLKD_MAX_LEVELS * sizeof(DevLevelStats));
+    L.acc_stats = place(MLKD_MAX_LEVELS * sizeof(DevLevelStats));
+    L.tmp_hist = place((size_t)MLKD_MAX_LEVELS * 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
+    L.acc_hist = place((size_t)MLKD_MAX_LEVELS * 3 * MLKD_MAX_BINS * sizeof(unsigned long long));
+    L.control = place(sizeof(DevControl));
     L.total = off;
     return L;
+}
+
+mlkd_status guards_write(char *arena, const size_t *guard, int n, cudaStream_t s)
+{
+    for (int i = 0; i < n && kGuardBytes; ++i)
+        MLKD_CUDA(cudaMemsetAsync(arena + guard[i], kGuardByte, kGuardBytes, s));
+    return MLKD_OK;
+}
+
+mlkd_status guards_check(const char *arena, const size_t *guard, int n)
+{
+    if (!kGuardBytes) return MLKD_OK;
+    unsigned char buf[kGuardBytes > 0 ? kGuardBytes : 1];
+    for (int i = 0; i < n; ++i) {
+        MLKD_CUDA(cudaMemcpy(buf, arena + guard[i], kGuardBytes, cudaMemcpyDeviceToHost));
+        for (size_t j = 0; j < kGuardBytes; ++j)
+            if (buf[j] != kGuardByte) return MLKD_EINTERNAL;
+    }
+    return MLKD_OK;
 }
 
 bool validate(const mlkd_problem *p, Derived *d)
@@ -394,6 +424,11 @@ mlkd_status mlkd_context_create(int device, void *arena, size_t arena_bytes, mlk
     c->tmp_hist = (unsigned long long *)(c->arena + L.tmp_hist);
     c->acc_hist = (unsigned long long *)(c->arena + L.acc_hist);
     c->control = (DevControl *)(c->arena + L.control);
+    if (kGuardBytes && (guards_write(c->arena, L.guard, L.n_guard, 0) != MLKD_OK ||
+                        cudaDeviceSynchronize() != cudaSuccess)) {
+        delete c;
+        return MLKD_ECUDA;
+    }
     *out = c;
     return MLKD_OK;
 }
@@ -648,7 +683,8 @@ mlkd_status mlkd_run_level(mlkd_context *ctx, const mlkd_problem *problem, int l
     MLKD_CUDA(cudaStreamSynchronize(s));
     to_host_stats(hs, out);
     st = harvest_timing(ctx);
-    return st != MLKD_OK ? st : device_checks();
+    if (st == MLKD_OK) st = device_checks();
+    return st != MLKD_OK ? st : guards_check(ctx->arena, ctx->L.guard, ctx->L.n_guard);
 }
 
 mlkd_status mlkd_debug_pairs(mlkd_context *ctx, const mlkd_problem *problem, int level,
@@ -854,8 +890,9 @@ static mlkd_status estimate_impl(mlkd_context *ctx, const mlkd_problem *problem,
         out->cost_level[l] = ctl.cost_level[l];
     }
     out->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    const mlkd_status hst = harvest_timing(ctx);
-    return hst != MLKD_OK ? hst : device_checks();
+    mlkd_status hst = harvest_timing(ctx);
+    if (hst == MLKD_OK) hst = device_checks();
+    return hst != MLKD_OK ? hst : guards_check(ctx->arena, ctx->L.guard, ctx->L.n_guard);
 }
 
 extern "C" {

@@ -31,9 +31,21 @@ constexpr uint32_t kWeylA = 0x9E3779B9u;         // Philox key increments (SC'11
 constexpr uint32_t kWeylB = 0xBB67AE85u;
 constexpr int kTimingRing = 64;
 
+// Canary bytes after each arena region in the debug build (MLKD_CHECKS):
+// written when the region is set up, compared after each synchronising call.
+#ifdef MLKD_CHECKS
+constexpr size_t kGuardBytes = 256;
+#else
+constexpr size_t kGuardBytes = 0;
+#endif
+constexpr unsigned char kGuardByte = 0xA5;
+constexpr int kMaxGuards = 16;
+
 // Arena layout of the base workspace (offsets in bytes).
 struct Layout {
     size_t partials, tmp_stats, acc_stats, tmp_hist, acc_hist, control, total;
+    size_t guard[kMaxGuards];    // canary offsets (debug build)
+    int n_guard;
 };
 
 // Derived, validated description of a problem.
@@ -69,6 +81,10 @@ namespace mlkd {
 void batch_release(mlkd_context *ctx);   // frees the batch graph cache (host side)
 void server_release(mlkd_context *ctx);  // stops a running server
 mlkd_status harvest_timing(mlkd_context *ctx);
+// Debug build: fills / compares the canaries at these arena offsets
+// (MLKD_EINTERNAL if a byte changed); no-ops in normal builds.
+mlkd_status guards_write(char *arena, const size_t *guard, int n, cudaStream_t s);
+mlkd_status guards_check(const char *arena, const size_t *guard, int n);
 // Debug builds: MLKD_EINTERNAL if a device check failed since the last call
 // (the caller has synchronised); MLKD_OK always in normal builds.
 mlkd_status device_checks();

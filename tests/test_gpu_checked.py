@@ -66,6 +66,16 @@ def run_all(mk, gpu_problem):
     out["after_runs"] = list(mk.device_checks())
     out["selftest"] = mk.debug_check_selftest(0)
     out["after_selftest"] = list(mk.device_checks())
+    if mk.device_checks()[0]:
+        # A stray write, made on the host: the first canary of the arena sits
+        # right after the 16 level slots of block partial rows (16 x 4096 x 8
+        # doubles); the next call must report it.
+        ctx.arena[16 * 4096 * 8 * 8] = 0
+        try:
+            ctx.run_level(gpu_problem(mk, CASES["free"], precision=mk.PREC_FP64), 1, 0, 100)
+            out["after_corruption"] = mk.MLKD_OK
+        except mk.MlkdError as e:
+            out["after_corruption"] = e.status
     ctx.close()
     return out
 
@@ -92,6 +102,14 @@ def test_selftest_reports_a_failed_check(checked):
     assert checked["after_selftest"][0] == 1 and checked["after_selftest"][1] > 0
 
 
+def test_canary_reports_a_stray_write(checked):
+    """The debug build surrounds the arena regions with canary bytes and
+    compares them after each synchronising call: a byte changed behind the
+    library's back gives MLKD_EINTERNAL."""
+    import paper_2004_04071_gb300 as mk
+    assert checked["after_corruption"] == mk.MLKD_EINTERNAL
+
+
 def _same(a, b):
     """Equal structure: floats to 1e-13 relative, everything else exactly."""
     if isinstance(a, list):
@@ -109,6 +127,6 @@ def test_checked_results_equal_the_normal_build(checked):
     normal = json.loads(json.dumps(run_all(mk, gpu_problem)))
     assert normal["selftest"] == mk.MLKD_ENOTFOUND
     for key, val in checked.items():
-        if key in ("checks", "after_runs", "selftest", "after_selftest"):
+        if key in ("checks", "after_runs", "selftest", "after_selftest", "after_corruption"):
             continue
         assert _same(val, normal[key]), (key, val, normal[key])
