@@ -405,7 +405,7 @@ def run_gpu(args):
                                "L=min(12,ceil(log2(dt0/(eps^2/4)))), tol=1e-3, 128 bins",
                    "form": args.form, "precision": args.precision, "n_fixed": fixed,
                    "batch_config": cfg.as_dict() if args.form == "batch" else None,
-                   "autotune": tune,  # seconds over warp {default, never} x ppt {1,2,4,8} x substeps {16,64,256,unbounded}
+                   "autotune": tune,  # seconds over warp {1024, never, 4096} x ppt {1,2,4,8} x substeps {16,64,256,unbounded}
                    "batch_config_time_to_tolerance": cfg_ttt.as_dict() if args.form == "batch" else None,
                    "autotune_time_to_tolerance": tune_ttt,
                    "events_per_step": ev / args.steps / world,
@@ -425,6 +425,7 @@ def run_gpu(args):
                                              for r in sel_res],
                    "level_selected_error_in_sd": [(r.estimate - x) / math.sqrt(r.variance)
                                                   for r, x in zip(sel_res, exact)],
+                   "level_selected_met": [r.variance <= TOL * TOL / 2 * (1 + 1e-9) for r in sel_res],
                    "time_to_tolerance_plain_fp64_s": ttt_fp64,
                    "time_to_tolerance_speedup_vs_plain_fp64": ttt_fp64 / ttt,
                    "estimates_plain_fp64": [r.estimate for r in r64],
