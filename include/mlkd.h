@@ -66,8 +66,8 @@ typedef enum {
 typedef enum { MLKD_QOI_X2 = 0, MLKD_QOI_X2_PERIODIC = 1, MLKD_QOI_DENSITY = 2,
                MLKD_QOI_X = 3 } mlkd_qoi;
 /* MLKD_QOI_X: F(x) = x, the position at T (the paper's test case, Sec. 5);
- * free space only, per-level calls only (mlkd_run_level, mlkd_estimate,
- * mlkd_debug_pairs). */
+ * free space only; per-level calls (mlkd_run_level, mlkd_estimate,
+ * mlkd_debug_pairs), and the batched form for the heterogeneous backgrounds. */
 
 /* Initial position: x = 0, or density proportional to 1 + cos(2 pi x) on the
  * periodic unit interval (inverse CDF of a uniform). */
