@@ -701,10 +701,11 @@ def run_batched64(args):
     # tune on a cheap sample of the mix: 16 of the requests at tol >= 2e-3
     sample = [mk.make_problem(precision=prec, **dict(dd, tol=max(dd["tol"], 2e-3))) for dd in dicts[:16]]
     best, secs = ctx.autotune_batch(sample, cfg)
+    # one warm-up and one timed run: a run takes about 100 s (the --steps and
+    # --warmup counts are the headline's)
     ts, rs = [], None
-    for _ in range(args.warmup):
-        ctx.estimate_batch(probs, best)
-    for _ in range(max(1, args.steps)):
+    ctx.estimate_batch(probs, best)
+    for _ in range(1):
         t = time.perf_counter()
         rs = ctx.estimate_batch(probs, best)
         ts.append(time.perf_counter() - t)
