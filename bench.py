@@ -698,9 +698,21 @@ def run_batched64(args):
     prec = {"fp32": mk.PREC_FP32_DY64, "fp32comp": mk.PREC_FP32_COMP, "fp64": mk.PREC_FP64}[args.precision]
     dicts = [dict(r, seed=0) for r in W.batched_requests(64, seed=0)]
     probs = [mk.make_problem(precision=prec, **dd) for dd in dicts]
-    # tune on a cheap sample of the mix: 16 of the requests at tol >= 2e-3
+    # tune on cheap samples of the mix: pairs per thread and slices on 16 of
+    # the requests at tol >= 2e-3; then the one-pair-per-warp threshold on all
+    # 64 at tol >= 1e-3 (a small sample is latency-bound and favours one pair
+    # per warp, while the whole mix is throughput-bound)
     sample = [mk.make_problem(precision=prec, **dict(dd, tol=max(dd["tol"], 2e-3))) for dd in dicts[:16]]
     best, secs = ctx.autotune_batch(sample, cfg)
+    floored = [mk.make_problem(precision=prec, **dict(dd, tol=max(dd["tol"], 1e-3))) for dd in dicts]
+    warp_secs = {}
+    for wp in (-1, 0, 4096):
+        c = mk.batch_config(**dict(best.as_dict(), warp_pair_min_events=wp))
+        ctx.estimate_batch(floored, c)
+        t = time.perf_counter()
+        ctx.estimate_batch(floored, c)
+        warp_secs[wp] = time.perf_counter() - t
+    best = mk.batch_config(**dict(best.as_dict(), warp_pair_min_events=min(warp_secs, key=warp_secs.get)))
     # one warm-up and one timed run: a run takes about 100 s (the --steps and
     # --warmup counts are the headline's)
     ts, rs = [], None
@@ -721,7 +733,9 @@ def run_batched64(args):
     out = {"metric": "64 batched MLMC estimators: time to all tolerances", "value": tm, "unit": "s",
            "higher_is_better": False, "data": "synthetic", "precision": args.precision,
            "events_per_s": ev / tm, "events": ev, "best_config": best.as_dict(),
-           "autotune_seconds_ppt_major": secs, "met_tolerance": ok,
+           "autotune_seconds_ppt_major": secs,
+           "warp_pair_threshold_seconds_on_tol_1e-3_mix": {str(k): v for k, v in warp_secs.items()},
+           "met_tolerance": ok,
            "levels_range": [min(len(x) for x in npairs), max(len(x) for x in npairs)],
            "pairs_per_level_range": [min(min(x) for x in npairs), max(max(x) for x in npairs)],
            "per_level_form_seconds": t_plain, "speedup_vs_per_level_form": t_plain / tm}
