@@ -142,7 +142,7 @@ struct BatchLaunch {
     int32_t max_nbins;
     int32_t slice_iters;
     int32_t n_slots;
-    int32_t refill_min;          // idle lanes a warp gathers before it restarts them together
+    int32_t refill_min;          // idle lanes a warp gathers before it hands them started pairs
     int32_t publish_spins;       // bound of the publication wait
     int32_t warp_pair_events;    // levels with at least this many events per pair run one pair per warp (0: never)
     int32_t dbg_req;             // per-pair readout of request slot dbg_req, estimator level
@@ -624,7 +624,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     bool coupled = false;
     typename BatchState<Real, PHYS>::type st[PPT];
     bool active[PPT];           // the lane's pair has events left
-    bool done[PPT];             // the lane holds a pair that reached T but is not yet summed
+    bool done[PPT];             // the lane holds a pair that reached T, not yet queued for summing
     PairSums<MODE> &mom = s_sums[threadIdx.x].mom;
     unsigned long long &ev_f_sum = s_sums[threadIdx.x].ev_f;
     unsigned long long &ev_c_sum = s_sums[threadIdx.x].ev_c;
