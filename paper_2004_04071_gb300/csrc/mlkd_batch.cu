@@ -608,6 +608,10 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
     int valid = hdr->valid;
     int iters = 0;
     int idle = 0;
+    // event iterations of this launch before the warp stores its state; an
+    // unbounded launch stops only if one warp ever reached 2^31 - 1 of them
+    // (it would then store its state like a slice, and the next launch resumes)
+    const int iter_limit = B.slice_iters > 0 ? B.slice_iters : 0x7fffffff;
     StartPool<Real> &SP = s_start[warp];
     FinishPool<Real> &FP = s_finish[warp];
     // warp-uniform bookkeeping, read from shared memory where it is needed
@@ -656,7 +660,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             L.bg.inv_Rdt = bp.inv_Rdt;
             L.n = D->n_level[level];
             L.M = D->M_level[level];
-            L.m_shift = (L.M & (L.M - 1)) == 0 ? __ffs(L.M) - 1 : -1;
+            L.divM.init(L.M);
             L.init = D->init;
             L.word2 = (uint32_t)D->level_of[level] << 24;
             L.request = D->request;
@@ -667,7 +671,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                 H.bg.dt = bp.dt;
                 H.n = L.n;
                 H.M = L.M;
-                H.m_shift = L.m_shift;
+                H.divM = L.divM;
                 H.x0 = (Real)D->x0;
                 H.word2 = L.word2;
                 H.request = L.request;
@@ -899,7 +903,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
 
     for (;;) {
         if (!valid) {
-            if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+            if (iters >= iter_limit) break;
             // Claim order: chunks of small rounds, then chunks whose single
             // pairs outlast a target slice (deep levels, so that the longest
             // serial work starts earliest), then the rest.  With nothing published, a warp of an
@@ -978,7 +982,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
             // takes its event k + 1 + j; the pair's QoI is summed by lane
             // (pair index mod 32).
             for (;;) {
-                if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+                if (iters >= iter_limit) break;
                 if (done[0]) {
                     if (lane == (int)(st[0].pair_lo & 31u)) finish(0);
                     done[0] = false;
@@ -1009,7 +1013,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
         for (;;) {
             // the budget is checked before the pools are touched, so a
             // resumed slice runs exactly the sequence an unsliced run would
-            if (B.slice_iters > 0 && iters >= B.slice_iters) break;
+            if (iters >= iter_limit) break;
 #pragma unroll
             for (int j = 0; j < PPT; ++j) {
                 // pairs that reached T in the last iteration: to the finish pool
@@ -1079,7 +1083,7 @@ batch_pair_kernel(const __grid_constant__ BatchLaunch B)
                         any_done = true;
                     }
                 ++iters;
-                if (__any_sync(kFullMask, any_done) || (B.slice_iters > 0 && iters >= B.slice_iters)) break;
+                if (__any_sync(kFullMask, any_done) || iters >= iter_limit) break;
             }
         }
         if (!chunk_done) {

@@ -330,6 +330,32 @@ __device__ __forceinline__ Draw<double> draw<double>(uint32_t k, uint32_t pair_l
 }
 
 // ---------------------------------------------------------------------------
+// floor(n / M) for 0 <= n < 2^31 and 2 <= M <= 2^30 by a multiply-high and a
+// shift (division by an invariant integer, Granlund and Montgomery, PLDI
+// 1994, Thm. 4.2).  With l = ceil(log2 M) and m = ceil(2^(31+l) / M):
+// 2^(31+l) <= m M <= 2^(31+l) + M - 1 < 2^(31+l) + 2^l, hence
+// floor(n/M) = floor(m n / 2^(31+l)) = umulhi(n, m) >> (l - 1), and m < 2^32
+// (m = 2^31 when M is a power of two).  The coarse-grid index of a fine step
+// takes two instructions for every M.
+// ---------------------------------------------------------------------------
+struct DivM {
+    uint32_t mul;
+    int post;
+    __host__ __device__ void init(int M)
+    {
+        int l = 1;
+        while ((1 << l) < M) ++l;
+        const unsigned long long t = 1ull << (31 + l);
+        mul = (uint32_t)((t + (unsigned long long)(M - 1)) / (unsigned long long)M);
+        post = l - 1;
+    }
+    __device__ __forceinline__ int operator()(int n) const
+    {
+        return (int)(__umulhi((uint32_t)n, mul) >> post);
+    }
+};
+
+// ---------------------------------------------------------------------------
 // Homogeneous background in the working precision.
 // ---------------------------------------------------------------------------
 template <typename Real> struct Background {

@@ -109,7 +109,8 @@ template <typename Real> struct HetPairState {
 
 template <typename Real> struct HetLevel {
     HetBg<Real> bg;
-    int n, M, m_shift;
+    int n, M;
+    DivM divM;                    // floor(n / M)
     Real x0;
     uint32_t word2, request;
 };
@@ -133,7 +134,7 @@ template <typename Real>
 __device__ __forceinline__ int het_coarse_end(const HetLevel<Real> &L, int ic, Real qc)
 {
     const int c = ic + (int)Arith<Real>::min_(qc, (Real)(4 * L.n + 4));
-    const int k = L.m_shift >= 0 ? c >> L.m_shift : c / L.M;
+    const int k = L.divM(c);
     return L.M * (k + 1);
 }
 

@@ -60,7 +60,7 @@ pair_kernel(const __grid_constant__ PairLaunch P)
     L.bg.inv_Rdt = bp.inv_Rdt;
     L.n = P.n;
     L.M = P.M;
-    L.m_shift = (P.M & (P.M - 1)) == 0 ? __ffs(P.M) - 1 : -1;
+    L.divM.init(P.M);
     L.init = P.init == 1 ? 1 : 0;          // a point start is set after pair_start
     L.word2 = P.word2;
     L.request = P.request;
@@ -72,7 +72,7 @@ pair_kernel(const __grid_constant__ PairLaunch P)
         H.bg.dt = bp.dt;
         H.n = P.n;
         H.M = P.M;
-        H.m_shift = L.m_shift;
+        H.divM = L.divM;
         H.x0 = (Real)P.x0;
         H.word2 = P.word2;
         H.request = P.request;
@@ -302,7 +302,7 @@ coarse_draws_kernel(const __grid_constant__ PairLaunch P, int per_pair, double *
     L.bg.inv_Rdt = bp.inv_Rdt;
     L.n = P.n;
     L.M = P.M;
-    L.m_shift = (P.M & (P.M - 1)) == 0 ? __ffs(P.M) - 1 : -1;
+    L.divM.init(P.M);
     L.init = P.init;
     L.word2 = P.word2;
     L.request = P.request;

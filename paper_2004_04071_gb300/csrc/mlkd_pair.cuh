@@ -38,7 +38,7 @@ template <typename Real> struct LevelCtx {
     Background<Real> bg;
     int n;                      // fine steps to T on this level
     int M;                      // refinement factor
-    int m_shift;                // log2 M if M is a power of two, else -1
+    DivM divM;                  // floor(n / M)
     int init;                   // 0: x0 = 0; 1: cosine density
     uint32_t word2;             // level << 24
     uint32_t request;
@@ -46,12 +46,10 @@ template <typename Real> struct LevelCtx {
 
 // End of the coarse step that contains fine-step position base + steps + f
 // (0 <= f < 1), with base on the coarse grid: base + M (steps / M + 1).
-// A power-of-two M (the usual case) divides by a shift.
 template <typename Real>
 __device__ __forceinline__ int next_coarse_end(const LevelCtx<Real> &L, int base, int steps)
 {
-    const int q = L.m_shift >= 0 ? steps >> L.m_shift : steps / L.M;
-    return base + L.M * (q + 1);
+    return base + L.M * (L.divM(steps) + 1);
 }
 
 // CPL: 0 = level 0 (single path), 1 = coupled pair, 2 = decided at run time.

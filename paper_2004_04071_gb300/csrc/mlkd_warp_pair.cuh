@@ -104,10 +104,13 @@ __device__ __forceinline__ bool warp_pair_step(PairState<Real> &st, const LevelC
         if (coupled) {
             // ---- coarse window: triggers, window sums, coarse steps ----
             const int qnc = (int)A::min_(qn, (Real)n);
-            const int cfl = min(ia + qnc, 2 * n + 2);          // floor of the collision after
-            const int Kn = L.m_shift >= 0 ? cfl >> L.m_shift : cfl / L.M;
+            // floor of the collision after, clamped at n: any collision at or
+            // after T lies past the coarse step of the one before it (n is a
+            // multiple of M), so the clamp changes no trigger
+            const int cfl = ia + min(qnc, n - min(ia, n));
+            const int Kn = L.divM(cfl);
             int Kp = __shfl_up_sync(kFullMask, Kn, 1);
-            if (lane == 0) Kp = st.Ec / L.M - 1;               // coarse step of the carried collision
+            if (lane == 0) Kp = L.divM(st.Ec) - 1;             // coarse step of the carried collision
             const bool trig = valid && Kn != Kp;
             const unsigned tmask = __ballot_sync(kFullMask, trig);
             const Real bh2 = valid ? bg.beta_hat_sq(hs) : Real(0);
