@@ -244,19 +244,18 @@ __device__ __forceinline__ Draw<Real> draw_r(uint32_t k, uint32_t pair_lo, uint3
 }
 
 // log u for the 24-bit uniform u = n 2^-24, n = (w >> 8) + 1 in [1, 2^24].
-// Exponent from the leading zero count, mantissa m in [sqrt(1/2), sqrt(2)),
-// and the series log m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9),
+// n = m 2^e with the mantissa m in [sqrt(1/2), sqrt(2)), read from the bits
+// of float(n) (exact for n <= 2^24): subtracting the bits of the float just
+// above sqrt(1/2) (0x3F3504F4) leaves e in the exponent field, and removing
+// e from the exponent leaves m.  Then the series
+// log m = 2 atanh(s) = 2 (s + s^3/3 + s^5/5 + s^7/7 + s^9/9),
 // s = (m - 1)/(m + 1), |s| <= 0.1716 (truncation below 1e-9).
 __device__ __forceinline__ float log_unit24(uint32_t w)
 {
     const uint32_t n = (w >> 8) + 1u;
-    const int lz = __clz(n);
-    int e = 31 - lz;                                          // floor(log2 n)
-    float m = __uint_as_float(0x3F800000u | (((n << lz) << 1) >> 9));
-    if (m > 1.41421356f) {
-        m *= 0.5f;
-        e += 1;
-    }
+    const uint32_t b = __float_as_uint(__uint2float_rn(n));
+    const int e = (int)(b - 0x3F3504F4u) >> 23;
+    const float m = __uint_as_float(b - ((uint32_t)e << 23));
     const float s = __fdividef(m - 1.0f, m + 1.0f);
     const float s2 = s * s;
     float p = fmaf(s2, 0.111111111f, 0.142857143f);
